@@ -1,0 +1,181 @@
+/*
+ * hzb.h — C ABI of the GB300 (sm_103a) multibody axisymmetric Helmholtz solver.
+ *
+ * Method: Hao, Martinsson, Young, "An efficient and highly accurate solver for
+ * multi-body acoustic scattering problems involving rotationally symmetric
+ * scatterers".  A sound-soft scattering problem (Sec. 2, Eq. (basic)) on m
+ * rotationally symmetric bodies is written as the combined-field BIE (Eq.
+ * (intHelm2))
+ *       1/2 sigma(x) + int_Gamma K(x,y) sigma(y) dA(y) = -v(x),
+ *       K(x,y) = d phi(x,y)/d n(y) - i eta phi(x,y),  phi = e^{ik|x-y|}/(4 pi |x-y|)
+ * (eta is a signed real coupling; the paper's Eq. (Gkappa) is eta = -k).  Each body
+ * is discretised by Gauss-Legendre panels on its generating curve times an
+ * equispaced azimuthal rule (Sec. 3.2); its diagonal block is inverted once per
+ * azimuthal Fourier mode (Eqs. (FAF), (singleinverse)); GMRES then solves the
+ * block-diagonally preconditioned system (Sec. 4, Eq. (precond))
+ *       sigma + D^{-1} B sigma = -D^{-1} v,
+ * where B holds the inter-body interactions K(x_i, x_j) w_j (Eq. (nystromnaive)).
+ *
+ * Conventions used by every call:
+ *   - Complex numbers are interleaved (re, im) doubles.
+ *   - Nodes are ordered body-major (order of hzb_add_body), then ring i along the
+ *     generating curve (from its first end), then azimuth l fastest; N is the
+ *     total node count.  A block of R vectors is stored node-major with the R
+ *     values of one node contiguous ("N x R").
+ *   - Host pointers are read or written before the call returns; the library
+ *     keeps no reference to them.  Device pointers (flag *_on_device = 1) must be
+ *     device memory of the context's GPU, and are accessed in stream order on the
+ *     context's stream.
+ *   - Every call returns an hzb_status; on failure hzb_last_error() describes it.
+ *   - The context owns all device memory it allocates; hzb_destroy frees it.
+ *   - A context is used by one host thread at a time.
+ *   - Order: hzb_create -> hzb_set_wave -> hzb_add_body* ->
+ *     hzb_build_scattering_matrices -> solves/applies/fields (any number).
+ *     Calls out of order return HZB_ESTATE.
+ */
+#ifndef HZB_H
+#define HZB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hzb_ctx hzb_ctx;
+
+typedef enum {
+    HZB_OK = 0,
+    HZB_EINVAL = -1,     /* bad argument (null pointer, even N_F, size out of range ...) */
+    HZB_ENOMEM = -2,     /* device or host allocation failed */
+    HZB_ECUDA = -3,      /* a CUDA runtime call failed */
+    HZB_ENOCONV = -4,    /* GMRES reached maxit; best iterate is stored */
+    HZB_ENAN = -5,       /* NaN or Inf met in a residual */
+    HZB_ETIMEOUT = -6,   /* a bounded device wait gave up */
+    HZB_ESTATE = -7      /* call out of order */
+} hzb_status;
+
+typedef enum {
+    HZB_PREC_FP64 = 0,        /* every kernel in FP64 */
+    HZB_PREC_MIXED_FP32 = 1   /* FP64 outer refinement, FP32 inter-body sum and modal apply inside */
+} hzb_precision;
+
+typedef enum { HZB_SPHERE = 0, HZB_SPHEROID = 1, HZB_OPEN_SHELL = 2 } hzb_shape_kind;
+
+typedef struct {
+    int device;            /* CUDA device ordinal */
+    void *cuda_stream;     /* cudaStream_t to launch on; NULL = the legacy default stream */
+    int precision;         /* hzb_precision */
+    double gmres_tol;      /* relative residual of the preconditioned system */
+    int restart;           /* GMRES restart length (<= 0: no restart, up to maxit) */
+    int maxit;             /* total GMRES iterations (inner iterations in mixed mode) */
+    double inner_tol;      /* mixed mode: relative tolerance of each inner FP32 solve */
+    int max_outer;         /* mixed mode: maximum refinement steps */
+} hzb_options;
+
+typedef struct {
+    int kind;              /* hzb_shape_kind */
+    double p[4];           /* SPHERE: (a); SPHEROID: (a, c) semi-axes (a,a,c);
+                              OPEN_SHELL: (R_out, R_in, opening half-angle [rad],
+                              rim radius = (R_out - R_in)/2), opening centred on body -z */
+    int n_panels;          /* Gauss-Legendre panels on the generating curve */
+    int gl_order;          /* nodes per panel, 2..32 */
+    int n_modes;           /* N_F, odd, 3..1023: azimuthal nodes = Fourier modes -M..M */
+} hzb_shape;
+
+typedef struct {
+    int iterations;          /* GMRES iterations (FP64 path) or total inner iterations (mixed) */
+    int outer_iterations;    /* refinement steps (mixed), 1 for the FP64 path */
+    int converged;           /* 1 if every right-hand side met the tolerance */
+    double rel_residual;     /* max over right-hand sides of the final ||b - A x|| / ||b|| */
+    double t_solve_ms;       /* device time of the solve (CUDA events) */
+    double t_setup_ms;       /* device time of hzb_build_scattering_matrices */
+    long long interbody_applies;  /* inter-body sums launched during the solve */
+} hzb_stats;
+
+/* Fill *o with defaults: device 0, default stream, FP64, tol 1e-10, no restart,
+ * maxit 500, inner_tol 1e-5, max_outer 10. */
+void hzb_default_options(hzb_options *o);
+
+/* Create a context on options->device.  Allocates nothing on the device yet.
+ * Errors: HZB_EINVAL (null), HZB_ECUDA (device unavailable). */
+hzb_status hzb_create(const hzb_options *options, hzb_ctx **out);
+hzb_status hzb_destroy(hzb_ctx *ctx);
+const char *hzb_last_error(const hzb_ctx *ctx);
+const char *hzb_status_string(hzb_status s);
+
+/* Change the stream later calls launch on. */
+hzb_status hzb_set_stream(hzb_ctx *ctx, void *cuda_stream);
+/* Change precision, tolerances and limits after creation. */
+hzb_status hzb_set_options(hzb_ctx *ctx, const hzb_options *options);
+
+/* Wavenumber k >= 0 and signed coupling eta (Sec. 2, Eq. (Gkappa) with +i k
+ * replaced by -i eta).  Must precede hzb_add_body. */
+hzb_status hzb_set_wave(hzb_ctx *ctx, double k, double eta);
+
+/* Add body number *body_id (0, 1, ...): shape in its own frame (symmetry axis =
+ * body z), centre c[3], rotation rot[9] row-major whose columns are the body x, y,
+ * z axes in world coordinates (x_world = c + rot * x_body).  Azimuth theta_l =
+ * 2 pi l / N_F is measured from the body x axis.  Bodies with identical hzb_shape
+ * share one set of scattering matrices (Sec. 6.2, repeated shapes). */
+hzb_status hzb_add_body(hzb_ctx *ctx, const hzb_shape *shape, const double c[3],
+                        const double rot[9], int *body_id);
+
+/* Total node count N (valid after the last hzb_add_body). */
+hzb_status hzb_num_nodes(const hzb_ctx *ctx, long long *n);
+
+/* Copy the surface rule to host arrays: xyz N x 3, normals N x 3 (outward unit),
+ * weights N (w = w_GL |gamma'| r 2 pi / N_F, Sec. 3.2).  Any pointer may be NULL.
+ * Forces node generation (device) if it has not happened yet. */
+hzb_status hzb_get_nodes(hzb_ctx *ctx, double *xyz, double *normals, double *weights);
+
+/* Setup, once: per distinct shape the modal kernels, the near-panel product
+ * integration, A~_p = 1/2 I + K_p and S_p = A~_p^{-1} for p = 0..M, all in FP64
+ * on the device (Sec. 3.2, Remark on the cost of precomputation). */
+hzb_status hzb_build_scattering_matrices(hzb_ctx *ctx);
+
+/* Copy A~_p (which = 0) or S_p (which = 1) of the shape of body `body`, mode p in
+ * 0..M, to host out (N_G x N_G complex, row-major). */
+hzb_status hzb_get_modal_block(hzb_ctx *ctx, int body, int p, int which, double *out);
+
+/* y = B sigma (inter-body sum only, Sec. 3.3).  sigma and y: N x R complex.
+ * precision: hzb_precision of the kernel used (FP64 or FP32 with FP64 in/out). */
+hzb_status hzb_interbody(hzb_ctx *ctx, int R, const double *sigma, double *y,
+                         int on_device, int precision);
+
+/* tau = alpha * sigma + beta * D^{-1} y (the per-body FFT -> S_p -> inverse FFT of
+ * the Remark after Eq. (precond)).  sigma may be NULL when alpha = 0. */
+hzb_status hzb_local_inverse(hzb_ctx *ctx, int R, const double *y, const double *sigma,
+                             double alpha, double beta, double *tau, int on_device,
+                             int precision);
+
+/* z = sigma + D^{-1} B sigma, the preconditioned operator of Eq. (precond). */
+hzb_status hzb_apply(hzb_ctx *ctx, int R, const double *sigma, double *z, int on_device,
+                     int precision);
+
+/* Solve for R incident plane waves v = exp(i k d.x), dirs R x 3 unit vectors (host).
+ * The densities stay in the context (hzb_get_density).  Returns HZB_ENOCONV if
+ * some right-hand side missed the tolerance (best iterate kept). */
+hzb_status hzb_solve_plane_waves(hzb_ctx *ctx, int R, const double *dirs, hzb_stats *stats);
+
+/* Solve for R general Dirichlet data sets: v is N x R complex (u = -v on Gamma).
+ * x0 (N x R complex, may be NULL) is an initial guess in the same memory space. */
+hzb_status hzb_solve_data(hzb_ctx *ctx, int R, const double *v, const double *x0,
+                          int on_device, hzb_stats *stats);
+
+/* Copy the densities of the last solve (N x R complex) to sigma. */
+hzb_status hzb_get_density(hzb_ctx *ctx, double *sigma, int on_device);
+
+/* Far-field pattern u_inf(xhat) = (1/4pi) sum_j w_j e^{-ik xhat.x_j}
+ * (-ik xhat.n_j - i eta) sigma_j of the last solve's densities, for n unit
+ * directions xhat (host, n x 3); out: n x R complex (host). */
+hzb_status hzb_far_field(hzb_ctx *ctx, int n, const double *xhat, double *out);
+
+/* Scattered field u(x) = sum_j w_j K(x, x_j) sigma_j at n exterior points x (host,
+ * n x 3), smooth rule (Eq. (intHelm1)); out: n x R complex (host). */
+hzb_status hzb_eval_field(hzb_ctx *ctx, int n, const double *x, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZB_H */

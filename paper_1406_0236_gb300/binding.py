@@ -1,0 +1,305 @@
+"""ctypes binding of include/hzb.h (names follow the C ABI; marshalling only).
+
+Host arrays are numpy complex128 / float64; device arrays are torch CUDA tensors
+(complex128), passed by data_ptr() with the on_device flag.  Nothing here computes
+any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(HERE, "libhzb.so")
+
+HZB_PREC_FP64 = 0
+HZB_PREC_MIXED_FP32 = 1
+HZB_SPHERE, HZB_SPHEROID, HZB_OPEN_SHELL = 0, 1, 2
+
+_STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
+           -4: "GMRES did not converge", -5: "non-finite value", -6: "device wait timed out",
+           -7: "call out of order"}
+
+
+class HzbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("hzb status %d (%s): %s" % (status, _STATUS.get(status, "?"), msg))
+        self.status = status
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
+                ("gmres_tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
+
+
+class _Shape(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("p", ctypes.c_double * 4), ("n_panels", ctypes.c_int),
+                ("gl_order", ctypes.c_int), ("n_modes", ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
+                ("t_setup_ms", ctypes.c_double), ("interbody_applies", ctypes.c_longlong)]
+
+
+@dataclass
+class Stats:
+    iterations: int
+    outer_iterations: int
+    converged: bool
+    rel_residual: float
+    t_solve_ms: float
+    t_setup_ms: float
+    interbody_applies: int
+    status: int = 0
+
+
+@dataclass
+class Options:
+    device: int = 0
+    precision: int = HZB_PREC_FP64
+    gmres_tol: float = 1e-10
+    restart: int = 0
+    maxit: int = 500
+    inner_tol: float = 1e-5
+    max_outer: int = 10
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """Load libhzb.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIBPATH):
+        raise ImportError("libhzb.so is not built (run paper_1406_0236_gb300/build.py); no CPU fallback exists")
+    L = ctypes.CDLL(_LIBPATH)
+    i, d, p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "hzb_default_options": (None, [ctypes.POINTER(_Options)]),
+        "hzb_create": (i, [ctypes.POINTER(_Options), ctypes.POINTER(p)]),
+        "hzb_destroy": (i, [p]),
+        "hzb_last_error": (ctypes.c_char_p, [p]),
+        "hzb_status_string": (ctypes.c_char_p, [i]),
+        "hzb_set_stream": (i, [p, p]),
+        "hzb_set_options": (i, [p, ctypes.POINTER(_Options)]),
+        "hzb_set_wave": (i, [p, d, d]),
+        "hzb_add_body": (i, [p, ctypes.POINTER(_Shape), _D, _D, ctypes.POINTER(i)]),
+        "hzb_num_nodes": (i, [p, ctypes.POINTER(ctypes.c_longlong)]),
+        "hzb_get_nodes": (i, [p, p, p, p]),
+        "hzb_build_scattering_matrices": (i, [p]),
+        "hzb_get_modal_block": (i, [p, i, i, i, p]),
+        "hzb_interbody": (i, [p, i, p, p, i, i]),
+        "hzb_local_inverse": (i, [p, i, p, p, d, d, p, i, i]),
+        "hzb_apply": (i, [p, i, p, p, i, i]),
+        "hzb_solve_plane_waves": (i, [p, i, p, ctypes.POINTER(_Stats)]),
+        "hzb_solve_data": (i, [p, i, p, p, i, ctypes.POINTER(_Stats)]),
+        "hzb_get_density": (i, [p, p, i]),
+        "hzb_far_field": (i, [p, i, p, p]),
+        "hzb_eval_field": (i, [p, i, p, p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _is_dev(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+def _ptr(a):
+    if _is_dev(a):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Solver:
+    """One context of the C library.  Typical use:
+
+        s = Solver(k, eta); s.add_body(...); s.build_scattering_matrices()
+        st = s.solve_plane_waves(dirs); sigma = s.get_density(); u = s.far_field(xhat)
+    """
+
+    def __init__(self, k: float, eta: float, options: Options = None, stream=None):
+        L = lib()
+        o = options or Options()
+        co = _Options()
+        L.hzb_default_options(ctypes.byref(co))
+        co.device, co.precision, co.gmres_tol = o.device, o.precision, o.gmres_tol
+        co.restart, co.maxit, co.inner_tol, co.max_outer = o.restart, o.maxit, o.inner_tol, o.max_outer
+        co.cuda_stream = stream
+        self._opt = co
+        h = ctypes.c_void_p()
+        self._check(L.hzb_create(ctypes.byref(co), ctypes.byref(h)), ctx=None)
+        self._h = h
+        self._check(L.hzb_set_wave(h, float(k), float(eta)))
+        self.k, self.eta = float(k), float(eta)
+        self.bodies = 0
+
+    # ------------------------------------------------------------ plumbing
+    def _check(self, status: int, ctx="self"):
+        if status != 0:
+            msg = lib().hzb_last_error(self._h).decode() if ctx is not None and getattr(self, "_h", None) else ""
+            raise HzbError(status, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hzb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle: int):
+        self._check(lib().hzb_set_stream(self._h, ctypes.c_void_p(stream_handle)))
+
+    def set_options(self, **kw):
+        for k_, v in kw.items():
+            setattr(self._opt, k_, v)
+        self._check(lib().hzb_set_options(self._h, ctypes.byref(self._opt)))
+
+    # ------------------------------------------------------------ geometry
+    def add_body(self, kind: int, params, n_panels: int, gl_order: int, n_modes: int, center, rot) -> int:
+        s = _Shape()
+        s.kind = int(kind)
+        pp = list(params) + [0.0] * (4 - len(params))
+        for q in range(4):
+            s.p[q] = float(pp[q])
+        s.n_panels, s.gl_order, s.n_modes = int(n_panels), int(gl_order), int(n_modes)
+        c = np.ascontiguousarray(center, dtype=np.float64)
+        r = np.ascontiguousarray(np.asarray(rot, dtype=np.float64).reshape(9))
+        bid = ctypes.c_int()
+        self._check(lib().hzb_add_body(self._h, ctypes.byref(s), c.ctypes.data_as(_D), r.ctypes.data_as(_D),
+                                       ctypes.byref(bid)))
+        self.bodies += 1
+        return bid.value
+
+    @classmethod
+    def from_workload(cls, wl, options: Options = None, stream=None) -> "Solver":
+        s = cls(wl.k, wl.eta, options, stream)
+        for b in wl.bodies:
+            sh = b.shape
+            s.add_body(sh.kind, sh.params, sh.n_panels, sh.gl_order, sh.n_modes, b.center, b.rot)
+        return s
+
+    @property
+    def N(self) -> int:
+        n = ctypes.c_longlong()
+        self._check(lib().hzb_num_nodes(self._h, ctypes.byref(n)))
+        return n.value
+
+    def get_nodes(self):
+        N = self.N
+        x = np.zeros((N, 3)); n = np.zeros((N, 3)); w = np.zeros(N)
+        self._check(lib().hzb_get_nodes(self._h, _ptr(x), _ptr(n), _ptr(w)))
+        return x, n, w
+
+    def build_scattering_matrices(self):
+        self._check(lib().hzb_build_scattering_matrices(self._h))
+
+    def get_modal_block(self, body: int, p: int, which: int = 1, ng: int = None) -> np.ndarray:
+        """which = 0: A~_p, which = 1: S_p (N_G x N_G complex)."""
+        if ng is None:
+            raise ValueError("pass ng (rings of the body's shape)")
+        out = np.zeros((ng, ng), dtype=np.complex128)
+        self._check(lib().hzb_get_modal_block(self._h, int(body), int(p), int(which), _ptr(out)))
+        return out
+
+    # ------------------------------------------------------------ operators
+    def _io(self, a):
+        dev = _is_dev(a)
+        if dev:
+            if not a.is_contiguous():
+                raise ValueError("device tensors must be contiguous")
+            out = a.new_empty(a.shape)
+        else:
+            a = np.ascontiguousarray(a, dtype=np.complex128)
+            out = np.empty_like(a)
+        R = 1 if a.ndim == 1 else int(a.shape[1])
+        return a, out, R, int(dev)
+
+    def interbody(self, sigma, precision: int = HZB_PREC_FP64):
+        a, out, R, dev = self._io(sigma)
+        self._check(lib().hzb_interbody(self._h, R, _ptr(a), _ptr(out), dev, int(precision)))
+        return out
+
+    def local_inverse(self, y, sigma=None, alpha: float = 0.0, beta: float = 1.0, precision: int = HZB_PREC_FP64):
+        a, out, R, dev = self._io(y)
+        sp = None
+        if sigma is not None:
+            s2 = sigma if dev else np.ascontiguousarray(sigma, dtype=np.complex128)
+            sp = _ptr(s2)
+        self._check(lib().hzb_local_inverse(self._h, R, _ptr(a), sp, float(alpha), float(beta), _ptr(out), dev,
+                                            int(precision)))
+        return out
+
+    def apply(self, sigma, precision: int = HZB_PREC_FP64):
+        a, out, R, dev = self._io(sigma)
+        self._check(lib().hzb_apply(self._h, R, _ptr(a), _ptr(out), dev, int(precision)))
+        return out
+
+    # ------------------------------------------------------------ solves
+    def _stats(self, st: _Stats, status: int) -> Stats:
+        return Stats(st.iterations, st.outer_iterations, bool(st.converged), st.rel_residual, st.t_solve_ms,
+                     st.t_setup_ms, st.interbody_applies, status)
+
+    def solve_plane_waves(self, dirs, allow_noconv: bool = False) -> Stats:
+        d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+        st = _Stats()
+        rc = lib().hzb_solve_plane_waves(self._h, int(d.shape[0]), _ptr(d), ctypes.byref(st))
+        if rc != 0 and not (allow_noconv and rc == -4):
+            self._check(rc)
+        self._R = int(d.shape[0])
+        return self._stats(st, rc)
+
+    def solve_data(self, v, x0=None, allow_noconv: bool = False) -> Stats:
+        a = v if _is_dev(v) else np.ascontiguousarray(v, dtype=np.complex128)
+        R = 1 if a.ndim == 1 else int(a.shape[1])
+        xp = None
+        if x0 is not None:
+            x0 = x0 if _is_dev(x0) else np.ascontiguousarray(x0, dtype=np.complex128)
+            xp = _ptr(x0)
+        st = _Stats()
+        rc = lib().hzb_solve_data(self._h, R, _ptr(a), xp, int(_is_dev(a)), ctypes.byref(st))
+        if rc != 0 and not (allow_noconv and rc == -4):
+            self._check(rc)
+        self._R = R
+        return self._stats(st, rc)
+
+    def get_density(self, out=None):
+        R = getattr(self, "_R", 1)
+        if out is None:
+            out = np.zeros((self.N, R), dtype=np.complex128)
+        self._check(lib().hzb_get_density(self._h, _ptr(out), int(_is_dev(out))))
+        return out
+
+    def far_field(self, xhat) -> np.ndarray:
+        x = np.ascontiguousarray(np.atleast_2d(xhat), dtype=np.float64)
+        out = np.zeros((x.shape[0], getattr(self, "_R", 1)), dtype=np.complex128)
+        self._check(lib().hzb_far_field(self._h, int(x.shape[0]), _ptr(x), _ptr(out)))
+        return out
+
+    def eval_field(self, pts) -> np.ndarray:
+        x = np.ascontiguousarray(np.atleast_2d(pts), dtype=np.float64)
+        out = np.zeros((x.shape[0], getattr(self, "_R", 1)), dtype=np.complex128)
+        self._check(lib().hzb_eval_field(self._h, int(x.shape[0]), _ptr(x), _ptr(out)))
+        return out

@@ -1,0 +1,183 @@
+// Internal declarations of the hzb library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hzb.h"
+
+namespace hzb {
+
+// ---------------------------------------------------------------- geometry (host)
+
+// One smooth piece of a generating curve.  type 0: (a sin t, c cos t);
+// type 1: arc of radius R at polar angle th0 + sg * t; type 2: rim semicircle.
+struct Piece {
+    int type;
+    double p[6];
+    double t0, t1;
+};
+
+struct Panel {
+    int piece;
+    double ta, tb;
+};
+
+// Discretised generating curve of one distinct shape.
+struct ShapeGeom {
+    hzb_shape spec;
+    int NG = 0, NF = 0, M = 0;
+    std::vector<Piece> pieces;
+    std::vector<Panel> panels;
+    // per ring node
+    std::vector<double> t, r, z, nr, nz, ds, speed;
+    std::vector<int> piece_of, panel_of;
+    std::vector<double> panel_len;
+    // near-panel list: for ring i, near_start[i] .. near_start[i+1]-1 index into near_panel
+    std::vector<int> near_start, near_panel;
+    std::vector<double> near_tstar;       // closest parameter on that panel
+};
+
+bool build_shape_geometry(const hzb_shape &spec, ShapeGeom &g, std::string &err);
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
+// evaluate gamma and gamma' of a piece at t
+void piece_eval(const Piece &pc, double t, double &r, double &z, double &dr, double &dz);
+
+// ---------------------------------------------------------------- device buffers
+
+template <typename T>
+struct DevBuf {
+    T *ptr = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t count) {
+        if (count <= n) return cudaSuccess;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&ptr, count * sizeof(T) + 256);
+        if (e == cudaSuccess) n = count;
+        return e;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        n = 0;
+    }
+};
+
+struct ShapeDev {
+    ShapeGeom geom;
+    std::vector<int> bodies;              // bodies using this shape, in order
+    DevBuf<double> ring;                  // NG x 8: r, z, nr, nz, ds, t, (unused)
+    DevBuf<long long> body_offs;          // first node of each body of this shape
+    DevBuf<double2> A64;                  // (M+1) x NG x NG: A~_p
+    DevBuf<double2> S64;                  // (M+1) x NG x NG: S_p = A~_p^{-1}
+    DevBuf<float2> S32;                   // FP32 copy of S64
+};
+
+struct BodyRec {
+    int shape;
+    double c[3];
+    double rot[9];
+    long long offset;   // first node
+    int n_nodes;
+    int index_in_shape;
+};
+
+// CTA work item of the inter-body sum: a contiguous target range inside one body.
+struct TargetBlock {
+    int start;      // first target node
+    int count;      // targets in this block
+    int excl_lo;    // source range of the target's own body [excl_lo, excl_hi)
+    int excl_hi;
+};
+
+}  // namespace hzb
+
+struct hzb_ctx {
+    hzb_options opt;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int state = 0;          // 0 created, 1 wave set, 2 bodies being added, 3 built
+    double k = 0.0, eta = 0.0;
+    std::vector<hzb::ShapeDev *> shapes;
+    std::vector<hzb::BodyRec> bodies;
+    long long N = 0;
+    bool nodes_ready = false;
+    double center[3] = {0, 0, 0};  // origin of the FP32 coordinates
+    double t_setup_ms = 0.0;
+
+    // geometry on the device
+    hzb::DevBuf<double4> pos64;     // x, y, z, w
+    hzb::DevBuf<double4> nrm64;     // nx, ny, nz, 0
+    hzb::DevBuf<float4> pos32;      // x - center (FP32), w
+    hzb::DevBuf<float4> nrm32;
+    hzb::DevBuf<int> body_of;
+    hzb::DevBuf<hzb::TargetBlock> tblocks;
+    int n_tblocks = 0;
+    hzb::DevBuf<double> body_xf;    // per body: c[3], rot[9]
+
+    // workspaces
+    hzb::DevBuf<double2> w_a, w_b, w_c, w_d;   // N x R
+    hzb::DevBuf<float2> f_a, f_b;              // N x R (FP32)
+    hzb::DevBuf<double2> yhat64;               // modal workspace FP64
+    hzb::DevBuf<double2> that64;
+    hzb::DevBuf<float2> yhat32, that32;
+    hzb::DevBuf<double2> s_b, s_r, s_d;        // solve: right-hand side, residual, correction
+    hzb::DevBuf<double2> io_in, io_out;        // staging of host inputs and outputs
+    hzb::DevBuf<double> io_small;              // staging of directions and points
+    hzb::DevBuf<double2> tiny;                 // residual norms
+    hzb::DevBuf<double2> sol;                  // densities of the last solve, N x R
+    int sol_R = 0;
+    hzb::DevBuf<double> red;                   // reduction scratch
+    hzb::DevBuf<double2> krylov;               // (m+1) x N x R
+    hzb::DevBuf<double2> small;                // Hessenberg etc.
+    double *host_pinned = nullptr;             // small pinned host buffer
+    size_t host_pinned_n = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    long long interbody_calls = 0;
+};
+
+// ---------------------------------------------------------------- kernels' host entry points
+namespace hzb {
+
+hzb_status fail(hzb_ctx *c, hzb_status s, const std::string &msg);
+hzb_status check_cuda(hzb_ctx *c, cudaError_t e, const char *what);
+
+// setup.cu
+hzb_status make_nodes(hzb_ctx *c);
+hzb_status build_shape_matrices(hzb_ctx *c, ShapeDev &s);
+
+// nbody.cu: y = B sigma; sigma, y device N x R complex FP64 (FP32 path converts internally)
+hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
+hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
+// field at external points (no exclusion): out T x R (device), pts T x 3 (device)
+hzb_status field_points64(hzb_ctx *c, int R, const double2 *sigma, int T, const double *pts,
+                          double2 *out);
+
+// modal.cu: tau = alpha sigma + beta D^{-1} y
+hzb_status local_inverse64(hzb_ctx *c, int R, const double2 *y, const double2 *sigma,
+                           double alpha, double beta, double2 *tau);
+hzb_status local_inverse32(hzb_ctx *c, int R, const double2 *y, const double2 *sigma,
+                           double alpha, double beta, double2 *tau);
+
+// krylov.cu
+hzb_status apply_op(hzb_ctx *c, int R, const double2 *x, double2 *z, int precision);
+hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is_zero,
+                       int precision, double tol, int maxit, int restart,
+                       int *iters, double *relres, int *converged);
+hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *st);
+
+// fields.cu
+hzb_status plane_waves(hzb_ctx *c, int R, const double *dirs_dev, double2 *v);
+hzb_status far_field64(hzb_ctx *c, int R, const double2 *sigma, int n, const double *xhat_dev,
+                       double2 *out);
+
+// small device helpers
+hzb_status vec_copy(hzb_ctx *c, double2 *dst, const double2 *src, size_t n);
+hzb_status vec_zero(hzb_ctx *c, double2 *dst, size_t n);
+
+}  // namespace hzb

@@ -1,0 +1,459 @@
+// GMRES on the block-diagonally preconditioned system (Sec. 4, Eq. (precond))
+//     sigma + D^{-1} B sigma = -D^{-1} v,
+// batched over R right-hand sides that each have their own Krylov space (one
+// operator apply serves all of them).  Arnoldi uses classical Gram-Schmidt with
+// one re-orthogonalisation (CGS2); the Hessenberg least-squares problem is updated
+// by complex Givens rotations on the device; the host reads back only the R
+// residual estimates per iteration.  The paper stops at a residual of 1e-9 and does
+// not state restart or orthogonalisation; zero initial guess unless one is given.
+//
+// Mixed precision (FP64 outer refinement): r = b - A x with the FP64 operator,
+// an inner GMRES on A d = r whose operator applies run the FP32 inter-body sum and
+// FP32 modal GEMMs (Arnoldi and least squares stay FP64), x += d, repeat.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "hzb_internal.h"
+#include "kernel_math.cuh"
+
+namespace hzb {
+
+static const int RED_THREADS = 256;
+
+// partial[(v * R + r) * nblk + blk] = sum over this block's nodes of conj(V_v) w
+__global__ void cdot_partial_kernel(long long N, int R, const double2 *__restrict__ V, long long vstride,
+                                    const double2 *__restrict__ w, double2 *partial)
+{
+    __shared__ double2 red[RED_THREADS];
+    const int v = blockIdx.y, r = blockIdx.z, nblk = gridDim.x;
+    const double2 *Vv = V + v * vstride;
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)nblk * blockDim.x) {
+        double2 a = Vv[i * R + r], b = w[i * R + r];
+        acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+        acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[((size_t)v * R + r) * nblk + blockIdx.x] = red[0];
+}
+
+__global__ void cdot_final_kernel(int nvr, int nblk, const double2 *partial, double2 *out)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nvr) return;
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = 0; b < nblk; ++b) s = cadd(s, partial[(size_t)e * nblk + b]);
+    out[e] = s;
+}
+
+// w[i][r] -= sum_{v < nv} V_v[i][r] h[v][r]
+__global__ void caxpy_multi_kernel(long long N, int R, int nv, const double2 *__restrict__ V, long long vstride,
+                                   const double2 *__restrict__ h, double2 *w)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * R) return;
+    int r = (int)(e % R);
+    double2 acc = w[e];
+    for (int v = 0; v < nv; ++v) {
+        double2 hv = h[v * R + r];
+        cfma(acc, make_double2(-hv.x, -hv.y), V[v * vstride + e]);
+    }
+    w[e] = acc;
+}
+
+// x[i][r] += sum_{v < jdone[r]} V_v[i][r] y[v][r]
+__global__ void update_x_kernel(long long N, int R, int nv, const double2 *__restrict__ V, long long vstride,
+                                const double2 *__restrict__ y, const int *__restrict__ jdone, double2 *x)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * R) return;
+    int r = (int)(e % R);
+    int nj = min(jdone[r], nv);
+    double2 acc = x[e];
+    for (int v = 0; v < nj; ++v) cfma(acc, y[v * R + r], V[v * vstride + e]);
+    x[e] = acc;
+}
+
+__global__ void scale_kernel(long long N, int R, const double2 *w, const double *inv, double2 *out)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * R) return;
+    out[e] = cscale(w[e], inv[e % R]);
+}
+
+__global__ void axpby_kernel(long long n, double a, const double2 *x, double b, const double2 *y, double2 *out)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double2 u = x[e], v = y[e];
+    out[e] = make_double2(a * u.x + b * v.x, a * u.y + b * v.y);
+}
+
+struct GmresState {
+    double2 *H;      // m x m x R: H[(row * m + col) * R + r]  (upper triangle after rotations)
+    double2 *cs, *sn;  // m x R
+    double2 *g;      // (m + 1) x R
+    double2 *h1, *h2;  // (m + 1) x R
+    double2 *nrm2;   // R  (w^H w)
+    double *bnorm;   // R
+    double *res;     // R relative residual estimate
+    double *inv;     // R scale of the next basis vector
+    int *active;     // R
+    int *jdone;      // R
+};
+
+// Start of a cycle: beta = ||r0||, g = (beta, 0, ...), 1/beta as the scale of V_0.
+__global__ void cycle_start_kernel(int R, int m, GmresState s, double tol, int first)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double beta = sqrt(fmax(s.nrm2[r].x, 0.0));
+    if (first) s.bnorm[r] = beta;
+    double bn = s.bnorm[r];
+    double rel = bn > 0.0 ? beta / bn : 0.0;
+    s.res[r] = rel;
+    int act = (bn > 0.0 && rel > tol && isfinite(beta)) ? 1 : 0;
+    s.active[r] = act;
+    s.jdone[r] = 0;
+    for (int q = 0; q <= m; ++q) s.g[q * R + r] = make_double2(0.0, 0.0);
+    s.g[r] = make_double2(beta, 0.0);
+    s.inv[r] = (act && beta > 0.0) ? 1.0 / beta : 0.0;
+}
+
+// Arnoldi column j: h = h1 + h2 (CGS2), h_{j+1,j} = ||w||; apply the previous
+// rotations, form the one that zeroes h_{j+1,j}, update g and the residual.
+__global__ void givens_kernel(int R, int m, int j, GmresState s, double tol)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    if (!s.active[r]) {
+        s.inv[r] = 0.0;
+        return;
+    }
+    double hn = sqrt(fmax(s.nrm2[r].x, 0.0));
+    for (int i = 0; i <= j; ++i) {
+        double2 v = cadd(s.h1[i * R + r], s.h2[i * R + r]);
+        s.H[((size_t)i * m + j) * R + r] = v;
+    }
+    for (int i = 0; i < j; ++i) {
+        double2 a = s.H[((size_t)i * m + j) * R + r], b = s.H[((size_t)(i + 1) * m + j) * R + r];
+        double2 c = s.cs[i * R + r], sn = s.sn[i * R + r];
+        double2 t = cadd(cmul(c, a), cmul(sn, b));
+        double2 u = csub(cmul(cconj(c), b), cmul(cconj(sn), a));
+        s.H[((size_t)i * m + j) * R + r] = t;
+        s.H[((size_t)(i + 1) * m + j) * R + r] = u;
+    }
+    double2 a = s.H[((size_t)j * m + j) * R + r];
+    double den = sqrt(a.x * a.x + a.y * a.y + hn * hn);
+    double2 c, sn;
+    if (den > 0.0) {
+        c = make_double2(a.x / den, -a.y / den);      // conj(a) / den
+        sn = make_double2(hn / den, 0.0);             // conj(h_{j+1,j}) / den, h real
+    } else {
+        c = make_double2(1.0, 0.0);
+        sn = make_double2(0.0, 0.0);
+    }
+    s.cs[j * R + r] = c;
+    s.sn[j * R + r] = sn;
+    s.H[((size_t)j * m + j) * R + r] = make_double2(den, 0.0);
+    double2 gj = s.g[j * R + r];
+    s.g[(j + 1) * R + r] = cscale(cmul(cconj(sn), gj), -1.0);
+    s.g[j * R + r] = cmul(c, gj);
+    double2 gn = s.g[(j + 1) * R + r];
+    double rel = sqrt(gn.x * gn.x + gn.y * gn.y) / s.bnorm[r];
+    s.res[r] = rel;
+    s.jdone[r] = j + 1;
+    bool done = !(rel > tol) || !(hn > 1e-300) || !isfinite(rel);
+    s.inv[r] = done ? 0.0 : 1.0 / hn;
+    if (done) s.active[r] = 0;
+}
+
+// y = H^{-1} g on the leading jdone x jdone upper triangle.
+__global__ void backsolve_kernel(int R, int m, GmresState s, double2 *y)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    int n = s.jdone[r];
+    for (int i = n - 1; i >= 0; --i) {
+        double2 acc = s.g[i * R + r];
+        for (int q = i + 1; q < n; ++q) cfma(acc, make_double2(-1.0, 0.0), cmul(s.H[((size_t)i * m + q) * R + r], y[q * R + r]));
+        double2 d = s.H[((size_t)i * m + i) * R + r];
+        double dd = d.x * d.x + d.y * d.y;
+        y[i * R + r] = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
+                                : make_double2(0.0, 0.0);
+    }
+}
+
+hzb_status vec_copy(hzb_ctx *c, double2 *dst, const double2 *src, size_t n)
+{
+    return check_cuda(c, cudaMemcpyAsync(dst, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream), "copy");
+}
+
+hzb_status vec_zero(hzb_ctx *c, double2 *dst, size_t n)
+{
+    return check_cuda(c, cudaMemsetAsync(dst, 0, n * sizeof(double2), c->stream), "memset");
+}
+
+static unsigned nblocks(long long n, int th = 256) { return (unsigned)((n + th - 1) / th); }
+
+// out[v * R + r] = sum_i conj(V_v[i][r]) w[i][r], v < nv
+static hzb_status cdots(hzb_ctx *c, int R, int nv, const double2 *V, long long vstride, const double2 *w,
+                        double2 *out)
+{
+    long long N = c->N;
+    int nblk = (int)std::min<long long>(120, std::max<long long>(1, N / (RED_THREADS * 8)));
+    size_t need = (size_t)nv * R * nblk;
+    if (check_cuda(c, c->w_d.ensure(std::max<size_t>(need, (size_t)N * R)), "alloc partial")) return HZB_ENOMEM;
+    cdot_partial_kernel<<<dim3(nblk, nv, R), RED_THREADS, 0, c->stream>>>(N, R, V, vstride, w, c->w_d.ptr);
+    cdot_final_kernel<<<nblocks(nv * R), 256, 0, c->stream>>>(nv * R, nblk, c->w_d.ptr, out);
+    return check_cuda(c, cudaGetLastError(), "cdot");
+}
+
+hzb_status apply_op(hzb_ctx *c, int R, const double2 *x, double2 *z, int precision)
+{
+    size_t n = (size_t)c->N * R;
+    if (check_cuda(c, c->w_c.ensure(n), "alloc apply")) return HZB_ENOMEM;
+    hzb_status st;
+    if (precision == HZB_PREC_MIXED_FP32) {
+        if ((st = interbody32(c, R, x, c->w_c.ptr))) return st;
+        return local_inverse32(c, R, c->w_c.ptr, x, 1.0, 1.0, z);
+    }
+    if ((st = interbody64(c, R, x, c->w_c.ptr))) return st;
+    return local_inverse64(c, R, c->w_c.ptr, x, 1.0, 1.0, z);
+}
+
+static hzb_status ensure_pinned(hzb_ctx *c, size_t n)
+{
+    if (c->host_pinned_n >= n) return HZB_OK;
+    if (c->host_pinned) cudaFreeHost(c->host_pinned);
+    c->host_pinned = nullptr;
+    c->host_pinned_n = 0;
+    if (check_cuda(c, cudaMallocHost(&c->host_pinned, n * sizeof(double)), "pinned")) return HZB_ENOMEM;
+    c->host_pinned_n = n;
+    return HZB_OK;
+}
+
+hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is_zero, int precision, double tol,
+                       int maxit, int restart, int *iters, double *relres, int *converged)
+{
+    const long long N = c->N;
+    const size_t NR = (size_t)N * R;
+    int m = (restart > 0) ? std::min(restart, maxit) : maxit;
+    // keep the Krylov basis within 32 GB of HBM: restart earlier for large N x R
+    const double basis_budget = 32.0 * (1ull << 30);
+    const long long m_fit = (long long)(basis_budget / (16.0 * (double)NR)) - 1;
+    m = (int)std::max<long long>(std::min<long long>(m, m_fit), 8);
+    hzb_status st;
+    if (check_cuda(c, c->krylov.ensure((size_t)(m + 1) * NR), "alloc krylov basis") ||
+        check_cuda(c, c->w_a.ensure(NR), "alloc") || check_cuda(c, c->w_b.ensure(NR), "alloc"))
+        return HZB_ENOMEM;
+    // small state, laid out in one buffer
+    size_t nsmall = (size_t)m * m * R + 2 * (size_t)m * R + 3 * (size_t)(m + 1) * R + R + (size_t)m * R + 4 * R;
+    if (check_cuda(c, c->small.ensure(nsmall), "alloc hessenberg")) return HZB_ENOMEM;
+    if (ensure_pinned(c, 2 * (size_t)R + 4)) return HZB_ENOMEM;
+    GmresState s;
+    double2 *p = c->small.ptr;
+    s.H = p; p += (size_t)m * m * R;
+    s.cs = p; p += (size_t)m * R;
+    s.sn = p; p += (size_t)m * R;
+    s.g = p; p += (size_t)(m + 1) * R;
+    s.h1 = p; p += (size_t)(m + 1) * R;
+    s.h2 = p; p += (size_t)(m + 1) * R;
+    s.nrm2 = p; p += R;
+    double2 *y = p; p += (size_t)m * R;
+    s.bnorm = (double *)p; p += R;
+    s.res = (double *)p; p += R;
+    s.inv = (double *)p; p += R;
+    int *ip = (int *)p;
+    s.active = ip;
+    s.jdone = ip + R;
+
+    double2 *V = c->krylov.ptr;
+    double2 *w = c->w_a.ptr;
+    const unsigned gN = nblocks((long long)NR);
+    const unsigned gR = nblocks(R, 64);
+    int total = 0;
+    bool first = true, all_done = false;
+    double *hres = c->host_pinned;
+    int *hact = (int *)(c->host_pinned + R);
+    if (x_is_zero && (st = vec_zero(c, x, NR))) return st;
+    // ||b|| once
+    if ((st = cdots(c, R, 1, b, 0, b, s.nrm2))) return st;
+    while (true) {
+        // r0 = b - A x  (b itself for a zero start)
+        if (first && x_is_zero) {
+            if ((st = vec_copy(c, w, b, NR))) return st;
+        } else {
+            if ((st = apply_op(c, R, x, c->w_b.ptr, precision))) return st;
+            axpby_kernel<<<gN, 256, 0, c->stream>>>((long long)NR, 1.0, b, -1.0, c->w_b.ptr, w);
+        }
+        if (!(first)) {
+            if ((st = cdots(c, R, 1, w, 0, w, s.nrm2))) return st;
+        }
+        cycle_start_kernel<<<gR, 64, 0, c->stream>>>(R, m, s, tol, first ? 1 : 0);
+        if (first && !x_is_zero) {
+            // the first norm above was ||b||; the residual norm of a non-zero start is needed too
+            if ((st = cdots(c, R, 1, w, 0, w, s.nrm2))) return st;
+            cycle_start_kernel<<<gR, 64, 0, c->stream>>>(R, m, s, tol, 0);
+        }
+        first = false;
+        scale_kernel<<<gN, 256, 0, c->stream>>>(N, R, w, s.inv, V);
+        cudaMemcpyAsync(hres, s.res, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(hact, s.active, R * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (check_cuda(c, cudaStreamSynchronize(c->stream), "gmres start")) return HZB_ECUDA;
+        bool any = false;
+        for (int r = 0; r < R; ++r) any |= hact[r] != 0;
+        if (!any || total >= maxit) {
+            all_done = !any;
+            break;
+        }
+        int j = 0;
+        for (; j < m && total < maxit; ++j) {
+            double2 *Vj = V + (size_t)j * NR;
+            if ((st = apply_op(c, R, Vj, w, precision))) return st;
+            if ((st = cdots(c, R, j + 1, V, (long long)NR, w, s.h1))) return st;
+            caxpy_multi_kernel<<<gN, 256, 0, c->stream>>>(N, R, j + 1, V, (long long)NR, s.h1, w);
+            if ((st = cdots(c, R, j + 1, V, (long long)NR, w, s.h2))) return st;
+            caxpy_multi_kernel<<<gN, 256, 0, c->stream>>>(N, R, j + 1, V, (long long)NR, s.h2, w);
+            if ((st = cdots(c, R, 1, w, 0, w, s.nrm2))) return st;
+            givens_kernel<<<gR, 64, 0, c->stream>>>(R, m, j, s, tol);
+            scale_kernel<<<gN, 256, 0, c->stream>>>(N, R, w, s.inv, V + (size_t)(j + 1) * NR);
+            cudaMemcpyAsync(hres, s.res, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+            cudaMemcpyAsync(hact, s.active, R * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+            if (check_cuda(c, cudaStreamSynchronize(c->stream), "gmres iteration")) return HZB_ECUDA;
+            ++total;
+            bool anyact = false;
+            for (int r = 0; r < R; ++r) anyact |= hact[r] != 0;
+            if (!anyact) break;
+        }
+        backsolve_kernel<<<gR, 64, 0, c->stream>>>(R, m, s, y);
+        update_x_kernel<<<gN, 256, 0, c->stream>>>(N, R, m, V, (long long)NR, y, s.jdone, x);
+        if (check_cuda(c, cudaGetLastError(), "gmres update")) return HZB_ECUDA;
+        bool anyact = false;
+        for (int r = 0; r < R; ++r) anyact |= hact[r] != 0;
+        if (!anyact) {
+            all_done = true;
+            break;
+        }
+        if (total >= maxit) break;
+    }
+    if (check_cuda(c, cudaStreamSynchronize(c->stream), "gmres end")) return HZB_ECUDA;
+    double worst = 0.0;
+    bool bad = false;
+    for (int r = 0; r < R; ++r) {
+        if (!std::isfinite(hres[r])) bad = true;
+        worst = std::max(worst, hres[r]);
+    }
+    *iters = total;
+    *relres = worst;
+    *converged = all_done && worst <= tol && !bad;
+    if (bad) return fail(c, HZB_ENAN, "non-finite residual in GMRES");
+    return HZB_OK;
+}
+
+// max_r ||b - A x|| / ||b|| with the FP64 operator; r_out (N x R) receives b - A x
+static hzb_status true_residual(hzb_ctx *c, int R, const double2 *b, const double2 *x, double2 *r_out,
+                                std::vector<double> &rel)
+{
+    const size_t NR = (size_t)c->N * R;
+    hzb_status st;
+    if ((st = apply_op(c, R, x, r_out, HZB_PREC_FP64))) return st;
+    axpby_kernel<<<nblocks((long long)NR), 256, 0, c->stream>>>((long long)NR, 1.0, b, -1.0, r_out, r_out);
+    DevBuf<double2> &tmp = c->tiny;
+    if (check_cuda(c, tmp.ensure(2 * (size_t)R), "alloc")) return HZB_ENOMEM;
+    if ((st = cdots(c, R, 1, r_out, 0, r_out, tmp.ptr)) || (st = cdots(c, R, 1, b, 0, b, tmp.ptr + R))) return st;
+    std::vector<double2> h(2 * R);
+    cudaMemcpyAsync(h.data(), tmp.ptr, 2 * R * sizeof(double2), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (check_cuda(c, e, "residual")) return HZB_ECUDA;
+    rel.assign(R, 0.0);
+    for (int r = 0; r < R; ++r) rel[r] = h[R + r].x > 0 ? std::sqrt(std::max(h[r].x, 0.0) / h[R + r].x) : 0.0;
+    return HZB_OK;
+}
+
+hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *stats)
+{
+    const size_t NR = (size_t)c->N * R;
+    hzb_status st;
+    DevBuf<double2> &bbuf = c->s_b, &rbuf = c->s_r, &dbuf = c->s_d;
+    auto cleanup = [&]() {};
+    if (check_cuda(c, c->sol.ensure(NR), "alloc densities") || check_cuda(c, bbuf.ensure(NR), "alloc rhs")) {
+        cleanup();
+        return HZB_ENOMEM;
+    }
+    c->sol_R = R;
+    long long calls0 = c->interbody_calls;
+    cudaEventRecord(c->ev0, c->stream);
+    // b = -D^{-1} v
+    if ((st = local_inverse64(c, R, v, nullptr, 0.0, -1.0, bbuf.ptr))) { cleanup(); return st; }
+    double2 *x = c->sol.ptr;
+    int it = 0, conv = 0, outer = 0;
+    double rr = 0.0;
+    hzb_status solve_status = HZB_OK;
+    if (x0) {
+        if ((st = vec_copy(c, x, x0, NR))) { cleanup(); return st; }
+    }
+    if (c->opt.precision == HZB_PREC_FP64) {
+        st = gmres_solve(c, R, bbuf.ptr, x, x0 ? 0 : 1, HZB_PREC_FP64, c->opt.gmres_tol, c->opt.maxit,
+                         c->opt.restart, &it, &rr, &conv);
+        if (st) { cleanup(); return st; }
+        outer = 1;
+        if (!conv) solve_status = HZB_ENOCONV;
+    } else {
+        if (check_cuda(c, rbuf.ensure(NR), "alloc") || check_cuda(c, dbuf.ensure(NR), "alloc")) {
+            cleanup();
+            return HZB_ENOMEM;
+        }
+        std::vector<double> rel(R, 1.0);
+        if (x0) {
+            if ((st = true_residual(c, R, bbuf.ptr, x, rbuf.ptr, rel))) { cleanup(); return st; }
+        } else {
+            if ((st = vec_zero(c, x, NR)) || (st = vec_copy(c, rbuf.ptr, bbuf.ptr, NR))) { cleanup(); return st; }
+        }
+        double worst = *std::max_element(rel.begin(), rel.end());
+        conv = worst <= c->opt.gmres_tol;
+        while (!conv && outer < c->opt.max_outer && it < c->opt.maxit) {
+            double tin = std::max(c->opt.inner_tol, 0.3 * c->opt.gmres_tol / std::max(worst, 1e-300));
+            tin = std::min(tin, 0.5);
+            int iin = 0, cin = 0;
+            double rin = 0.0;
+            st = gmres_solve(c, R, rbuf.ptr, dbuf.ptr, 1, HZB_PREC_MIXED_FP32, tin, c->opt.maxit - it,
+                             c->opt.restart, &iin, &rin, &cin);
+            if (st && st != HZB_ENOCONV) { cleanup(); return st; }
+            it += iin;
+            axpby_kernel<<<nblocks((long long)NR), 256, 0, c->stream>>>((long long)NR, 1.0, x, 1.0, dbuf.ptr, x);
+            if ((st = true_residual(c, R, bbuf.ptr, x, rbuf.ptr, rel))) { cleanup(); return st; }
+            ++outer;
+            double nw = *std::max_element(rel.begin(), rel.end());
+            if (!std::isfinite(nw)) { cleanup(); return fail(c, HZB_ENAN, "non-finite refinement residual"); }
+            worst = nw;
+            conv = worst <= c->opt.gmres_tol;
+        }
+        rr = worst;
+        if (!conv) solve_status = HZB_ENOCONV;
+    }
+    cudaEventRecord(c->ev1, c->stream);
+    if (check_cuda(c, cudaEventSynchronize(c->ev1), "solve")) { cleanup(); return HZB_ECUDA; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    if (stats) {
+        stats->iterations = it;
+        stats->outer_iterations = outer;
+        stats->converged = conv;
+        stats->rel_residual = rr;
+        stats->t_solve_ms = ms;
+        stats->t_setup_ms = c->t_setup_ms;
+        stats->interbody_applies = c->interbody_calls - calls0;
+    }
+    cleanup();
+    if (solve_status == HZB_ENOCONV) return fail(c, HZB_ENOCONV, "GMRES did not reach the tolerance");
+    return HZB_OK;
+}
+
+}  // namespace hzb

@@ -1,0 +1,97 @@
+"""GPU parity of the hot-path operators: inter-body sum B (Sec. 3.3), block-diagonal
+inverse D^{-1} (Remark after Eq. (precond)) and the preconditioned apply, in FP64
+and FP32, against the oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._common import gpu_solver, oracle_problem, rand_c, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_pair():
+    sph = W.ShapeSpec(W.SPHEROID, (1.0, 2.0), 5, 7, 11)
+    shell = W.ShapeSpec(W.OPEN_SHELL, (1.0, 0.8, np.pi / 3, 0.1), 9, 6, 9)
+    ball = W.ShapeSpec(W.SPHERE, (0.7,), 3, 5, 7)
+    bodies = [W.Body(sph, np.array([-2.0, 0.2, 0.0]), W.rotation_taking_z_to([0.3, 1.0, 0.2])),
+              W.Body(shell, np.array([1.7, -0.1, 0.3]), W.rotation_taking_z_to([-1.0, 0.2, 0.4])),
+              W.Body(ball, np.array([0.1, 2.4, -0.5]), np.eye(3)),
+              W.Body(sph, np.array([0.0, -2.6, 1.0]), W.rotation_taking_z_to([0.0, 0.0, -1.0]))]
+    return W.Workload("mixed4", bodies, 3.0, 3.0, np.array([[0, 0, 1.0]]))
+
+
+CASES = {"two_spheres_tiny": lambda: W.tiny_two_spheres(), "mixed4": _mixed_pair}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def pair(request):
+    require_gpu()
+    from oracle import Problem
+    wl = CASES[request.param]()
+    return gpu_solver(wl), Problem(wl)
+
+
+@pytest.mark.parametrize("R", [1, 3, 9])
+def test_interbody_fp64(pair, R):
+    s, P = pair
+    sig = rand_c((P.N, R), 11 + R)
+    got = s.interbody(sig)
+    ref = P.interbody(sig)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("R", [1, 5])
+def test_interbody_fp32(pair, R):
+    s, P = pair
+    sig = rand_c((P.N, R), 21 + R)
+    got = s.interbody(sig, precision=1)
+    ref = P.interbody(sig)
+    assert rel_l2(got, ref) < 2e-6
+
+
+@pytest.mark.parametrize("R", [1, 4])
+def test_local_inverse(pair, R):
+    s, P = pair
+    y = rand_c((P.N, R), 31 + R)
+    sig = rand_c((P.N, R), 41 + R)
+    ref = 0.5 * sig - 2.0 * P.local_inverse(y)
+    got = s.local_inverse(y, sig, alpha=0.5, beta=-2.0)
+    assert rel_l2(got, ref) < 1e-11
+    got32 = s.local_inverse(y, sig, alpha=0.5, beta=-2.0, precision=1)
+    assert rel_l2(got32, ref) < 1e-5
+
+
+def test_apply_fp64(pair):
+    s, P = pair
+    sig = rand_c((P.N, 2), 51)
+    assert rel_l2(s.apply(sig), P.apply(sig)) < 1e-11
+
+
+def test_device_tensors_round_trip(pair):
+    import torch
+    s, P = pair
+    sig = rand_c((P.N, 2), 61)
+    t = torch.from_numpy(sig).cuda()
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    out = s.apply(t)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), P.apply(sig)) < 1e-11
+
+
+def test_spheroids_258560_sampled_rows():
+    """Full-size eight-spheroid workload in the benchmark's launch configuration:
+    B sigma on 96 seeded target rows (FP64 and FP32) against the oracle's rows."""
+    require_gpu()
+    from oracle import Problem
+    wl = W.spheroids8()
+    s = gpu_solver(wl)
+    P = Problem(wl)
+    assert s.N == 258560 == P.N
+    sig = rand_c((P.N, 1), 71)
+    rows = np.sort(np.random.default_rng(72).choice(P.N, 96, replace=False)).astype(np.int32)
+    ref = P.interbody(sig, targets=rows)
+    y64 = s.interbody(sig)
+    y32 = s.interbody(sig, precision=1)
+    assert np.abs(y64[rows] - ref).max() < 1e-11 * np.abs(ref).max()
+    assert rel_l2(y32[rows], ref) < 1e-5

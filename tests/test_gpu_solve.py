@@ -1,0 +1,155 @@
+"""GPU solves (Sec. 4 GMRES on Eq. (precond)) against the oracle and physics:
+FP64 path <= 1e-10 and mixed path <= 1e-7 relative l2 in density and far field;
+Green's identity (Sec. 6 accuracy protocol); Mie series; multi-RHS batches; the
+stored oracle far field; error statuses of the C ABI."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._common import gpu_solver, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "two_spheres_8200_farfield.txt")
+
+
+@pytest.fixture(scope="module")
+def two_spheres_ref():
+    """Oracle reference of the two-sphere 8,200-unknown workload (GMRES to 1e-13)."""
+    require_gpu()
+    from oracle import Problem, fields, gmres
+    wl = W.two_spheres()
+    P = Problem(wl)
+    v = fields.plane_wave(P.nodes.x, wl.directions, wl.k)[:, 0]
+    res = gmres(P.apply, P.rhs(v), 1e-13)
+    assert res.converged
+    return wl, P, res.x
+
+
+def test_fp64_solve_matches_oracle(two_spheres_ref):
+    from oracle import fields
+    wl, P, sig_ref = two_spheres_ref
+    s = gpu_solver(wl, precision=0, tol=1e-12)
+    st = s.solve_plane_waves(wl.directions)
+    assert st.converged and st.rel_residual <= 1e-12
+    sig = s.get_density()[:, 0]
+    assert rel_l2(sig, sig_ref) <= 1e-10
+    xh = W.uniform_directions(12, 5)
+    ff = s.far_field(xh)[:, 0]
+    assert rel_l2(ff, fields.far_field(P.nodes, sig_ref, wl.k, wl.eta, xh)) <= 1e-10
+    gold = np.loadtxt(GOLDEN)
+    ffg = s.far_field(gold[:, :3])[:, 0]
+    assert rel_l2(ffg, gold[:, 3] + 1j * gold[:, 4]) <= 1e-10
+
+
+def test_mixed_solve_matches_oracle(two_spheres_ref):
+    from oracle import fields
+    wl, P, sig_ref = two_spheres_ref
+    s = gpu_solver(wl, precision=1, tol=1e-9)
+    st = s.solve_plane_waves(wl.directions)
+    assert st.converged and st.outer_iterations >= 1
+    sig = s.get_density()[:, 0]
+    assert rel_l2(sig, sig_ref) <= 1e-7
+    xh = W.uniform_directions(12, 6)
+    assert rel_l2(s.far_field(xh)[:, 0], fields.far_field(P.nodes, sig_ref, wl.k, wl.eta, xh)) <= 1e-7
+
+
+def test_green_identity_on_device():
+    require_gpu()
+    from oracle import fields
+    wl = W.two_spheres()
+    s = gpu_solver(wl, tol=1e-12)
+    x, _, _ = s.get_nodes()
+    src = W.point_sources(wl, 5)
+    tg = W.exterior_targets(wl, 10, 6)
+    v = -fields.point_source_field(x, src, wl.k)
+    st = s.solve_data(v)
+    assert st.converged
+    u = s.eval_field(tg)[:, 0]
+    ue = fields.point_source_field(tg, src, wl.k)
+    assert np.abs(u - ue).max() / np.abs(ue).max() < 1e-10
+
+
+def test_mie_single_sphere_on_device():
+    require_gpu()
+    from oracle import fields
+    sh = W.ShapeSpec(W.SPHERE, (1.0,), 8, 10, 25)
+    wl = W.Workload("sphere", [W.Body(sh, np.zeros(3), np.eye(3))], 2.0, 2.0, np.array([[0, 0, 1.0]]))
+    s = gpu_solver(wl, tol=1e-12)
+    s.solve_plane_waves(wl.directions)
+    xh = W.uniform_directions(16, 3)
+    mie = fields.mie_far_field(1.0, 2.0, xh[:, 2])
+    assert np.abs(s.far_field(xh)[:, 0] - mie).max() < 1e-11 * np.abs(mie).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_rhs_equal_single_solves(precision):
+    require_gpu()
+    wl = W.two_spheres(n_panels=6, gl_order=8, n_modes=21)
+    dirs = W.uniform_directions(5, 9)
+    s = gpu_solver(wl, precision=precision, tol=1e-11)
+    st = s.solve_plane_waves(dirs)
+    assert st.converged
+    batch = s.get_density()
+    for r in (0, 3):
+        s1 = gpu_solver(wl, precision=precision, tol=1e-11)
+        s1.solve_plane_waves(dirs[r:r + 1])
+        assert rel_l2(batch[:, r], s1.get_density()[:, 0]) < (1e-10 if precision == 0 else 1e-8)
+
+
+def test_restarted_gmres_and_initial_guess():
+    require_gpu()
+    wl = W.two_spheres(n_panels=6, gl_order=8, n_modes=21)
+    s = gpu_solver(wl, tol=1e-12)
+    s.solve_plane_waves(wl.directions)
+    ref = s.get_density()
+    s2 = gpu_solver(wl, tol=1e-12, restart=3, maxit=300)
+    st = s2.solve_plane_waves(wl.directions)
+    assert st.converged
+    assert rel_l2(s2.get_density(), ref) < 1e-10
+    x, _, _ = s.get_nodes()
+    from oracle import fields
+    v = fields.plane_wave(x, wl.directions, wl.k)
+    st3 = s.solve_data(v, x0=ref)          # exact start: converges at once
+    assert st3.converged and st3.iterations <= 1
+
+
+def test_error_statuses():
+    require_gpu()
+    from paper_1406_0236_gb300 import HzbError, Solver
+    s = Solver(2.0, 2.0)
+    with pytest.raises(HzbError) as e:
+        s.add_body(W.SPHERE, (1.0,), 4, 6, 8, np.zeros(3), np.eye(3))     # even N_F
+    assert e.value.status == -1
+    with pytest.raises(HzbError) as e:
+        s.build_scattering_matrices()                                      # no bodies
+    assert e.value.status == -7
+    with pytest.raises(HzbError) as e:
+        s.add_body(W.SPHERE, (1.0,), 4, 6, 9, np.zeros(3), 2 * np.eye(3))   # not a rotation
+    assert e.value.status == -1
+    s.add_body(W.SPHERE, (1.0,), 4, 6, 9, np.zeros(3), np.eye(3))
+    with pytest.raises(HzbError) as e:
+        s.solve_plane_waves([[0, 0, 1.0]])                                 # not built
+    assert e.value.status == -7
+    s.build_scattering_matrices()
+    with pytest.raises(HzbError) as e:
+        s.solve_plane_waves([[0, 0, 2.0]])                                 # not a unit vector
+    assert e.value.status == -1
+    with pytest.raises(HzbError) as e:
+        s.far_field([[0, 0, 1.0]])                                         # no solve yet
+    assert e.value.status == -7
+    st = s.solve_plane_waves([[0, 0, 1.0]])
+    assert st.converged
+
+
+def test_nonconvergence_is_reported():
+    require_gpu()
+    from paper_1406_0236_gb300 import HzbError
+    wl = W.two_spheres(n_panels=6, gl_order=8, n_modes=21)
+    s = gpu_solver(wl, tol=1e-14, maxit=2)
+    with pytest.raises(HzbError) as e:
+        s.solve_plane_waves(wl.directions)
+    assert e.value.status == -4
+    st = s.solve_plane_waves(wl.directions, allow_noconv=True)
+    assert not st.converged and st.iterations == 2
