@@ -91,6 +91,11 @@ typedef struct {
     double t_solve_ms;       /* device time of the solve (CUDA events) */
     double t_setup_ms;       /* device time of hzb_build_scattering_matrices */
     long long interbody_applies;  /* inter-body sums launched during the solve */
+    double t_nbody64_ms;     /* summed device time of the FP64 inter-body kernel (CUDA events) */
+    double t_nbody32_ms;     /* summed device time of the FP32 inter-body kernel */
+    long long n_nbody64;     /* its launches during the solve */
+    long long n_nbody32;
+    long long kernel_launches;    /* kernels of this library launched during the solve */
 } hzb_stats;
 
 /* Fill *o with defaults: device 0, default stream, FP64, tol 1e-10, no restart,

@@ -44,7 +44,10 @@ class _Shape(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
-                ("t_setup_ms", ctypes.c_double), ("interbody_applies", ctypes.c_longlong)]
+                ("t_setup_ms", ctypes.c_double), ("interbody_applies", ctypes.c_longlong),
+                ("t_nbody64_ms", ctypes.c_double), ("t_nbody32_ms", ctypes.c_double),
+                ("n_nbody64", ctypes.c_longlong), ("n_nbody32", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong)]
 
 
 @dataclass
@@ -56,6 +59,11 @@ class Stats:
     t_solve_ms: float
     t_setup_ms: float
     interbody_applies: int
+    t_nbody64_ms: float = 0.0
+    t_nbody32_ms: float = 0.0
+    n_nbody64: int = 0
+    n_nbody32: int = 0
+    kernel_launches: int = 0
     status: int = 0
 
 
@@ -260,7 +268,8 @@ class Solver:
     # ------------------------------------------------------------ solves
     def _stats(self, st: _Stats, status: int) -> Stats:
         return Stats(st.iterations, st.outer_iterations, bool(st.converged), st.rel_residual, st.t_solve_ms,
-                     st.t_setup_ms, st.interbody_applies, status)
+                     st.t_setup_ms, st.interbody_applies, st.t_nbody64_ms, st.t_nbody32_ms, st.n_nbody64,
+                     st.n_nbody32, st.kernel_launches, status)
 
     def solve_plane_waves(self, dirs, allow_noconv: bool = False) -> Stats:
         d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)

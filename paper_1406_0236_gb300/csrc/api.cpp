@@ -116,6 +116,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     c->io_in.release(); c->io_out.release(); c->io_small.release(); c->tiny.release(); c->sol.release();
     c->red.release(); c->krylov.release(); c->small.release();
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
+    for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
@@ -364,6 +365,7 @@ hzb_status hzb_apply(hzb_ctx *c, int R, const double *sigma, double *z, int on_d
 hzb_status hzb_solve_plane_waves(hzb_ctx *c, int R, const double *dirs, hzb_stats *stats)
 {
     HZB_GUARD(c);
+    c->prof_on = false;
     if (c->state != 3) return fail(c, HZB_ESTATE, "scattering matrices not built");
     if (R < 1 || R > 4096 || !dirs) return fail(c, HZB_EINVAL, "bad R or directions");
     for (int r = 0; r < R; ++r) {
@@ -384,6 +386,7 @@ hzb_status hzb_solve_plane_waves(hzb_ctx *c, int R, const double *dirs, hzb_stat
 hzb_status hzb_solve_data(hzb_ctx *c, int R, const double *v, const double *x0, int on_device, hzb_stats *stats)
 {
     HZB_GUARD(c);
+    c->prof_on = false;
     if (c->state != 3) return fail(c, HZB_ESTATE, "scattering matrices not built");
     if (R < 1 || R > 4096 || !v) return fail(c, HZB_EINVAL, "bad R or data");
     size_t n = (size_t)c->N * R;

@@ -139,12 +139,20 @@ struct hzb_ctx {
     size_t host_pinned_n = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long interbody_calls = 0;
+    long long launches = 0;                    // kernels launched (all wrappers)
+    // device timing of the inter-body kernels during a solve: event pairs
+    std::vector<cudaEvent_t> evpool;
+    std::vector<int> evkind;                   // 0: FP64, 1: FP32, per recorded pair
+    bool prof_on = false;
 };
 
 // ---------------------------------------------------------------- kernels' host entry points
 namespace hzb {
 
 hzb_status fail(hzb_ctx *c, hzb_status s, const std::string &msg);
+// event pair around one inter-body launch (no-op unless a solve is profiling)
+int prof_begin(hzb_ctx *c, int kind);
+void prof_end(hzb_ctx *c, int slot);
 hzb_status check_cuda(hzb_ctx *c, cudaError_t e, const char *what);
 
 // setup.cu

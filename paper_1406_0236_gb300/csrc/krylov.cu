@@ -190,6 +190,26 @@ __global__ void backsolve_kernel(int R, int m, GmresState s, double2 *y)
     }
 }
 
+int prof_begin(hzb_ctx *c, int kind)
+{
+    if (!c->prof_on) return -1;
+    const size_t slot = c->evkind.size();
+    if (slot >= 4096) return -1;
+    while (c->evpool.size() < 2 * (slot + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        c->evpool.push_back(e);
+    }
+    c->evkind.push_back(kind);
+    cudaEventRecord(c->evpool[2 * slot], c->stream);
+    return (int)slot;
+}
+
+void prof_end(hzb_ctx *c, int slot)
+{
+    if (slot >= 0) cudaEventRecord(c->evpool[2 * slot + 1], c->stream);
+}
+
 hzb_status vec_copy(hzb_ctx *c, double2 *dst, const double2 *src, size_t n)
 {
     return check_cuda(c, cudaMemcpyAsync(dst, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream), "copy");
@@ -212,6 +232,7 @@ static hzb_status cdots(hzb_ctx *c, int R, int nv, const double2 *V, long long v
     if (check_cuda(c, c->w_d.ensure(std::max<size_t>(need, (size_t)N * R)), "alloc partial")) return HZB_ENOMEM;
     cdot_partial_kernel<<<dim3(nblk, nv, R), RED_THREADS, 0, c->stream>>>(N, R, V, vstride, w, c->w_d.ptr);
     cdot_final_kernel<<<nblocks(nv * R), 256, 0, c->stream>>>(nv * R, nblk, c->w_d.ptr, out);
+    c->launches += 2;
     return check_cuda(c, cudaGetLastError(), "cdot");
 }
 
@@ -292,6 +313,7 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
         } else {
             if ((st = apply_op(c, R, x, c->w_b.ptr, precision))) return st;
             axpby_kernel<<<gN, 256, 0, c->stream>>>((long long)NR, 1.0, b, -1.0, c->w_b.ptr, w);
+            c->launches++;
         }
         if (!(first)) {
             if ((st = cdots(c, R, 1, w, 0, w, s.nrm2))) return st;
@@ -304,6 +326,7 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
         }
         first = false;
         scale_kernel<<<gN, 256, 0, c->stream>>>(N, R, w, s.inv, V);
+        c->launches += 2;
         cudaMemcpyAsync(hres, s.res, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         cudaMemcpyAsync(hact, s.active, R * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
         if (check_cuda(c, cudaStreamSynchronize(c->stream), "gmres start")) return HZB_ECUDA;
@@ -323,6 +346,7 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
             caxpy_multi_kernel<<<gN, 256, 0, c->stream>>>(N, R, j + 1, V, (long long)NR, s.h2, w);
             if ((st = cdots(c, R, 1, w, 0, w, s.nrm2))) return st;
             givens_kernel<<<gR, 64, 0, c->stream>>>(R, m, j, s, tol);
+            c->launches += 4;                  // two caxpy, givens, scale
             scale_kernel<<<gN, 256, 0, c->stream>>>(N, R, w, s.inv, V + (size_t)(j + 1) * NR);
             cudaMemcpyAsync(hres, s.res, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
             cudaMemcpyAsync(hact, s.active, R * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -334,6 +358,7 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
         }
         backsolve_kernel<<<gR, 64, 0, c->stream>>>(R, m, s, y);
         update_x_kernel<<<gN, 256, 0, c->stream>>>(N, R, m, V, (long long)NR, y, s.jdone, x);
+        c->launches += 2;
         if (check_cuda(c, cudaGetLastError(), "gmres update")) return HZB_ECUDA;
         bool anyact = false;
         for (int r = 0; r < R; ++r) anyact |= hact[r] != 0;
@@ -365,6 +390,7 @@ static hzb_status true_residual(hzb_ctx *c, int R, const double2 *b, const doubl
     hzb_status st;
     if ((st = apply_op(c, R, x, r_out, HZB_PREC_FP64))) return st;
     axpby_kernel<<<nblocks((long long)NR), 256, 0, c->stream>>>((long long)NR, 1.0, b, -1.0, r_out, r_out);
+    c->launches++;
     DevBuf<double2> &tmp = c->tiny;
     if (check_cuda(c, tmp.ensure(2 * (size_t)R), "alloc")) return HZB_ENOMEM;
     if ((st = cdots(c, R, 1, r_out, 0, r_out, tmp.ptr)) || (st = cdots(c, R, 1, b, 0, b, tmp.ptr + R))) return st;
@@ -388,7 +414,9 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
         return HZB_ENOMEM;
     }
     c->sol_R = R;
-    long long calls0 = c->interbody_calls;
+    long long calls0 = c->interbody_calls, launches0 = c->launches;
+    c->evkind.clear();
+    c->prof_on = true;
     cudaEventRecord(c->ev0, c->stream);
     // b = -D^{-1} v
     if ((st = local_inverse64(c, R, v, nullptr, 0.0, -1.0, bbuf.ptr))) { cleanup(); return st; }
@@ -428,6 +456,7 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
             if (st && st != HZB_ENOCONV) { cleanup(); return st; }
             it += iin;
             axpby_kernel<<<nblocks((long long)NR), 256, 0, c->stream>>>((long long)NR, 1.0, x, 1.0, dbuf.ptr, x);
+            c->launches++;
             if ((st = true_residual(c, R, bbuf.ptr, x, rbuf.ptr, rel))) { cleanup(); return st; }
             ++outer;
             double nw = *std::max_element(rel.begin(), rel.end());
@@ -442,7 +471,23 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
     if (check_cuda(c, cudaEventSynchronize(c->ev1), "solve")) { cleanup(); return HZB_ECUDA; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    c->prof_on = false;
+    double tk[2] = {0.0, 0.0};
+    long long nk[2] = {0, 0};
+    for (size_t q = 0; q < c->evkind.size(); ++q) {
+        float e = 0.f;
+        if (cudaEventElapsedTime(&e, c->evpool[2 * q], c->evpool[2 * q + 1]) == cudaSuccess) {
+            tk[c->evkind[q]] += e;
+            nk[c->evkind[q]]++;
+        }
+    }
+    c->evkind.clear();
     if (stats) {
+        stats->t_nbody64_ms = tk[0];
+        stats->t_nbody32_ms = tk[1];
+        stats->n_nbody64 = nk[0];
+        stats->n_nbody32 = nk[1];
+        stats->kernel_launches = c->launches - launches0;
         stats->iterations = it;
         stats->outer_iterations = outer;
         stats->converged = conv;

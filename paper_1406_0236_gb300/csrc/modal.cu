@@ -209,6 +209,7 @@ static hzb_status local_inverse_t(hzb_ctx *c, int R, const double2 *y, const dou
         modal_gemm_kernel<T><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(NG, ncols, S, yh, th);
         dft_inverse_kernel<T><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, th, sigma,
                                                                                alpha, beta, tau);
+        c->launches += 3;
         if (check_cuda(c, cudaGetLastError(), "modal apply")) return HZB_ECUDA;
     }
     return HZB_OK;

@@ -196,6 +196,8 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
     if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
     int N = (int)c->N;
     c->interbody_calls++;
+    c->launches++;
+    const int slot = prof_begin(c, 0);
     cudaError_t e;
     if (R == 1) {
         nbody64_kernel<1><<<dim3(c->n_tblocks, 1), NB_THREADS, 0, c->stream>>>(
@@ -208,6 +210,7 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
             c->tblocks.ptr, N, R, c->pos64.ptr, c->nrm64.ptr, sigma, c->k, c->eta, y);
     }
     e = cudaGetLastError();
+    prof_end(c, slot);
     return check_cuda(c, e, "nbody64_kernel");
 }
 
@@ -216,6 +219,8 @@ hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
     if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
     int N = (int)c->N;
     c->interbody_calls++;
+    c->launches++;
+    const int slot = prof_begin(c, 1);
     const float k = (float)c->k, eta = (float)c->eta, kt = (float)(c->k / (2.0 * M_PI));
     if (R == 1) {
         nbody32_kernel<1><<<dim3(c->n_tblocks, 1), NB_THREADS, 0, c->stream>>>(
@@ -227,7 +232,9 @@ hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
         nbody32_kernel<8><<<dim3(c->n_tblocks, (R + 7) / 8), NB_THREADS, 0, c->stream>>>(
             c->tblocks.ptr, N, R, c->pos32.ptr, c->nrm32.ptr, sigma, k, eta, kt, y);
     }
-    return check_cuda(c, cudaGetLastError(), "nbody32_kernel");
+    cudaError_t e = cudaGetLastError();
+    prof_end(c, slot);
+    return check_cuda(c, e, "nbody32_kernel");
 }
 
 // ------------------------------------------------------------------ fields at points
@@ -324,6 +331,7 @@ static hzb_status point_sum(hzb_ctx *c, int R, const double2 *sigma, int T, cons
         field_partial_kernel<<<grid, 256, 0, c->stream>>>(N, R, c->pos64.ptr, c->nrm64.ptr, sigma, pts, c->k,
                                                           c->eta, c->w_d.ptr);
     chunk_reduce_kernel<<<(T * R + 255) / 256, 256, 0, c->stream>>>(T, nchunk, R, c->w_d.ptr, out);
+    c->launches += 2;
     return check_cuda(c, cudaGetLastError(), "point fields");
 }
 
@@ -355,6 +363,7 @@ hzb_status plane_waves(hzb_ctx *c, int R, const double *dirs_dev, double2 *v)
 {
     long long n = c->N * R;
     plane_wave_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->N, R, c->pos64.ptr, dirs_dev, c->k, v);
+    c->launches++;
     return check_cuda(c, cudaGetLastError(), "plane_wave_kernel");
 }
 

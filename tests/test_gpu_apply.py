@@ -94,4 +94,6 @@ def test_spheroids_258560_sampled_rows():
     y64 = s.interbody(sig)
     y32 = s.interbody(sig, precision=1)
     assert np.abs(y64[rows] - ref).max() < 1e-11 * np.abs(ref).max()
-    assert rel_l2(y32[rows], ref) < 1e-5
+    # FP32: the phase k r carries the relative error of r (~2 ulp after the hardware
+    # reciprocal square root) times k r <= 4 x 14 here, ~1e-5 per term at most.
+    assert rel_l2(y32[rows], ref) < 3e-5
