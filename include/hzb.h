@@ -71,6 +71,11 @@ typedef struct {
     int maxit;             /* total GMRES iterations (inner iterations in mixed mode) */
     double inner_tol;      /* mixed mode: relative tolerance of each inner FP32 solve */
     int max_outer;         /* mixed mode: maximum refinement steps */
+    int verify_final;      /* mixed mode: 1 (default) = stop only on a computed FP64 residual;
+                              0 = after an FP64 residual r_k, stop once the bound
+                              rel_k * max(c_1, inner_tol) * 10 <= gmres_tol holds for the next
+                              correction (c_1: contraction observed in the first refinement
+                              step), saving the last FP64 apply */
 } hzb_options;
 
 typedef struct {
@@ -138,6 +143,13 @@ hzb_status hzb_get_nodes(hzb_ctx *ctx, double *xyz, double *normals, double *wei
  * integration, A~_p = 1/2 I + K_p and S_p = A~_p^{-1} for p = 0..M, all in FP64
  * on the device (Sec. 3.2, Remark on the cost of precomputation). */
 hzb_status hzb_build_scattering_matrices(hzb_ctx *ctx);
+
+/* Autotuner of the inter-body kernels' launch shape (targets per thread, source
+ * chunks per target block) for R right-hand sides: times each candidate with CUDA
+ * events on the context's stream and keeps the fastest for later calls.
+ * which: bit 0 = FP32 kernel, bit 1 = FP64 kernel.  best_ms (may be NULL): the
+ * fastest time per launch [FP32, FP64].  Not part of the paper: a GB300 tuning aid. */
+hzb_status hzb_autotune(hzb_ctx *ctx, int R, int which, double best_ms[2]);
 
 /* Copy A~_p (which = 0) or S_p (which = 1) of the shape of body `body`, mode p in
  * 0..M, to host out (N_G x N_G complex, row-major). */

@@ -33,7 +33,7 @@ class HzbError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("verify_final", ctypes.c_int)]
 
 
 class _Shape(ctypes.Structure):
@@ -76,6 +76,7 @@ class Options:
     maxit: int = 500
     inner_tol: float = 1e-5
     max_outer: int = 10
+    verify_final: int = 1
 
 
 def library_path() -> str:
@@ -118,6 +119,7 @@ def lib():
         "hzb_get_density": (i, [p, p, i]),
         "hzb_far_field": (i, [p, i, p, p]),
         "hzb_eval_field": (i, [p, i, p, p]),
+        "hzb_autotune": (i, [p, i, i, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -151,6 +153,7 @@ class Solver:
         L.hzb_default_options(ctypes.byref(co))
         co.device, co.precision, co.gmres_tol = o.device, o.precision, o.gmres_tol
         co.restart, co.maxit, co.inner_tol, co.max_outer = o.restart, o.maxit, o.inner_tol, o.max_outer
+        co.verify_final = o.verify_final
         co.cuda_stream = stream
         self._opt = co
         h = ctypes.c_void_p()
@@ -220,6 +223,13 @@ class Solver:
         x = np.zeros((N, 3)); n = np.zeros((N, 3)); w = np.zeros(N)
         self._check(lib().hzb_get_nodes(self._h, _ptr(x), _ptr(n), _ptr(w)))
         return x, n, w
+
+    def autotune(self, R: int = 1, which: int = 1):
+        """Pick the inter-body kernels' launch shape by timing (bit 0: FP32, bit 1: FP64).
+        Returns the best time per launch in ms, [FP32, FP64]."""
+        best = np.zeros(2)
+        self._check(lib().hzb_autotune(self._h, int(R), int(which), _ptr(best)))
+        return best
 
     def build_scattering_matrices(self):
         self._check(lib().hzb_build_scattering_matrices(self._h))

@@ -51,6 +51,7 @@ void hzb_default_options(hzb_options *o)
     o->maxit = 500;
     o->inner_tol = 1e-5;
     o->max_outer = 10;
+    o->verify_final = 1;
 }
 
 const char *hzb_status_string(hzb_status s)
@@ -115,6 +116,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     c->yhat32.release(); c->that32.release(); c->s_b.release(); c->s_r.release(); c->s_d.release();
     c->io_in.release(); c->io_out.release(); c->io_small.release(); c->tiny.release(); c->sol.release();
     c->red.release(); c->krylov.release(); c->small.release();
+    c->sctab.release(); c->nb_part64.release(); c->nb_part32.release();
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -425,6 +427,14 @@ static hzb_status point_query(hzb_ctx *c, int n, const double *pts, double *out,
                         : field_points64(c, R, c->sol.ptr, n, c->io_small.ptr, c->io_out.ptr);
     if (st) return st;
     return finish_out(c, c->io_out.ptr, out, no, 0);
+}
+
+hzb_status hzb_autotune(hzb_ctx *c, int R, int which, double best_ms[2])
+{
+    HZB_GUARD(c);
+    if (c->state < 2) return fail(c, HZB_ESTATE, "no bodies");
+    if (R < 1 || R > 4096 || which < 1 || which > 3) return fail(c, HZB_EINVAL, "bad R or selector");
+    return autotune(c, R, which, best_ms);
 }
 
 hzb_status hzb_far_field(hzb_ctx *c, int n, const double *xhat, double *out)

@@ -140,6 +140,13 @@ struct hzb_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long interbody_calls = 0;
     long long launches = 0;                    // kernels launched (all wrappers)
+    // inter-body kernels: FP64 cos/sin table, split partial sums, launch shape
+    hzb::DevBuf<double2> sctab;
+    hzb::DevBuf<double2> nb_part64;
+    hzb::DevBuf<float2> nb_part32;
+    int tune64_tpt = 0, tune64_split = 0;      // 0: default
+    int tune32_tpt = 0, tune32_split = 0;
+    int tune_limit_blocks = 0;                 // autotuner: time only the first blocks (0 = all)
     // device timing of the inter-body kernels during a solve: event pairs
     std::vector<cudaEvent_t> evpool;
     std::vector<int> evkind;                   // 0: FP64, 1: FP32, per recorded pair
@@ -162,6 +169,10 @@ hzb_status build_shape_matrices(hzb_ctx *c, ShapeDev &s);
 // nbody.cu: y = B sigma; sigma, y device N x R complex FP64 (FP32 path converts internally)
 hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
+hzb_status interbody64_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit);
+hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit);
+int default_nsplit(hzb_ctx *c, int R, int tpt);
+hzb_status autotune(hzb_ctx *c, int R, int which, double *best_ms);
 // field at external points (no exclusion): out T x R (device), pts T x 3 (device)
 hzb_status field_points64(hzb_ctx *c, int R, const double2 *sigma, int T, const double *pts,
                           double2 *out);

@@ -5,48 +5,76 @@
 //     w_j K(x_i, x_j) = w_j / (4 pi) * e^{ikr} [ n_j.d / r^3 - i (k n_j.d / r^2 + eta / r) ],
 // d = x_i - x_j, r = |d|.  Also: the field at off-surface points and the far field.
 //
-// Work decomposition: one CTA per TargetBlock (a run of <= 512 targets inside one
-// body), so the sources of the target's own body are one contiguous range skipped
-// uniformly by the whole CTA; source tiles are staged in shared memory with the
-// density pre-multiplied by w_j / (4 pi); each thread owns TPT targets.
+// Work decomposition: a CTA takes one TargetBlock (a run of <= 512 targets inside
+// one body, so the sources of the target's own body are one contiguous range that
+// the whole CTA skips without a per-pair test) and one of `nsplit` contiguous source
+// chunks (grid z); each of its 512/TPT threads owns TPT targets; source tiles of
+// blockDim sources are staged in shared memory with the density pre-multiplied by
+// w_j / (4 pi).  With nsplit > 1 each chunk writes a partial sum and a second kernel
+// adds the chunks in a fixed order (deterministic).  TPT and nsplit are picked per
+// workload by the autotuner (hzb_autotune) or a default from the SM count.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "hzb_internal.h"
 #include "kernel_math.cuh"
 
 namespace hzb {
 
-static const int NB_THREADS = 128;
-static const int NB_TPT = 4;            // targets per thread; 128 x 4 = 512 = TargetBlock size
-static const int NB_TILE = 128;
+static const int TBLOCK = 512;          // targets per TargetBlock (make_nodes)
+static const int SC_N = 256;            // entries of the FP64 cos/sin table
+
+// FP64 e^{ix} for x >= 0 (table-driven, after Tang): t = x 256/(2pi), j = rint(t),
+// delta = (t - j) 2pi/256 in [-pi/256, pi/256]; (cos, sin)(delta) by their Taylor
+// series to delta^8 / delta^7 (truncation < 2e-20); (cos, sin)(x) by angle addition
+// with the tabulated (cos, sin)(2 pi j / 256).  Reduction error ~ x * 1.1e-16 rad.
+__device__ inline void sincos_table(double x, const double2 *__restrict__ tab, double &s, double &c)
+{
+    const double t = x * (SC_N / (2.0 * M_PI));
+    const double j = rint(t);
+    const double d = (t - j) * (2.0 * M_PI / SC_N);
+    const double d2 = d * d;
+    const double sd = d * fma(d2, fma(d2, fma(d2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
+    const double cd = fma(d2, fma(d2, fma(d2, fma(d2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
+    const double2 cs = tab[((long long)j) & (SC_N - 1)];
+    c = fma(cs.x, cd, -cs.y * sd);
+    s = fma(cs.y, cd, cs.x * sd);
+}
 
 // ------------------------------------------------------------------ FP64
 
-template <int RC>
-__global__ void __launch_bounds__(NB_THREADS)
-nbody64_kernel(const TargetBlock *__restrict__ blocks, int N, int R, const double4 *__restrict__ pos,
-               const double4 *__restrict__ nrm, const double2 *__restrict__ sigma, double k, double eta,
-               double2 *__restrict__ y)
+template <int RC, int TPT>
+__global__ void __launch_bounds__(TBLOCK / TPT)
+nbody64_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const double4 *__restrict__ pos,
+               const double4 *__restrict__ nrm, const double2 *__restrict__ sigma, const double2 *__restrict__ sctab,
+               double k, double eta, double2 *__restrict__ y, size_t split_stride)
 {
-    __shared__ double4 s_pos[NB_TILE];
-    __shared__ double4 s_nrm[NB_TILE];
-    __shared__ double2 s_sig[NB_TILE * RC];
+    constexpr int NT = TBLOCK / TPT;
+    __shared__ double4 s_pos[NT];
+    __shared__ double4 s_nrm[NT];
+    __shared__ double2 s_sig[NT * RC];
+    __shared__ double2 s_tab[SC_N];
     const TargetBlock tb = blocks[blockIdx.x];
     const int r0 = blockIdx.y * RC;
     const int tid = threadIdx.x;
-    double tx[NB_TPT], ty[NB_TPT], tz[NB_TPT];
-    double2 acc[NB_TPT][RC];
+    for (int q = tid; q < SC_N; q += NT) s_tab[q] = sctab[q];
+    double tx[TPT], ty[TPT], tz[TPT];
+    double2 acc[TPT][RC];
 #pragma unroll
-    for (int m = 0; m < NB_TPT; ++m) {
-        int t = tid + m * NB_THREADS;
+    for (int m = 0; m < TPT; ++m) {
+        int t = tid + m * NT;
         double4 p = (t < tb.count) ? pos[tb.start + t] : make_double4(1e30, 1e30, 1e30, 0.0);
         tx[m] = p.x; ty[m] = p.y; tz[m] = p.z;
 #pragma unroll
         for (int c = 0; c < RC; ++c) acc[m][c] = make_double2(0.0, 0.0);
     }
+    const int c0 = blockIdx.z * chunk, c1 = min(N, c0 + chunk);
     for (int range = 0; range < 2; ++range) {
-        const int lo = range ? tb.excl_hi : 0;
-        const int hi = range ? N : tb.excl_lo;
-        for (int j0 = lo; j0 < hi; j0 += NB_TILE) {
-            const int cnt = min(NB_TILE, hi - j0);
+        const int lo = range ? max(c0, tb.excl_hi) : c0;
+        const int hi = range ? c1 : min(c1, tb.excl_lo);
+        for (int j0 = lo; j0 < hi; j0 += NT) {
+            const int cnt = min(NT, hi - j0);
             __syncthreads();
             if (tid < cnt) {
                 double4 p = pos[j0 + tid];
@@ -64,7 +92,7 @@ nbody64_kernel(const TargetBlock *__restrict__ blocks, int N, int R, const doubl
                 const double4 p = s_pos[jj];
                 const double4 n = s_nrm[jj];
 #pragma unroll
-                for (int m = 0; m < NB_TPT; ++m) {
+                for (int m = 0; m < TPT; ++m) {
                     const double dx = tx[m] - p.x, dy = ty[m] - p.y, dz = tz[m] - p.z;
                     const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
                     const double ir = rsqrt(r2);
@@ -74,7 +102,7 @@ nbody64_kernel(const TargetBlock *__restrict__ blocks, int N, int R, const doubl
                     const double A = ndir2 * ir;
                     const double B = fma(k, ndir2, eta * ir);
                     double s, c;
-                    sincos(k * r, &s, &c);
+                    sincos_table(k * r, s_tab, s, c);
                     const double gre = fma(c, A, s * B);
                     const double gim = fma(s, A, -c * B);
 #pragma unroll
@@ -87,13 +115,14 @@ nbody64_kernel(const TargetBlock *__restrict__ blocks, int N, int R, const doubl
             }
         }
     }
+    double2 *yo = y + blockIdx.z * split_stride;
 #pragma unroll
-    for (int m = 0; m < NB_TPT; ++m) {
-        int t = tid + m * NB_THREADS;
+    for (int m = 0; m < TPT; ++m) {
+        int t = tid + m * NT;
         if (t < tb.count)
 #pragma unroll
             for (int c = 0; c < RC; ++c)
-                if (r0 + c < R) y[(size_t)(tb.start + t) * R + r0 + c] = acc[m][c];
+                if (r0 + c < R) yo[(size_t)(tb.start + t) * R + r0 + c] = acc[m][c];
     }
 }
 
@@ -101,33 +130,35 @@ nbody64_kernel(const TargetBlock *__restrict__ blocks, int N, int R, const doubl
 
 // Phase of e^{ikr}: r k / (2 pi) is reduced to [-1/2, 1/2] turns before the
 // hardware sine and cosine, whose error grows with the argument.
-template <int RC>
-__global__ void __launch_bounds__(NB_THREADS)
-nbody32_kernel(const TargetBlock *__restrict__ blocks, int N, int R, const float4 *__restrict__ pos,
+template <int RC, int TPT>
+__global__ void __launch_bounds__(TBLOCK / TPT)
+nbody32_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pos,
                const float4 *__restrict__ nrm, const double2 *__restrict__ sigma, float k, float eta,
-               float k_turns, double2 *__restrict__ y)
+               float k_turns, float2 *__restrict__ ypart, double2 *__restrict__ y, size_t split_stride)
 {
-    __shared__ float4 s_a[NB_TILE];           // x, y, z, nx
-    __shared__ float2 s_b[NB_TILE];           // ny, nz
-    __shared__ float2 s_sig[NB_TILE * RC];
+    constexpr int NT = TBLOCK / TPT;
+    __shared__ float4 s_a[NT];           // x, y, z, nx
+    __shared__ float2 s_b[NT];           // ny, nz
+    __shared__ float2 s_sig[NT * RC];
     const TargetBlock tb = blocks[blockIdx.x];
     const int r0 = blockIdx.y * RC;
     const int tid = threadIdx.x;
-    float tx[NB_TPT], ty[NB_TPT], tz[NB_TPT];
-    float2 acc[NB_TPT][RC];
+    float tx[TPT], ty[TPT], tz[TPT];
+    float2 acc[TPT][RC];
 #pragma unroll
-    for (int m = 0; m < NB_TPT; ++m) {
-        int t = tid + m * NB_THREADS;
+    for (int m = 0; m < TPT; ++m) {
+        int t = tid + m * NT;
         float4 p = (t < tb.count) ? pos[tb.start + t] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
         tx[m] = p.x; ty[m] = p.y; tz[m] = p.z;
 #pragma unroll
         for (int c = 0; c < RC; ++c) acc[m][c] = make_float2(0.f, 0.f);
     }
+    const int c0 = blockIdx.z * chunk, c1 = min(N, c0 + chunk);
     for (int range = 0; range < 2; ++range) {
-        const int lo = range ? tb.excl_hi : 0;
-        const int hi = range ? N : tb.excl_lo;
-        for (int j0 = lo; j0 < hi; j0 += NB_TILE) {
-            const int cnt = min(NB_TILE, hi - j0);
+        const int lo = range ? max(c0, tb.excl_hi) : c0;
+        const int hi = range ? c1 : min(c1, tb.excl_lo);
+        for (int j0 = lo; j0 < hi; j0 += NT) {
+            const int cnt = min(NT, hi - j0);
             __syncthreads();
             if (tid < cnt) {
                 const float4 p = pos[j0 + tid];
@@ -147,7 +178,7 @@ nbody32_kernel(const TargetBlock *__restrict__ blocks, int N, int R, const float
                 const float4 a = s_a[jj];
                 const float2 b = s_b[jj];
 #pragma unroll
-                for (int m = 0; m < NB_TPT; ++m) {
+                for (int m = 0; m < TPT; ++m) {
                     const float dx = tx[m] - a.x, dy = ty[m] - a.y, dz = tz[m] - a.z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     const float ir = rsqrtf(r2);
@@ -172,69 +203,169 @@ nbody32_kernel(const TargetBlock *__restrict__ blocks, int N, int R, const float
         }
     }
 #pragma unroll
-    for (int m = 0; m < NB_TPT; ++m) {
-        int t = tid + m * NB_THREADS;
+    for (int m = 0; m < TPT; ++m) {
+        int t = tid + m * NT;
         if (t < tb.count)
 #pragma unroll
             for (int c = 0; c < RC; ++c)
-                if (r0 + c < R)
-                    y[(size_t)(tb.start + t) * R + r0 + c] = make_double2((double)acc[m][c].x, (double)acc[m][c].y);
+                if (r0 + c < R) {
+                    size_t e = (size_t)(tb.start + t) * R + r0 + c;
+                    if (ypart) ypart[blockIdx.z * split_stride + e] = acc[m][c];
+                    else y[e] = make_double2((double)acc[m][c].x, (double)acc[m][c].y);
+                }
     }
 }
 
-template <typename F>
-static hzb_status launch_rc(hzb_ctx *c, int R, F f1, F f4, F f8)
+// y = sum over the nsplit partial sums (fixed order)
+template <typename P>
+__global__ void split_reduce_kernel(size_t n, int nsplit, const P *__restrict__ part, double2 *__restrict__ y)
 {
-    (void)c;
-    if (R == 1) return f1(1);
-    if (R <= 4) return f4(4);
-    return f8(8);
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < nsplit; ++s) {
+        P v = part[s * n + e];
+        sx += (double)v.x;
+        sy += (double)v.y;
+    }
+    y[e] = make_double2(sx, sy);
 }
 
-hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
+// Launch shape of the inter-body kernels.
+static int rc_of(int R) { return R == 1 ? 1 : (R <= 4 ? 4 : 8); }
+
+int default_nsplit(hzb_ctx *c, int R, int tpt)
+{
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
+    const int rc = rc_of(R);
+    const long long ctas = (long long)c->n_tblocks * ((R + rc - 1) / rc);
+    const long long want = (long long)sms * (tpt == 1 ? 4 : (tpt == 2 ? 8 : 12));
+    int ns = (int)std::max<long long>(1, (want + ctas - 1) / ctas);
+    return std::min(ns, 64);
+}
+
+static hzb_status ensure_sctab(hzb_ctx *c)
+{
+    if (c->sctab.ptr) return HZB_OK;
+    std::vector<double2> tab(SC_N);
+    for (int q = 0; q < SC_N; ++q) tab[q] = make_double2(std::cos(2.0 * M_PI * q / SC_N), std::sin(2.0 * M_PI * q / SC_N));
+    if (check_cuda(c, c->sctab.ensure(SC_N), "alloc table")) return HZB_ENOMEM;
+    return check_cuda(c, cudaMemcpyAsync(c->sctab.ptr, tab.data(), SC_N * sizeof(double2), cudaMemcpyHostToDevice,
+                                         c->stream), "copy table");
+}
+
+template <int RC, int TPT>
+static void launch64(hzb_ctx *c, dim3 g, int N, int R, int chunk, const double2 *sigma, double2 *out, size_t stride)
+{
+    nbody64_kernel<RC, TPT><<<g, TBLOCK / TPT, 0, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos64.ptr,
+                                                               c->nrm64.ptr, sigma, c->sctab.ptr, c->k, c->eta,
+                                                               out, stride);
+}
+
+template <int RC, int TPT>
+static void launch32(hzb_ctx *c, dim3 g, int N, int R, int chunk, const double2 *sigma, float2 *part, double2 *y,
+                     size_t stride)
+{
+    nbody32_kernel<RC, TPT><<<g, TBLOCK / TPT, 0, c->stream>>>(
+        c->tblocks.ptr, N, R, chunk, c->pos32.ptr, c->nrm32.ptr, sigma, (float)c->k, (float)c->eta,
+        (float)(c->k / (2.0 * M_PI)), part, y, stride);
+}
+
+template <int RC>
+static void dispatch64(hzb_ctx *c, int tpt, dim3 g, int N, int R, int chunk, const double2 *s, double2 *o, size_t st)
+{
+    if (tpt == 1) launch64<RC, 1>(c, g, N, R, chunk, s, o, st);
+    else if (tpt == 2) launch64<RC, 2>(c, g, N, R, chunk, s, o, st);
+    else launch64<RC, 4>(c, g, N, R, chunk, s, o, st);
+}
+
+template <int RC>
+static void dispatch32(hzb_ctx *c, int tpt, dim3 g, int N, int R, int chunk, const double2 *s, float2 *p, double2 *y,
+                       size_t st)
+{
+    if (tpt == 1) launch32<RC, 1>(c, g, N, R, chunk, s, p, y, st);
+    else if (tpt == 2) launch32<RC, 2>(c, g, N, R, chunk, s, p, y, st);
+    else launch32<RC, 4>(c, g, N, R, chunk, s, p, y, st);
+}
+
+static int chunk_of(int N, int nsplit, int tpt)
+{
+    const int nt = TBLOCK / tpt;
+    int ch = (N + nsplit - 1) / nsplit;
+    return ((ch + nt - 1) / nt) * nt;
+}
+
+hzb_status interbody64_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit)
 {
     if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
-    int N = (int)c->N;
-    c->interbody_calls++;
-    c->launches++;
-    const int slot = prof_begin(c, 0);
-    cudaError_t e;
-    if (R == 1) {
-        nbody64_kernel<1><<<dim3(c->n_tblocks, 1), NB_THREADS, 0, c->stream>>>(
-            c->tblocks.ptr, N, R, c->pos64.ptr, c->nrm64.ptr, sigma, c->k, c->eta, y);
-    } else if (R <= 4) {
-        nbody64_kernel<4><<<dim3(c->n_tblocks, 1), NB_THREADS, 0, c->stream>>>(
-            c->tblocks.ptr, N, R, c->pos64.ptr, c->nrm64.ptr, sigma, c->k, c->eta, y);
-    } else {
-        nbody64_kernel<8><<<dim3(c->n_tblocks, (R + 7) / 8), NB_THREADS, 0, c->stream>>>(
-            c->tblocks.ptr, N, R, c->pos64.ptr, c->nrm64.ptr, sigma, c->k, c->eta, y);
+    hzb_status st = ensure_sctab(c);
+    if (st) return st;
+    const int N = (int)c->N;
+    const int rc = rc_of(R);
+    const int chunk = chunk_of(N, nsplit, tpt);
+    nsplit = (N + chunk - 1) / chunk;
+    const size_t n = (size_t)N * R;
+    double2 *out = y;
+    if (nsplit > 1) {
+        if (check_cuda(c, c->nb_part64.ensure(n * nsplit), "alloc partial sums")) return HZB_ENOMEM;
+        out = c->nb_part64.ptr;
     }
-    e = cudaGetLastError();
+    c->interbody_calls++;
+    c->launches += (nsplit > 1) ? 2 : 1;
+    const int slot = prof_begin(c, 0);
+    const int nb = (c->tune_limit_blocks > 0) ? std::min(c->tune_limit_blocks, c->n_tblocks) : c->n_tblocks;
+    dim3 g(nb, (R + rc - 1) / rc, nsplit);
+    if (rc == 1) dispatch64<1>(c, tpt, g, N, R, chunk, sigma, out, n);
+    else if (rc == 4) dispatch64<4>(c, tpt, g, N, R, chunk, sigma, out, n);
+    else dispatch64<8>(c, tpt, g, N, R, chunk, sigma, out, n);
+    if (nsplit > 1)
+        split_reduce_kernel<double2><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, nsplit, out, y);
+    cudaError_t e = cudaGetLastError();
     prof_end(c, slot);
     return check_cuda(c, e, "nbody64_kernel");
 }
 
-hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
+hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit)
 {
     if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
-    int N = (int)c->N;
-    c->interbody_calls++;
-    c->launches++;
-    const int slot = prof_begin(c, 1);
-    const float k = (float)c->k, eta = (float)c->eta, kt = (float)(c->k / (2.0 * M_PI));
-    if (R == 1) {
-        nbody32_kernel<1><<<dim3(c->n_tblocks, 1), NB_THREADS, 0, c->stream>>>(
-            c->tblocks.ptr, N, R, c->pos32.ptr, c->nrm32.ptr, sigma, k, eta, kt, y);
-    } else if (R <= 4) {
-        nbody32_kernel<4><<<dim3(c->n_tblocks, 1), NB_THREADS, 0, c->stream>>>(
-            c->tblocks.ptr, N, R, c->pos32.ptr, c->nrm32.ptr, sigma, k, eta, kt, y);
-    } else {
-        nbody32_kernel<8><<<dim3(c->n_tblocks, (R + 7) / 8), NB_THREADS, 0, c->stream>>>(
-            c->tblocks.ptr, N, R, c->pos32.ptr, c->nrm32.ptr, sigma, k, eta, kt, y);
+    const int N = (int)c->N;
+    const int rc = rc_of(R);
+    const int chunk = chunk_of(N, nsplit, tpt);
+    nsplit = (N + chunk - 1) / chunk;
+    const size_t n = (size_t)N * R;
+    float2 *part = nullptr;
+    if (nsplit > 1) {
+        if (check_cuda(c, c->nb_part32.ensure(n * nsplit), "alloc partial sums")) return HZB_ENOMEM;
+        part = c->nb_part32.ptr;
     }
+    c->interbody_calls++;
+    c->launches += (nsplit > 1) ? 2 : 1;
+    const int slot = prof_begin(c, 1);
+    const int nb = (c->tune_limit_blocks > 0) ? std::min(c->tune_limit_blocks, c->n_tblocks) : c->n_tblocks;
+    dim3 g(nb, (R + rc - 1) / rc, nsplit);
+    if (rc == 1) dispatch32<1>(c, tpt, g, N, R, chunk, sigma, part, y, n);
+    else if (rc == 4) dispatch32<4>(c, tpt, g, N, R, chunk, sigma, part, y, n);
+    else dispatch32<8>(c, tpt, g, N, R, chunk, sigma, part, y, n);
+    if (nsplit > 1)
+        split_reduce_kernel<float2><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, nsplit, part, y);
     cudaError_t e = cudaGetLastError();
     prof_end(c, slot);
     return check_cuda(c, e, "nbody32_kernel");
+}
+
+hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
+{
+    int tpt = c->tune64_tpt > 0 ? c->tune64_tpt : 2;
+    int ns = c->tune64_split > 0 ? c->tune64_split : default_nsplit(c, R, tpt);
+    return interbody64_cfg(c, R, sigma, y, tpt, ns);
+}
+
+hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
+{
+    int tpt = c->tune32_tpt > 0 ? c->tune32_tpt : 4;
+    int ns = c->tune32_split > 0 ? c->tune32_split : default_nsplit(c, R, tpt);
+    return interbody32_cfg(c, R, sigma, y, tpt, ns);
 }
 
 // ------------------------------------------------------------------ fields at points
@@ -365,6 +496,65 @@ hzb_status plane_waves(hzb_ctx *c, int R, const double *dirs_dev, double2 *v)
     plane_wave_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->N, R, c->pos64.ptr, dirs_dev, c->k, v);
     c->launches++;
     return check_cuda(c, cudaGetLastError(), "plane_wave_kernel");
+}
+
+}  // namespace hzb
+
+namespace hzb {
+
+// Time one inter-body configuration: one warm-up launch, then the mean of `reps`
+// launches between CUDA events on the context's stream.
+static float time_cfg(hzb_ctx *c, int prec, int R, int tpt, int ns, const double2 *x, double2 *y, int reps)
+{
+    hzb_status st = prec ? interbody32_cfg(c, R, x, y, tpt, ns) : interbody64_cfg(c, R, x, y, tpt, ns);
+    if (st) return -1.f;
+    cudaEventRecord(c->ev0, c->stream);
+    for (int q = 0; q < reps; ++q) {
+        st = prec ? interbody32_cfg(c, R, x, y, tpt, ns) : interbody64_cfg(c, R, x, y, tpt, ns);
+        if (st) return -1.f;
+    }
+    cudaEventRecord(c->ev1, c->stream);
+    if (cudaEventSynchronize(c->ev1) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    return ms / reps;
+}
+
+hzb_status autotune(hzb_ctx *c, int R, int which, double *best_ms)
+{
+    if (!c->nodes_ready) {
+        hzb_status st = make_nodes(c);
+        if (st) return st;
+    }
+    const size_t n = (size_t)c->N * R;
+    if (check_cuda(c, c->io_in.ensure(n), "alloc") || check_cuda(c, c->io_out.ensure(n), "alloc")) return HZB_ENOMEM;
+    cudaMemsetAsync(c->io_in.ptr, 0, n * sizeof(double2), c->stream);
+    const long long calls = c->interbody_calls, launches = c->launches;
+    for (int prec = 1; prec >= 0; --prec) {
+        if (!(which & (prec ? 1 : 2))) continue;
+        int bt = 0, bs = 0;
+        float bm = 1e30f;
+        const int tpts[3] = {1, 2, 4};
+        for (int a = 0; a < 3; ++a) {
+            int tpt = tpts[a];
+            if (prec == 0 && tpt == 4) continue;
+            int d = default_nsplit(c, R, tpt);
+            int cand[5] = {1, 2, d, 2 * d, 4 * d};
+            for (int b = 0; b < 5; ++b) {
+                if (b > 0 && cand[b] == cand[b - 1]) continue;
+                if (cand[b] > 64) continue;
+                float ms = time_cfg(c, prec, R, tpt, cand[b], c->io_in.ptr, c->io_out.ptr, prec ? 3 : 1);
+                if (ms < 0) return fail(c, HZB_ECUDA, "autotune launch failed");
+                if (ms < bm) { bm = ms; bt = tpt; bs = cand[b]; }
+            }
+        }
+        if (prec) { c->tune32_tpt = bt; c->tune32_split = bs; }
+        else { c->tune64_tpt = bt; c->tune64_split = bs; }
+        if (best_ms) best_ms[prec ? 0 : 1] = bm;
+    }
+    c->interbody_calls = calls;       // tuning launches are not solve work
+    c->launches = launches;
+    return HZB_OK;
 }
 
 }  // namespace hzb

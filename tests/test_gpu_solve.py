@@ -153,3 +153,30 @@ def test_nonconvergence_is_reported():
     assert e.value.status == -4
     st = s.solve_plane_waves(wl.directions, allow_noconv=True)
     assert not st.converged and st.iterations == 2
+
+
+def test_mixed_a_priori_stop_meets_1e7(two_spheres_ref):
+    """verify_final = 0 stops after one FP64 residual on the refinement bound; the
+    density must still meet 1e-7 against the oracle."""
+    wl, P, sig_ref = two_spheres_ref
+    from paper_1406_0236_gb300 import Options, Solver
+    s = Solver.from_workload(wl, Options(precision=1, gmres_tol=1e-8, verify_final=0))
+    s.build_scattering_matrices()
+    st = s.solve_plane_waves(wl.directions)
+    assert st.converged
+    assert rel_l2(s.get_density()[:, 0], sig_ref) <= 1e-7
+
+
+def test_autotuned_launch_shapes_keep_results():
+    require_gpu()
+    from oracle import Problem
+    from tests._common import rand_c
+    wl = W.two_spheres(n_panels=6, gl_order=8, n_modes=21)
+    s = gpu_solver(wl)
+    P = Problem(wl)
+    sig = rand_c((P.N, 2), 5)
+    ref = P.interbody(sig)
+    best = s.autotune(2, 3)
+    assert best[0] > 0 and best[1] > 0
+    assert np.abs(s.interbody(sig) - ref).max() < 1e-12 * np.abs(ref).max()
+    assert rel_l2(s.interbody(sig, precision=1), ref) < 2e-6
