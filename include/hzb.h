@@ -192,6 +192,39 @@ hzb_status hzb_far_field(hzb_ctx *ctx, int n, const double *xhat, double *out);
  * n x 3), smooth rule (Eq. (intHelm1)); out: n x R complex (host). */
 hzb_status hzb_eval_field(hzb_ctx *ctx, int n, const double *x, double *out);
 
+/* ------------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper; it only seeds GMRES through the
+ * x0 of hzb_solve_data, and the zero-guess solve remains the fallback).
+ * A multilayer perceptron: n_in inputs -> depth hidden layers of `width` units with
+ * GELU(a) = a Phi(a) -> n_out linear outputs.  Parameters are stored layer by layer
+ * as W (n_out_l x n_in_l, row-major) then b (n_out_l), FP32 masters with a BF16
+ * copy used by the forward and backward products; activations and accumulations
+ * are FP32.  Loss: (1/B) sum over the batch and outputs of (y - t)^2.  Optimiser:
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  Batches: B x n_in
+ * inputs and B x n_out targets, row-major FP32, host or device (flag).
+ * ------------------------------------------------------------------------------ */
+typedef struct hzb_mlp hzb_mlp;
+
+/* Create on `device` launching on `stream` (NULL = default stream); weights drawn
+ * uniformly in +-1/sqrt(fan_in) from a splitmix64 stream seeded by `seed`, biases 0. */
+hzb_status hzb_mlp_create(int device, void *stream, int n_in, int width, int depth, int n_out,
+                          unsigned long long seed, hzb_mlp **out);
+hzb_status hzb_mlp_destroy(hzb_mlp *m);
+const char *hzb_mlp_last_error(const hzb_mlp *m);
+hzb_status hzb_mlp_num_params(const hzb_mlp *m, long long *n);
+/* FP32 master parameters to / from host memory (set also refreshes the BF16 copy). */
+hzb_status hzb_mlp_get_params(hzb_mlp *m, float *out);
+hzb_status hzb_mlp_set_params(hzb_mlp *m, const float *in);
+/* y = network(x) for a batch of B rows. */
+hzb_status hzb_mlp_forward(hzb_mlp *m, int B, const float *x, float *y, int on_device);
+/* Loss (host float) and the gradient of every parameter (same layout as the
+ * parameters; host or device per the flag; either output may be NULL). */
+hzb_status hzb_mlp_gradients(hzb_mlp *m, int B, const float *x, const float *t, float *loss,
+                             float *grads, int on_device);
+/* One Adam step on the batch; *loss (may be NULL) receives the loss before the step. */
+hzb_status hzb_mlp_train_step(hzb_mlp *m, int B, const float *x, const float *t, float lr,
+                              float *loss, int on_device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ each body (Sec. 3.2), block-diagonal preconditioner with per-mode scattering
 matrices and GMRES (Sec. 4).
 """
 from .binding import (HZB_PREC_FP64, HZB_PREC_MIXED_FP32, HZB_OPEN_SHELL, HZB_SPHERE, HZB_SPHEROID,
-                      HzbError, Options, Solver, Stats, lib, library_path)
+                      HzbError, Mlp, Options, Solver, Stats, lib, library_path)
 
 __all__ = ["HZB_PREC_FP64", "HZB_PREC_MIXED_FP32", "HZB_SPHERE", "HZB_SPHEROID", "HZB_OPEN_SHELL",
-           "HzbError", "Options", "Solver", "Stats", "lib", "library_path"]
+           "HzbError", "Mlp", "Options", "Solver", "Stats", "lib", "library_path"]

@@ -322,3 +322,106 @@ class Solver:
         out = np.zeros((x.shape[0], getattr(self, "_R", 1)), dtype=np.complex128)
         self._check(lib().hzb_eval_field(self._h, int(x.shape[0]), _ptr(x), _ptr(out)))
         return out
+
+
+class Mlp:
+    """The warm-start network of the C ABI (hzb_mlp_*): BF16 weights, FP32 activations
+    and accumulation, Adam.  Batches are float32 arrays (numpy host or torch CUDA)."""
+
+    def __init__(self, n_in: int, width: int, depth: int, n_out: int, seed: int = 1, device: int = 0,
+                 stream=None):
+        L = lib()
+        self._sig()
+        h = ctypes.c_void_p()
+        rc = L.hzb_mlp_create(int(device), stream, int(n_in), int(width), int(depth), int(n_out),
+                              ctypes.c_ulonglong(seed), ctypes.byref(h))
+        if rc != 0:
+            raise HzbError(rc, "hzb_mlp_create")
+        self._h = h
+        self.n_in, self.width, self.depth, self.n_out = n_in, width, depth, n_out
+
+    @staticmethod
+    def _sig():
+        L = lib()
+        i, p, f = ctypes.c_int, ctypes.c_void_p, ctypes.c_float
+        for name, res, args in (
+                ("hzb_mlp_create", i, [i, p, i, i, i, i, ctypes.c_ulonglong, ctypes.POINTER(p)]),
+                ("hzb_mlp_destroy", i, [p]),
+                ("hzb_mlp_last_error", ctypes.c_char_p, [p]),
+                ("hzb_mlp_num_params", i, [p, ctypes.POINTER(ctypes.c_longlong)]),
+                ("hzb_mlp_get_params", i, [p, p]),
+                ("hzb_mlp_set_params", i, [p, p]),
+                ("hzb_mlp_forward", i, [p, i, p, p, i]),
+                ("hzb_mlp_gradients", i, [p, i, p, p, ctypes.POINTER(f), p, i]),
+                ("hzb_mlp_train_step", i, [p, i, p, p, f, ctypes.POINTER(f), i])):
+            fn = getattr(L, name)
+            fn.restype, fn.argtypes = res, args
+
+    def _check(self, rc):
+        if rc != 0:
+            raise HzbError(rc, lib().hzb_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hzb_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        n = ctypes.c_longlong()
+        self._check(lib().hzb_mlp_num_params(self._h, ctypes.byref(n)))
+        return n.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.num_params, dtype=np.float32)
+        self._check(lib().hzb_mlp_get_params(self._h, _ptr(out)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(lib().hzb_mlp_set_params(self._h, _ptr(p)))
+
+    def layers(self, flat: np.ndarray):
+        """Split a flat parameter vector into [(W, b)] per layer."""
+        out, off = [], 0
+        dims = [self.n_in] + [self.width] * self.depth + [self.n_out]
+        for i, o in zip(dims[:-1], dims[1:]):
+            W = flat[off:off + i * o].reshape(o, i); off += i * o
+            b = flat[off:off + o]; off += o
+            out.append((W, b))
+        return out
+
+    def forward(self, x):
+        dev = _is_dev(x)
+        if dev:
+            y = x.new_empty((x.shape[0], self.n_out))
+        else:
+            x = np.ascontiguousarray(x, dtype=np.float32)
+            y = np.zeros((x.shape[0], self.n_out), dtype=np.float32)
+        self._check(lib().hzb_mlp_forward(self._h, int(x.shape[0]), _ptr(x), _ptr(y), int(dev)))
+        return y
+
+    def gradients(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(self.num_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        self._check(lib().hzb_mlp_gradients(self._h, int(x.shape[0]), _ptr(x), _ptr(t), ctypes.byref(loss),
+                                            _ptr(g), 0))
+        return float(loss.value), g
+
+    def train_step(self, x, t, lr: float) -> float:
+        dev = _is_dev(x)
+        if not dev:
+            x = np.ascontiguousarray(x, dtype=np.float32)
+            t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = ctypes.c_float()
+        self._check(lib().hzb_mlp_train_step(self._h, int(x.shape[0]), _ptr(x), _ptr(t), float(lr),
+                                             ctypes.byref(loss), int(dev)))
+        return float(loss.value)

@@ -1,0 +1,154 @@
+"""Learned warm start for GMRES: incident direction -> density, through a POD basis.
+
+1. Training densities: the library solves the plane-wave problems of the training
+   directions (batched right-hand sides, FP64 accuracy via mixed refinement).
+2. POD basis: the leading left singular vectors of the N x T snapshot matrix
+   (library SVD of torch; an offline step, not part of any solve).
+3. Network: hzb_mlp (BF16 weights, FP32 accumulation, hand-written CUDA kernels)
+   maps the direction (3 numbers) to the n_pod complex POD coefficients (2 n_pod
+   real outputs, scaled to unit RMS), trained with Adam on the MSE loss.
+4. Guess: x0 = U c(d), passed to hzb_solve_data; the zero-guess solve is the
+   fallback (a guess never changes the converged answer, only the iterations).
+
+Run the full protocol (two unit spheres, 8,200 unknowns; 4,096 training and 512
+held-out directions; 4 hidden layers of 512, 256 POD modes):
+
+    python -m paper_1406_0236_gb300.warm_start
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+class WarmStart:
+    def __init__(self, solver, n_pod: int = 256, width: int = 512, depth: int = 4, seed: int = 1):
+        import torch
+
+        from .binding import Mlp
+        self.torch = torch
+        self.s = solver
+        self.n_pod, self.width, self.depth = n_pod, width, depth
+        self.mlp = Mlp(3, width, depth, 2 * n_pod, seed=seed, stream=torch.cuda.current_stream().cuda_stream)
+        self.U = None
+        self.scale = 1.0
+        self.losses = []
+
+    # -------------------------------------------------------------- data
+    def training_densities(self, dirs: np.ndarray, batch: int = 64):
+        """Densities (N x T complex128, device) of the plane waves `dirs` (T x 3)."""
+        torch = self.torch
+        N = self.s.N
+        X = torch.empty((N, dirs.shape[0]), dtype=torch.complex128, device="cuda")
+        for a in range(0, dirs.shape[0], batch):
+            d = dirs[a:a + batch]
+            self.s.solve_plane_waves(d)
+            out = torch.empty((N, d.shape[0]), dtype=torch.complex128, device="cuda")
+            self.s.get_density(out)
+            X[:, a:a + d.shape[0]] = out
+        return X
+
+    def fit(self, dirs: np.ndarray, X=None, epochs: int = 400, batch: int = 256, lr: float = 1e-3,
+            lr_final: float = 2e-5):
+        torch = self.torch
+        if X is None:
+            X = self.training_densities(dirs)
+        U, _, _ = torch.linalg.svd(X, full_matrices=False)
+        self.U = U[:, :self.n_pod].contiguous()
+        C = self.U.conj().T @ X                                         # n_pod x T coefficients
+        T = torch.stack([C.real, C.imag], dim=-1).reshape(self.n_pod * 2, -1).T.contiguous()  # T x 2n_pod
+        self.scale = float(T.pow(2).mean().sqrt())
+        Tn = (T / self.scale).float().contiguous()
+        D = torch.from_numpy(np.ascontiguousarray(dirs, dtype=np.float32)).cuda()
+        n = D.shape[0]
+        g = torch.Generator(device="cuda").manual_seed(11)
+        steps = epochs * max(1, n // batch)
+        q = 0
+        for ep in range(epochs):
+            perm = torch.randperm(n, device="cuda", generator=g)
+            for a in range(0, n - batch + 1, batch):
+                idx = perm[a:a + batch]
+                rate = lr * (lr_final / lr) ** (q / max(steps - 1, 1))      # geometric decay
+                loss = self.mlp.train_step(D[idx].contiguous(), Tn[idx].contiguous(), rate)
+                q += 1
+            self.losses.append(loss)
+        return self
+
+    def guess(self, dirs: np.ndarray):
+        """x0 = U c(d) for directions (R x 3): N x R complex128 device tensor."""
+        torch = self.torch
+        D = torch.from_numpy(np.ascontiguousarray(dirs, dtype=np.float32)).cuda()
+        y = self.mlp.forward(D).double() * self.scale                   # R x 2n_pod
+        c = torch.complex(y[:, 0::2], y[:, 1::2]).T                       # n_pod x R
+        return (self.U @ c).contiguous()
+
+
+def plane_wave_data(x_nodes, dirs, k):
+    """v = exp(i k d . x) at the nodes (N x R complex128, device)."""
+    import torch
+    X = torch.from_numpy(np.ascontiguousarray(x_nodes)).cuda()
+    D = torch.from_numpy(np.ascontiguousarray(dirs, dtype=np.float64)).cuda()
+    return torch.exp(1j * k * (X @ D.T)).contiguous()
+
+
+def iterations_with_and_without(s, ws: WarmStart, dirs, k, tol: float):
+    """Per-direction GMRES iterations to the relative residual tol, zero guess vs warm start."""
+    x, _, _ = s.get_nodes()
+    it0, it1 = [], []
+    for r in range(dirs.shape[0]):
+        v = plane_wave_data(x, dirs[r:r + 1], k)
+        st0 = s.solve_data(v)
+        x0 = ws.guess(dirs[r:r + 1])
+        st1 = s.solve_data(v, x0=x0)
+        it0.append(st0.iterations)
+        it1.append(st1.iterations)
+    return np.array(it0), np.array(it1)
+
+
+def main():
+    import torch
+
+    import workloads as W
+    from .binding import Options, Solver
+
+    wl = W.two_spheres()
+    s = Solver.from_workload(wl, Options(precision=1, gmres_tol=1e-11, verify_final=1),
+                             stream=torch.cuda.current_stream().cuda_stream)
+    s.build_scattering_matrices()
+    train = W.uniform_directions(4096, 20140602)
+    held = W.uniform_directions(512, 20140603)
+    t0 = time.time()
+    ws = WarmStart(s)
+    X = ws.training_densities(train)
+    t_data = time.time() - t0
+    t0 = time.time()
+    ws.fit(train, X)
+    torch.cuda.synchronize()
+    t_fit = time.time() - t0
+    # iterations to 1e-7 on the held-out directions: FP64 path, zero guess vs warm start
+    s.set_options(precision=0, gmres_tol=1e-7)
+    it0, it1 = iterations_with_and_without(s, ws, held, wl.k, 1e-7)
+    # density error of the bare guess
+    Xh = ws.training_densities(held)
+    G = ws.guess(held)
+    gerr = (torch.linalg.vector_norm(G - Xh, dim=0) / torch.linalg.vector_norm(Xh, dim=0)).cpu().numpy()
+    print(json.dumps({
+        "workload": "two_spheres_8200", "train": 4096, "held_out": 512, "pod_modes": ws.n_pod,
+        "mlp": "3 -> 4 x 512 GELU -> 512", "t_training_solves_s": t_data, "t_fit_s": t_fit,
+        "final_loss": ws.losses[-1],
+        "gmres_iterations_to_1e-7": {"zero_guess_mean": float(it0.mean()), "warm_mean": float(it1.mean()),
+                                     "zero_guess_max": int(it0.max()), "warm_max": int(it1.max())},
+        "guess_rel_err_median": float(np.median(gerr)), "guess_rel_err_max": float(gerr.max()),
+    }))
+
+
+if __name__ == "__main__":
+    main()
