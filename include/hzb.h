@@ -166,6 +166,19 @@ hzb_status hzb_local_inverse(hzb_ctx *ctx, int R, const double *y, const double 
                              double alpha, double beta, double *tau, int on_device,
                              int precision);
 
+/* The same FP64 D^{-1} apply as hzb_local_inverse (device pointers, N x R complex),
+ * for callers that cannot allocate device memory when they call: code inside CUDA
+ * stream capture (allocation is not capturable), real-time or embedded pipelines
+ * with a memory budget fixed at start-up, runtimes that own the device allocator.
+ * It allocates nothing: its scratch is a static 16 MiB device array of the library
+ * (held by every GPU that loads it until exit), so a call fails with HZB_EINVAL when
+ * a shape's mode panel (M+1) x N_G x (2 m_s R) exceeds 524,288 complex values.  All
+ * calls on a device share that array: calls that overlap on the GPU race.  The first
+ * call on a device looks up the array's address; make it before any stream capture.
+ * The paper has no counterpart of this entry point. */
+hzb_status hzb_local_inverse_noalloc(hzb_ctx *ctx, int R, const double *y, const double *sigma,
+                                     double alpha, double beta, double *tau);
+
 /* z = sigma + D^{-1} B sigma, the preconditioned operator of Eq. (precond). */
 hzb_status hzb_apply(hzb_ctx *ctx, int R, const double *sigma, double *z, int on_device,
                      int precision);

@@ -120,6 +120,7 @@ def lib():
         "hzb_far_field": (i, [p, i, p, p]),
         "hzb_eval_field": (i, [p, i, p, p]),
         "hzb_autotune": (i, [p, i, i, p]),
+        "hzb_local_inverse_noalloc": (i, [p, i, p, p, d, d, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -268,6 +269,18 @@ class Solver:
             sp = _ptr(s2)
         self._check(lib().hzb_local_inverse(self._h, R, _ptr(a), sp, float(alpha), float(beta), _ptr(out), dev,
                                             int(precision)))
+        return out
+
+    def local_inverse_noalloc(self, y, sigma=None, alpha: float = 0.0, beta: float = 1.0, out=None):
+        """FP64 D^{-1} apply through hzb_local_inverse_noalloc: device tensors only; the
+        library allocates nothing for this call (static scratch, see include/hzb.h)."""
+        if not _is_dev(y) or (sigma is not None and not _is_dev(sigma)):
+            raise ValueError("local_inverse_noalloc takes CUDA tensors only")
+        R = 1 if y.ndim == 1 else int(y.shape[1])
+        if out is None:
+            out = y.new_empty(y.shape)
+        sp = _ptr(sigma) if sigma is not None else None
+        self._check(lib().hzb_local_inverse_noalloc(self._h, R, _ptr(y), sp, float(alpha), float(beta), _ptr(out)))
         return out
 
     def apply(self, sigma, precision: int = HZB_PREC_FP64):

@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
 
-SOURCES = ["api.cpp", "geometry.cpp", "setup.cu", "nbody.cu", "modal.cu", "krylov.cu", "mlp.cu"]
+SOURCES = ["api.cpp", "geometry.cpp", "setup.cu", "nbody.cu", "modal.cu", "krylov.cu", "mlp.cu", "noalloc.cu"]
 HEADERS = ["hzb_internal.h", "curve.h", "kernel_math.cuh"]
 
 

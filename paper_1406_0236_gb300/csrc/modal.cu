@@ -7,6 +7,8 @@
 // body of that shape, the +p and -p coefficient vectors of all right-hand sides.
 // Column layout of a shape's mode-p panel: col = (2 * body_in_shape + sign) * R + r,
 // sign 0 for +p and 1 for -p (the -0 columns are zero).
+#include <algorithm>
+
 #include "hzb_internal.h"
 #include "kernel_math.cuh"
 
@@ -225,6 +227,47 @@ hzb_status local_inverse32(hzb_ctx *c, int R, const double2 *y, const double2 *s
                            double2 *tau)
 {
     return local_inverse_t<float>(c, R, y, sigma, alpha, beta, tau);
+}
+
+}  // namespace hzb
+
+namespace hzb {
+
+// The FP64 D^{-1} apply with caller-provided scratch: yh and th each hold at least
+// (M+1) x N_G x (2 m_s R) complex values for every shape (shapes run one after the
+// other on the stream, reusing them).  Launches the same kernels as local_inverse64
+// and allocates nothing.
+hzb_status local_inverse64_scratch(hzb_ctx *c, int R, const double2 *y, const double2 *sigma, double alpha,
+                                   double beta, double2 *tau, double2 *yh, double2 *th)
+{
+    for (ShapeDev *sp : c->shapes) {
+        ShapeDev &sd = *sp;
+        const int NG = sd.geom.NG, NF = sd.geom.NF, M = sd.geom.M;
+        const int ms = (int)sd.bodies.size();
+        const int ncols = 2 * ms * R;
+        const long long *doff = sd.body_offs.ptr;
+        size_t smem = (size_t)NF * (R + 1) * sizeof(double2);
+        if (smem > 200 * 1024) return fail(c, HZB_EINVAL, "n_modes * R too large for the modal apply");
+        cudaFuncSetAttribute(dft_forward_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(dft_inverse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dft_forward_kernel<double><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, y, yh);
+        modal_gemm_kernel<double><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(
+            NG, ncols, sd.S64.ptr, yh, th);
+        dft_inverse_kernel<double><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, th,
+                                                                                    sigma, alpha, beta, tau);
+        c->launches += 3;
+        if (check_cuda(c, cudaGetLastError(), "modal apply")) return HZB_ECUDA;
+    }
+    return HZB_OK;
+}
+
+// Largest per-shape panel (M+1) x N_G x (2 m_s R) of the context, in complex values.
+size_t modal_panel_elems(const hzb_ctx *c, int R)
+{
+    size_t mx = 0;
+    for (const ShapeDev *sp : c->shapes)
+        mx = std::max(mx, (size_t)(sp->geom.M + 1) * sp->geom.NG * (2 * sp->bodies.size() * (size_t)R));
+    return mx;
 }
 
 }  // namespace hzb
