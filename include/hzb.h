@@ -57,7 +57,10 @@ typedef enum {
 
 typedef enum {
     HZB_PREC_FP64 = 0,        /* every kernel in FP64 */
-    HZB_PREC_MIXED_FP32 = 1   /* FP64 outer refinement, FP32 inter-body sum and modal apply inside */
+    HZB_PREC_MIXED_FP32 = 1,  /* FP64 outer refinement, FP32 inter-body sum and modal apply inside */
+    HZB_PREC_DOUBLE_FLOAT = 2 /* inter-body sum in double-float (two FP32 numbers, ~48-bit
+                                 significand, ~1e-13 relative per term) on the FP32 pipe;
+                                 valid for hzb_interbody/hzb_apply and as the refinement residual */
 } hzb_precision;
 
 typedef enum { HZB_SPHERE = 0, HZB_SPHEROID = 1, HZB_OPEN_SHELL = 2 } hzb_shape_kind;
@@ -76,6 +79,8 @@ typedef struct {
                               rel_k * max(c_1, inner_tol) * 10 <= gmres_tol holds for the next
                               correction (c_1: contraction observed in the first refinement
                               step), saving the last FP64 apply */
+    int residual;          /* mixed mode: precision of the refinement residual's inter-body sum,
+                              HZB_PREC_FP64 (default) or HZB_PREC_DOUBLE_FLOAT */
 } hzb_options;
 
 typedef struct {
@@ -101,6 +106,8 @@ typedef struct {
     long long n_nbody64;     /* its launches during the solve */
     long long n_nbody32;
     long long kernel_launches;    /* kernels of this library launched during the solve */
+    double t_nbodydf_ms;     /* summed device time of the double-float inter-body kernel */
+    long long n_nbodydf;
 } hzb_stats;
 
 /* Fill *o with defaults: device 0, default stream, FP64, tol 1e-10, no restart,
@@ -127,7 +134,7 @@ hzb_status hzb_set_wave(hzb_ctx *ctx, double k, double eta);
  * body z), centre c[3], rotation rot[9] row-major whose columns are the body x, y,
  * z axes in world coordinates (x_world = c + rot * x_body).  Azimuth theta_l =
  * 2 pi l / N_F is measured from the body x axis.  Bodies with identical hzb_shape
- * share one set of scattering matrices (Sec. 6.2, repeated shapes). */
+ * share one set of scattering matrices (the remark on repeated shapes in Sec. 6). */
 hzb_status hzb_add_body(hzb_ctx *ctx, const hzb_shape *shape, const double c[3],
                         const double rot[9], int *body_id);
 
@@ -150,6 +157,17 @@ hzb_status hzb_build_scattering_matrices(hzb_ctx *ctx);
  * which: bit 0 = FP32 kernel, bit 1 = FP64 kernel.  best_ms (may be NULL): the
  * fastest time per launch [FP32, FP64].  Not part of the paper: a GB300 tuning aid. */
 hzb_status hzb_autotune(hzb_ctx *ctx, int R, int which, double best_ms[2]);
+
+/* GMRES execution controls (no effect on results beyond rounding of where a
+ * converged right-hand side stops):
+ *   check_every: Arnoldi steps issued between host reads of the residual estimates
+ *                (0 = auto: 4 when N x R <= 1e6, else 1); a right-hand side that
+ *                converges inside a chunk is frozen on the device, so later steps of
+ *                the chunk change nothing for it;
+ *   use_graphs:  capture each Arnoldi step j (operator apply, CGS2, Givens) once as a
+ *                CUDA graph and replay it in later iterations and solves (-1 auto:
+ *                on when N x R <= 4e6; needs a non-default stream). */
+hzb_status hzb_set_execution(hzb_ctx *ctx, int check_every, int use_graphs);
 
 /* Copy A~_p (which = 0) or S_p (which = 1) of the shape of body `body`, mode p in
  * 0..M, to host out (N_G x N_G complex, row-major). */

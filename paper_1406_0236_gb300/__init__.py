@@ -12,8 +12,8 @@ scatterers" — combined-field BIE (Sec. 2), Fourier-mode Nystrom discretisation
 each body (Sec. 3.2), block-diagonal preconditioner with per-mode scattering
 matrices and GMRES (Sec. 4).
 """
-from .binding import (HZB_PREC_FP64, HZB_PREC_MIXED_FP32, HZB_OPEN_SHELL, HZB_SPHERE, HZB_SPHEROID,
+from .binding import (HZB_PREC_DOUBLE_FLOAT, HZB_PREC_FP64, HZB_PREC_MIXED_FP32, HZB_OPEN_SHELL, HZB_SPHERE, HZB_SPHEROID,
                       HzbError, Mlp, Options, Solver, Stats, lib, library_path)
 
-__all__ = ["HZB_PREC_FP64", "HZB_PREC_MIXED_FP32", "HZB_SPHERE", "HZB_SPHEROID", "HZB_OPEN_SHELL",
+__all__ = ["HZB_PREC_DOUBLE_FLOAT", "HZB_PREC_FP64", "HZB_PREC_MIXED_FP32", "HZB_SPHERE", "HZB_SPHEROID", "HZB_OPEN_SHELL",
            "HzbError", "Mlp", "Options", "Solver", "Stats", "lib", "library_path"]

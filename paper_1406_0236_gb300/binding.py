@@ -17,6 +17,7 @@ _LIBPATH = os.path.join(HERE, "libhzb.so")
 
 HZB_PREC_FP64 = 0
 HZB_PREC_MIXED_FP32 = 1
+HZB_PREC_DOUBLE_FLOAT = 2
 HZB_SPHERE, HZB_SPHEROID, HZB_OPEN_SHELL = 0, 1, 2
 
 _STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
@@ -33,7 +34,8 @@ class HzbError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("verify_final", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("verify_final", ctypes.c_int),
+                ("residual", ctypes.c_int)]
 
 
 class _Shape(ctypes.Structure):
@@ -47,7 +49,8 @@ class _Stats(ctypes.Structure):
                 ("t_setup_ms", ctypes.c_double), ("interbody_applies", ctypes.c_longlong),
                 ("t_nbody64_ms", ctypes.c_double), ("t_nbody32_ms", ctypes.c_double),
                 ("n_nbody64", ctypes.c_longlong), ("n_nbody32", ctypes.c_longlong),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("t_nbodydf_ms", ctypes.c_double),
+                ("n_nbodydf", ctypes.c_longlong)]
 
 
 @dataclass
@@ -64,6 +67,8 @@ class Stats:
     n_nbody64: int = 0
     n_nbody32: int = 0
     kernel_launches: int = 0
+    t_nbodydf_ms: float = 0.0
+    n_nbodydf: int = 0
     status: int = 0
 
 
@@ -77,6 +82,7 @@ class Options:
     inner_tol: float = 1e-5
     max_outer: int = 10
     verify_final: int = 1
+    residual: int = HZB_PREC_FP64
 
 
 def library_path() -> str:
@@ -121,6 +127,7 @@ def lib():
         "hzb_eval_field": (i, [p, i, p, p]),
         "hzb_autotune": (i, [p, i, i, p]),
         "hzb_local_inverse_noalloc": (i, [p, i, p, p, d, d, p]),
+        "hzb_set_execution": (i, [p, i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -155,6 +162,7 @@ class Solver:
         co.device, co.precision, co.gmres_tol = o.device, o.precision, o.gmres_tol
         co.restart, co.maxit, co.inner_tol, co.max_outer = o.restart, o.maxit, o.inner_tol, o.max_outer
         co.verify_final = o.verify_final
+        co.residual = o.residual
         co.cuda_stream = stream
         self._opt = co
         h = ctypes.c_void_p()
@@ -183,6 +191,10 @@ class Solver:
 
     def set_stream(self, stream_handle: int):
         self._check(lib().hzb_set_stream(self._h, ctypes.c_void_p(stream_handle)))
+
+    def set_execution(self, check_every: int = 0, use_graphs: int = -1):
+        """GMRES steps between host checks (0 = auto) and CUDA graphs (-1 auto, 0 off, 1 on)."""
+        self._check(lib().hzb_set_execution(self._h, int(check_every), int(use_graphs)))
 
     def set_options(self, **kw):
         for k_, v in kw.items():
@@ -292,7 +304,7 @@ class Solver:
     def _stats(self, st: _Stats, status: int) -> Stats:
         return Stats(st.iterations, st.outer_iterations, bool(st.converged), st.rel_residual, st.t_solve_ms,
                      st.t_setup_ms, st.interbody_applies, st.t_nbody64_ms, st.t_nbody32_ms, st.n_nbody64,
-                     st.n_nbody32, st.kernel_launches, status)
+                     st.n_nbody32, st.kernel_launches, st.t_nbodydf_ms, st.n_nbodydf, status)
 
     def solve_plane_waves(self, dirs, allow_noconv: bool = False) -> Stats:
         d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)

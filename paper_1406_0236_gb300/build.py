@@ -21,8 +21,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
 
-SOURCES = ["api.cpp", "geometry.cpp", "setup.cu", "nbody.cu", "modal.cu", "krylov.cu", "mlp.cu", "noalloc.cu"]
-HEADERS = ["hzb_internal.h", "curve.h", "kernel_math.cuh"]
+SOURCES = ["api.cpp", "geometry.cpp", "setup.cu", "nbody.cu", "modal.cu", "krylov.cu", "mlp.cu", "noalloc.cu",
+           "nbody_df.cu"]
+# double-float error-free transformations must not be contracted into fused multiply-adds
+PER_FILE = {"nbody_df.cu": ["-fmad=false"]}
+HEADERS = ["hzb_internal.h", "curve.h", "kernel_math.cuh", "dfloat.cuh"]
 
 
 def nvcc() -> str:
@@ -41,6 +44,7 @@ def _compile(src: str, extra) -> str:
     deps = [os.path.join(SRC, src)] + [os.path.join(SRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "hzb.h")]
     if os.path.exists(obj) and os.path.getmtime(obj) >= _newest(deps):
         return obj
+    extra = list(extra) + PER_FILE.get(src, [])
     cmd = [nvcc()] + ARCH + FLAGS + list(extra) + ["-c", os.path.join(SRC, src), "-o", obj]
     if src.endswith(".cpp"):
         cmd = [nvcc()] + ARCH + FLAGS + list(extra) + ["-x", "cu", "-c", os.path.join(SRC, src), "-o", obj]

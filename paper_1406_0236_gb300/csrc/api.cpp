@@ -52,6 +52,7 @@ void hzb_default_options(hzb_options *o)
     o->inner_tol = 1e-5;
     o->max_outer = 10;
     o->verify_final = 1;
+    o->residual = HZB_PREC_FP64;
 }
 
 const char *hzb_status_string(hzb_status s)
@@ -72,6 +73,7 @@ const char *hzb_status_string(hzb_status s)
 static bool valid_options(const hzb_options *o)
 {
     return o && o->device >= 0 && (o->precision == HZB_PREC_FP64 || o->precision == HZB_PREC_MIXED_FP32) &&
+           (o->residual == HZB_PREC_FP64 || o->residual == HZB_PREC_DOUBLE_FLOAT) &&
            o->gmres_tol > 0 && o->maxit > 0 && o->max_outer > 0 && o->inner_tol > 0 && o->inner_tol < 1;
 }
 
@@ -117,7 +119,9 @@ hzb_status hzb_destroy(hzb_ctx *c)
     c->io_in.release(); c->io_out.release(); c->io_small.release(); c->tiny.release(); c->sol.release();
     c->red.release(); c->krylov.release(); c->small.release();
     c->sctab.release(); c->nb_part64.release(); c->nb_part32.release();
+    c->dfa.release(); c->dfb.release(); c->dfc.release(); c->dftab.release();
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
+    release_graphs(c);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -302,7 +306,8 @@ static hzb_status check_apply_args(hzb_ctx *c, int R, const void *a, const void 
     if (c->state < 2) return fail(c, HZB_ESTATE, "no bodies");
     if (need_build && c->state != 3) return fail(c, HZB_ESTATE, "scattering matrices not built");
     if (R < 1 || R > 4096 || !a || !b) return fail(c, HZB_EINVAL, "bad R or null pointer");
-    if (precision != HZB_PREC_FP64 && precision != HZB_PREC_MIXED_FP32) return fail(c, HZB_EINVAL, "bad precision");
+    if (precision != HZB_PREC_FP64 && precision != HZB_PREC_MIXED_FP32 && precision != HZB_PREC_DOUBLE_FLOAT)
+        return fail(c, HZB_EINVAL, "bad precision");
     return HZB_OK;
 }
 
@@ -320,7 +325,8 @@ hzb_status hzb_interbody(hzb_ctx *c, int R, const double *sigma, double *y, int 
         if (check_cuda(c, c->io_out.ensure(n), "alloc")) return HZB_ENOMEM;
         out = c->io_out.ptr;
     }
-    st = (precision == HZB_PREC_FP64) ? interbody64(c, R, s, out) : interbody32(c, R, s, out);
+    st = (precision == HZB_PREC_FP64) ? interbody64(c, R, s, out)
+         : (precision == HZB_PREC_DOUBLE_FLOAT) ? interbody_df(c, R, s, out) : interbody32(c, R, s, out);
     if (st) return st;
     return finish_out(c, out, y, n, on_device);
 }
@@ -341,8 +347,8 @@ hzb_status hzb_local_inverse(hzb_ctx *c, int R, const double *y, const double *s
         if (check_cuda(c, c->io_out.ensure(n), "alloc")) return HZB_ENOMEM;
         out = c->io_out.ptr;
     }
-    st = (precision == HZB_PREC_FP64) ? local_inverse64(c, R, dy, ds, alpha, beta, out)
-                                      : local_inverse32(c, R, dy, ds, alpha, beta, out);
+    st = (precision == HZB_PREC_MIXED_FP32) ? local_inverse32(c, R, dy, ds, alpha, beta, out)
+                                            : local_inverse64(c, R, dy, ds, alpha, beta, out);
     if (st) return st;
     return finish_out(c, out, tau, n, on_device);
 }
@@ -435,6 +441,16 @@ hzb_status hzb_autotune(hzb_ctx *c, int R, int which, double best_ms[2])
     if (c->state < 2) return fail(c, HZB_ESTATE, "no bodies");
     if (R < 1 || R > 4096 || which < 1 || which > 3) return fail(c, HZB_EINVAL, "bad R or selector");
     return autotune(c, R, which, best_ms);
+}
+
+hzb_status hzb_set_execution(hzb_ctx *c, int check_every, int use_graphs)
+{
+    if (!c) return HZB_EINVAL;
+    if (check_every < 0 || check_every > 64 || use_graphs < -1 || use_graphs > 1)
+        return fail(c, HZB_EINVAL, "check_every in [0, 64], use_graphs in {-1, 0, 1}");
+    c->check_every = check_every;
+    c->use_graphs = use_graphs;
+    return HZB_OK;
 }
 
 hzb_status hzb_far_field(hzb_ctx *c, int n, const double *xhat, double *out)

@@ -147,6 +147,18 @@ struct hzb_ctx {
     int tune64_tpt = 0, tune64_split = 0;      // 0: default
     int tune32_tpt = 0, tune32_split = 0;
     int tune_limit_blocks = 0;                 // autotuner: time only the first blocks (0 = all)
+    // double-float inter-body kernel: split positions/normals, cos/sin table, launch shape
+    hzb::DevBuf<float4> dfa, dfb, dfc, dftab;
+    bool df_ready = false;
+    int tunedf_tpt = 0, tunedf_split = 0;
+    // GMRES execution: steps between host checks (0 = auto) and CUDA graphs (-1 auto, 0 off, 1 on)
+    int check_every = 0;
+    int use_graphs = -1;
+    std::vector<cudaGraphExec_t> gexec;        // captured Arnoldi step j
+    std::vector<long long> glaunch;            // kernels per captured step
+    unsigned char gkey[256];
+    bool gkey_valid = false;
+    bool capturing = false;
     // device timing of the inter-body kernels during a solve: event pairs
     std::vector<cudaEvent_t> evpool;
     std::vector<int> evkind;                   // 0: FP64, 1: FP32, per recorded pair
@@ -169,6 +181,7 @@ hzb_status build_shape_matrices(hzb_ctx *c, ShapeDev &s);
 // nbody.cu: y = B sigma; sigma, y device N x R complex FP64 (FP32 path converts internally)
 hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
+hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   // nbody_df.cu
 hzb_status interbody64_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit);
 hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit);
 int default_nsplit(hzb_ctx *c, int R, int tpt);
@@ -189,6 +202,7 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
                        int precision, double tol, int maxit, int restart,
                        int *iters, double *relres, int *converged);
 hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *st);
+void release_graphs(hzb_ctx *c);
 
 // fields.cu
 hzb_status plane_waves(hzb_ctx *c, int R, const double *dirs_dev, double2 *v);

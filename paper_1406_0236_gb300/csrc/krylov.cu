@@ -12,6 +12,7 @@
 // FP32 modal GEMMs (Arnoldi and least squares stay FP64), x += d, repeat.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "hzb_internal.h"
@@ -192,7 +193,7 @@ __global__ void backsolve_kernel(int R, int m, GmresState s, double2 *y)
 
 int prof_begin(hzb_ctx *c, int kind)
 {
-    if (!c->prof_on) return -1;
+    if (!c->prof_on || c->capturing) return -1;
     const size_t slot = c->evkind.size();
     if (slot >= 4096) return -1;
     while (c->evpool.size() < 2 * (slot + 1)) {
@@ -245,6 +246,10 @@ hzb_status apply_op(hzb_ctx *c, int R, const double2 *x, double2 *z, int precisi
         if ((st = interbody32(c, R, x, c->w_c.ptr))) return st;
         return local_inverse32(c, R, c->w_c.ptr, x, 1.0, 1.0, z);
     }
+    if (precision == HZB_PREC_DOUBLE_FLOAT) {
+        if ((st = interbody_df(c, R, x, c->w_c.ptr))) return st;
+        return local_inverse64(c, R, c->w_c.ptr, x, 1.0, 1.0, z);
+    }
     if ((st = interbody64(c, R, x, c->w_c.ptr))) return st;
     return local_inverse64(c, R, c->w_c.ptr, x, 1.0, 1.0, z);
 }
@@ -259,6 +264,64 @@ static hzb_status ensure_pinned(hzb_ctx *c, size_t n)
     c->host_pinned_n = n;
     return HZB_OK;
 }
+
+// Pointers and sizes a captured Arnoldi step depends on: a change invalidates the graphs.
+struct GraphKey {
+    const void *p[14];
+    long long N;
+    int R, m, precision, tpt32, split32, tpt64, split64;
+    bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+static void drop_graphs(hzb_ctx *c)
+{
+    for (cudaGraphExec_t g : c->gexec)
+        if (g) cudaGraphExecDestroy(g);
+    c->gexec.clear();
+    c->glaunch.clear();
+}
+
+// Replay the captured graph of Arnoldi step j (capturing it on first use).
+template <typename F>
+static hzb_status graph_step(hzb_ctx *c, int j, F &step, const GraphKey &key)
+{
+    if (!c->gkey_valid || std::memcmp(c->gkey, &key, sizeof(GraphKey)) != 0) {
+        drop_graphs(c);
+        std::memcpy(c->gkey, &key, sizeof(GraphKey));
+        c->gkey_valid = true;
+    }
+    if ((int)c->gexec.size() <= j) {
+        c->gexec.resize(j + 1, nullptr);
+        c->glaunch.resize(j + 1, 0);
+    }
+    if (!c->gexec[j]) {
+        const long long l0 = c->launches, i0 = c->interbody_calls;
+        if (check_cuda(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture"))
+            return HZB_ECUDA;
+        c->capturing = true;
+        hzb_status st = step(j);
+        c->capturing = false;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (st || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return st ? st : check_cuda(c, e, "end capture");
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (check_cuda(c, e, "graph instantiate")) return HZB_ECUDA;
+        c->gexec[j] = ex;
+        c->glaunch[j] = c->launches - l0;
+        c->launches = l0;
+        c->interbody_calls = i0;
+    }
+    c->launches += c->glaunch[j];
+    c->interbody_calls += 1;
+    return check_cuda(c, cudaGraphLaunch(c->gexec[j], c->stream), "graph launch");
+}
+
+void release_graphs(hzb_ctx *c) { drop_graphs(c); }
 
 hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is_zero, int precision, double tol,
                        int maxit, int restart, int *iters, double *relres, int *converged)
@@ -299,10 +362,32 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
     double2 *w = c->w_a.ptr;
     const unsigned gN = nblocks((long long)NR);
     const unsigned gR = nblocks(R, 64);
-    int total = 0;
+    int total = 0, real_iters = 0;
     bool first = true, all_done = false;
     double *hres = c->host_pinned;
     int *hact = (int *)(c->host_pinned + R);
+    int *hjd = hact + R;
+    // dot-product partial sums sized for the largest step, so that a captured step
+    // never reallocates
+    {
+        int nblk = (int)std::min<long long>(120, std::max<long long>(1, N / (RED_THREADS * 8)));
+        if (check_cuda(c, c->w_d.ensure(std::max<size_t>((size_t)(m + 1) * R * nblk, NR)), "alloc partial"))
+            return HZB_ENOMEM;
+    }
+    // CUDA graphs need a capturable (non-legacy) stream; auto = small problems only
+    bool graphs = c->use_graphs > 0 || (c->use_graphs < 0 && (long long)NR <= 4000000);
+    if (c->stream == nullptr) graphs = false;
+    GraphKey graph_key;
+    std::memset(&graph_key, 0, sizeof(graph_key));
+    {
+        const void *ps[14] = {V, w, c->small.ptr, c->w_c.ptr, c->w_d.ptr, c->yhat64.ptr, c->that64.ptr,
+                              c->yhat32.ptr, c->that32.ptr, c->nb_part32.ptr, c->nb_part64.ptr, c->sctab.ptr,
+                              (const void *)c->stream, c->tblocks.ptr};
+        std::memcpy(graph_key.p, ps, sizeof(ps));
+        graph_key.N = N; graph_key.R = R; graph_key.m = m; graph_key.precision = precision;
+        graph_key.tpt32 = c->tune32_tpt; graph_key.split32 = c->tune32_split;
+        graph_key.tpt64 = c->tune64_tpt; graph_key.split64 = c->tune64_split;
+    }
     if (x_is_zero && (st = vec_zero(c, x, NR))) return st;
     // ||b|| once
     if ((st = cdots(c, R, 1, b, 0, b, s.nrm2))) return st;
@@ -336,25 +421,47 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
             all_done = !any;
             break;
         }
-        int j = 0;
-        for (; j < m && total < maxit; ++j) {
-            double2 *Vj = V + (size_t)j * NR;
-            if ((st = apply_op(c, R, Vj, w, precision))) return st;
-            if ((st = cdots(c, R, j + 1, V, (long long)NR, w, s.h1))) return st;
-            caxpy_multi_kernel<<<gN, 256, 0, c->stream>>>(N, R, j + 1, V, (long long)NR, s.h1, w);
-            if ((st = cdots(c, R, j + 1, V, (long long)NR, w, s.h2))) return st;
-            caxpy_multi_kernel<<<gN, 256, 0, c->stream>>>(N, R, j + 1, V, (long long)NR, s.h2, w);
-            if ((st = cdots(c, R, 1, w, 0, w, s.nrm2))) return st;
-            givens_kernel<<<gR, 64, 0, c->stream>>>(R, m, j, s, tol);
+        // One Arnoldi step: z = A V_j, CGS2 against V_0..V_j, norm, Givens, V_{j+1}.
+        auto arnoldi_step = [&](int jj) -> hzb_status {
+            hzb_status e2;
+            double2 *Vj = V + (size_t)jj * NR;
+            if ((e2 = apply_op(c, R, Vj, w, precision))) return e2;
+            if ((e2 = cdots(c, R, jj + 1, V, (long long)NR, w, s.h1))) return e2;
+            caxpy_multi_kernel<<<gN, 256, 0, c->stream>>>(N, R, jj + 1, V, (long long)NR, s.h1, w);
+            if ((e2 = cdots(c, R, jj + 1, V, (long long)NR, w, s.h2))) return e2;
+            caxpy_multi_kernel<<<gN, 256, 0, c->stream>>>(N, R, jj + 1, V, (long long)NR, s.h2, w);
+            if ((e2 = cdots(c, R, 1, w, 0, w, s.nrm2))) return e2;
+            givens_kernel<<<gR, 64, 0, c->stream>>>(R, m, jj, s, tol);
             c->launches += 4;                  // two caxpy, givens, scale
-            scale_kernel<<<gN, 256, 0, c->stream>>>(N, R, w, s.inv, V + (size_t)(j + 1) * NR);
+            scale_kernel<<<gN, 256, 0, c->stream>>>(N, R, w, s.inv, V + (size_t)(jj + 1) * NR);
+            return HZB_OK;
+        };
+        // Steps run in chunks of `every` without host synchronisation: a right-hand
+        // side that converges inside a chunk is frozen by givens_kernel (its next basis
+        // vectors are zero and its jdone stays), so the extra steps change nothing.
+        const int every = c->check_every > 0 ? c->check_every : ((long long)NR <= 1000000 ? 4 : 1);
+        int j = 0;
+        while (j < m && total < maxit) {
+            const int q = std::min(every, std::min(m - j, maxit - total));
+            for (int t = 0; t < q; ++t, ++j, ++total) {
+                if (graphs && j > 0) {
+                    if ((st = graph_step(c, j, arnoldi_step, graph_key))) return st;
+                } else if ((st = arnoldi_step(j))) {
+                    return st;
+                }
+            }
             cudaMemcpyAsync(hres, s.res, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
             cudaMemcpyAsync(hact, s.active, R * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+            cudaMemcpyAsync(hjd, s.jdone, R * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
             if (check_cuda(c, cudaStreamSynchronize(c->stream), "gmres iteration")) return HZB_ECUDA;
-            ++total;
             bool anyact = false;
             for (int r = 0; r < R; ++r) anyact |= hact[r] != 0;
             if (!anyact) break;
+        }
+        {
+            int jmax = 0;
+            for (int r = 0; r < R; ++r) jmax = std::max(jmax, hjd[r]);
+            real_iters += jmax;
         }
         backsolve_kernel<<<gR, 64, 0, c->stream>>>(R, m, s, y);
         update_x_kernel<<<gN, 256, 0, c->stream>>>(N, R, m, V, (long long)NR, y, s.jdone, x);
@@ -375,7 +482,7 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
         if (!std::isfinite(hres[r])) bad = true;
         worst = std::max(worst, hres[r]);
     }
-    *iters = total;
+    *iters = real_iters;
     *relres = worst;
     *converged = all_done && worst <= tol && !bad;
     if (bad) return fail(c, HZB_ENAN, "non-finite residual in GMRES");
@@ -388,7 +495,7 @@ static hzb_status true_residual(hzb_ctx *c, int R, const double2 *b, const doubl
 {
     const size_t NR = (size_t)c->N * R;
     hzb_status st;
-    if ((st = apply_op(c, R, x, r_out, HZB_PREC_FP64))) return st;
+    if ((st = apply_op(c, R, x, r_out, c->opt.residual))) return st;
     axpby_kernel<<<nblocks((long long)NR), 256, 0, c->stream>>>((long long)NR, 1.0, b, -1.0, r_out, r_out);
     c->launches++;
     DevBuf<double2> &tmp = c->tiny;
@@ -485,8 +592,8 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     c->prof_on = false;
-    double tk[2] = {0.0, 0.0};
-    long long nk[2] = {0, 0};
+    double tk[3] = {0.0, 0.0, 0.0};
+    long long nk[3] = {0, 0, 0};
     for (size_t q = 0; q < c->evkind.size(); ++q) {
         float e = 0.f;
         if (cudaEventElapsedTime(&e, c->evpool[2 * q], c->evpool[2 * q + 1]) == cudaSuccess) {
@@ -498,6 +605,8 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
     if (stats) {
         stats->t_nbody64_ms = tk[0];
         stats->t_nbody32_ms = tk[1];
+        stats->t_nbodydf_ms = tk[2];
+        stats->n_nbodydf = nk[2];
         stats->n_nbody64 = nk[0];
         stats->n_nbody32 = nk[1];
         stats->kernel_launches = c->launches - launches0;

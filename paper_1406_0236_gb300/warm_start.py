@@ -2,8 +2,9 @@
 
 1. Training densities: the library solves the plane-wave problems of the training
    directions (batched right-hand sides, FP64 accuracy via mixed refinement).
-2. POD basis: the leading left singular vectors of the N x T snapshot matrix
-   (library SVD of torch; an offline step, not part of any solve).
+2. POD basis: the leading left singular vectors of the N x T snapshot matrix, by the
+   randomized range finder of Halko, Martinsson and Tropp in complex64 (offline;
+   library GEMM/QR/SVD of torch on a (n_pod + 64)-column sketch).
 3. Network: hzb_mlp (BF16 weights, FP32 accumulation, hand-written CUDA kernels)
    maps the direction (3 numbers) to the n_pod complex POD coefficients (2 n_pod
    real outputs, scaled to unit RMS), trained with Adam on the MSE loss.
@@ -56,19 +57,38 @@ class WarmStart:
             X[:, a:a + d.shape[0]] = out
         return X
 
+    def pod_basis(self, X, oversample: int = 64, seed: int = 7):
+        """Leading n_pod left singular vectors of X (randomized range finder, one power step)."""
+        torch = self.torch
+        g = torch.Generator(device="cuda").manual_seed(seed)
+        X32 = X.to(torch.complex64)
+        k = min(self.n_pod + oversample, X.shape[1])
+        Om = torch.complex(torch.randn(X.shape[1], k, device="cuda", generator=g),
+                           torch.randn(X.shape[1], k, device="cuda", generator=g))
+        Q, _ = torch.linalg.qr(X32 @ Om)
+        Q, _ = torch.linalg.qr(X32 @ (X32.conj().T @ Q))                 # one power iteration
+        Ub, _, _ = torch.linalg.svd(Q.conj().T @ X32, full_matrices=False)
+        U = (Q @ Ub[:, :self.n_pod]).to(torch.complex128)
+        U, _ = torch.linalg.qr(U)                                         # re-orthonormalise in FP64
+        return U.contiguous()
+
     def fit(self, dirs: np.ndarray, X=None, epochs: int = 400, batch: int = 256, lr: float = 1e-3,
             lr_final: float = 2e-5):
         torch = self.torch
         if X is None:
             X = self.training_densities(dirs)
-        U, _, _ = torch.linalg.svd(X, full_matrices=False)
-        self.U = U[:, :self.n_pod].contiguous()
+        t0 = time.time()
+        self.U = self.pod_basis(X)
         C = self.U.conj().T @ X                                         # n_pod x T coefficients
-        T = torch.stack([C.real, C.imag], dim=-1).reshape(self.n_pod * 2, -1).T.contiguous()  # T x 2n_pod
+        # T x 2 n_pod targets: row t = (Re c_0, Im c_0, Re c_1, Im c_1, ...) of sample t
+        T = torch.stack([C.real, C.imag], dim=-1).permute(1, 0, 2).reshape(X.shape[1], 2 * self.n_pod).contiguous()
+        torch.cuda.synchronize()
+        self.t_pod = time.time() - t0
         self.scale = float(T.pow(2).mean().sqrt())
         Tn = (T / self.scale).float().contiguous()
         D = torch.from_numpy(np.ascontiguousarray(dirs, dtype=np.float32)).cuda()
         n = D.shape[0]
+        t0 = time.time()
         g = torch.Generator(device="cuda").manual_seed(11)
         steps = epochs * max(1, n // batch)
         q = 0
@@ -80,6 +100,9 @@ class WarmStart:
                 loss = self.mlp.train_step(D[idx].contiguous(), Tn[idx].contiguous(), rate)
                 q += 1
             self.losses.append(loss)
+        torch.cuda.synchronize()
+        self.t_train = time.time() - t0
+        self.train_steps = q
         return self
 
     def guess(self, dirs: np.ndarray):
@@ -136,17 +159,46 @@ def main():
     # iterations to 1e-7 on the held-out directions: FP64 path, zero guess vs warm start
     s.set_options(precision=0, gmres_tol=1e-7)
     it0, it1 = iterations_with_and_without(s, ws, held, wl.k, 1e-7)
-    # density error of the bare guess
+    # density error of the bare guess (reference: mixed refinement to 1e-11)
+    s.set_options(precision=1, gmres_tol=1e-11, verify_final=1)
     Xh = ws.training_densities(held)
     G = ws.guess(held)
     gerr = (torch.linalg.vector_norm(G - Xh, dim=0) / torch.linalg.vector_norm(Xh, dim=0)).cpu().numpy()
+    # held-out throughput, batches of 64 right-hand sides, residual 1e-8 (density error checked):
+    # FP64 GPU path from zero against mixed precision + warm start
+    x, _, _ = s.get_nodes()
+
+    def timed(prec, warm):
+        s.set_options(precision=prec, gmres_tol=1e-8, verify_final=1 if prec == 0 else 0)
+        out = torch.empty_like(Xh)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        its = []
+        for a in range(0, held.shape[0], 64):
+            d = held[a:a + 64]
+            v = plane_wave_data(x, d, wl.k)
+            st = s.solve_data(v, x0=ws.guess(d) if warm else None)
+            its.append(st.iterations)
+            s.get_density(out[:, a:a + d.shape[0]])
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        err = float((torch.linalg.vector_norm(out - Xh, dim=0) / torch.linalg.vector_norm(Xh, dim=0)).max())
+        return held.shape[0] / dt, its, err
+
+    r64, it64, e64 = timed(0, False)
+    rmw, itmw, emw = timed(1, True)
+    rm0, itm0, em0 = timed(1, False)
     print(json.dumps({
         "workload": "two_spheres_8200", "train": 4096, "held_out": 512, "pod_modes": ws.n_pod,
         "mlp": "3 -> 4 x 512 GELU -> 512", "t_training_solves_s": t_data, "t_fit_s": t_fit,
+        "t_pod_s": ws.t_pod, "t_train_s": ws.t_train, "train_steps": ws.train_steps,
         "final_loss": ws.losses[-1],
         "gmres_iterations_to_1e-7": {"zero_guess_mean": float(it0.mean()), "warm_mean": float(it1.mean()),
                                      "zero_guess_max": int(it0.max()), "warm_max": int(it1.max())},
         "guess_rel_err_median": float(np.median(gerr)), "guess_rel_err_max": float(gerr.max()),
+        "held_out_solves_per_s": {"fp64_gpu_zero_guess": r64, "mixed_plus_mlp": rmw, "mixed_zero_guess": rm0},
+        "held_out_density_err_max": {"fp64_gpu_zero_guess": e64, "mixed_plus_mlp": emw, "mixed_zero_guess": em0},
+        "batch_iterations": {"fp64_gpu_zero_guess": it64, "mixed_plus_mlp": itmw, "mixed_zero_guess": itm0},
     }))
 
 

@@ -97,3 +97,26 @@ def test_spheroids_258560_sampled_rows():
     # FP32: the phase k r carries the relative error of r (~2 ulp after the hardware
     # reciprocal square root) times k r <= 4 x 14 here, ~1e-5 per term at most.
     assert rel_l2(y32[rows], ref) < 3e-5
+
+
+@pytest.mark.parametrize("R", [1, 3, 9])
+def test_interbody_double_float(pair, R):
+    """Double-float (two FP32 numbers) inter-body sum: FP64-class accuracy."""
+    s, P = pair
+    sig = rand_c((P.N, R), 81 + R)
+    got = s.interbody(sig, precision=2)
+    ref = P.interbody(sig)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_spheroids_258560_double_float_rows():
+    require_gpu()
+    from oracle import Problem
+    wl = W.spheroids8()
+    s = gpu_solver(wl)
+    P = Problem(wl)
+    sig = rand_c((P.N, 1), 91)
+    rows = np.sort(np.random.default_rng(92).choice(P.N, 96, replace=False)).astype(np.int32)
+    ref = P.interbody(sig, targets=rows)
+    ydf = s.interbody(sig, precision=2)
+    assert np.abs(ydf[rows] - ref).max() < 1e-11 * np.abs(ref).max()
