@@ -67,7 +67,9 @@ typedef enum { HZB_SPHERE = 0, HZB_SPHEROID = 1, HZB_OPEN_SHELL = 2 } hzb_shape_
 
 typedef struct {
     int device;            /* CUDA device ordinal */
-    void *cuda_stream;     /* cudaStream_t to launch on; NULL = the legacy default stream */
+    void *cuda_stream;     /* cudaStream_t to launch on; NULL = the legacy default stream.  The
+                              stream must stay valid while the context uses it (change it with
+                              hzb_set_stream before destroying it) */
     int precision;         /* hzb_precision */
     double gmres_tol;      /* relative residual of the preconditioned system */
     int restart;           /* GMRES restart length (<= 0: no restart, up to maxit) */

@@ -202,3 +202,23 @@ def cached_scattering(rg: Rings, k: float, eta: float) -> np.ndarray:
     if key not in _CACHE:
         _CACHE[key] = scattering_matrices(modal_system(rg, k, eta))
     return _CACHE[key]
+
+
+def modal_rows(rg: Rings, rows, k: float, eta: float, M: Optional[int] = None) -> np.ndarray:
+    """Rows i in `rows` of A~_p = 1/2 I + K_p for p = 0..M, as (M+1, len(rows), N_G):
+    the same entries modal_matrices builds, computed only for the requested targets
+    (row i depends only on target ring i)."""
+    if M is None:
+        M = (rg.shape.n_modes - 1) // 2
+    rows = np.atleast_1d(rows)
+    out = np.zeros((M + 1, rows.size, rg.n), dtype=np.complex128)
+    for a, i in enumerate(rows):
+        nb = near_panels(rg, int(i))
+        far = np.nonzero(~np.isin(rg.panel, nb))[0]
+        if far.size:
+            md = _modes_trapezoid(rg, int(i), far, k, eta, M)
+            out[:, a, far] = (md * (rg.r[far] * rg.ds[far])[:, None]).T
+        for b in nb:
+            out[:, a, rg.panel_nodes(b)] = near_panel_entries(rg, int(i), b, k, eta, M)
+        out[:, a, int(i)] += 0.5
+    return out

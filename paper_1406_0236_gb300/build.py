@@ -24,7 +24,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 SOURCES = ["api.cpp", "geometry.cpp", "setup.cu", "nbody.cu", "modal.cu", "krylov.cu", "mlp.cu", "noalloc.cu",
            "nbody_df.cu"]
 # double-float error-free transformations must not be contracted into fused multiply-adds
-PER_FILE = {"nbody_df.cu": ["-fmad=false"]}
+# the FP32 inter-body kernel flushes denormals (irrelevant to its values, cheaper intrinsics)
+PER_FILE = {"nbody_df.cu": ["-fmad=false"], "nbody.cu": ["-ftz=true"]}
 HEADERS = ["hzb_internal.h", "curve.h", "kernel_math.cuh", "dfloat.cuh"]
 
 

@@ -31,11 +31,14 @@ hzb_status check_cuda(hzb_ctx *c, cudaError_t e, const char *what)
 
 }  // namespace hzb
 
+// Entry of every call: valid context, its device current, and no stale (non-sticky)
+// error of an unrelated earlier runtime call left for this call's checks to report.
 #define HZB_GUARD(c)                                                 \
     do {                                                             \
         if (!(c)) return HZB_EINVAL;                                 \
         if (cudaSetDevice((c)->opt.device) != cudaSuccess)           \
             return fail((c), HZB_ECUDA, "cudaSetDevice failed");     \
+        cudaGetLastError();                                          \
     } while (0)
 
 extern "C" {
@@ -107,7 +110,8 @@ hzb_status hzb_destroy(hzb_ctx *c)
 {
     if (!c) return HZB_EINVAL;
     cudaSetDevice(c->opt.device);
-    cudaStreamSynchronize(c->stream);
+    // the caller's stream may already be gone: wait for the whole device instead
+    cudaDeviceSynchronize();
     for (ShapeDev *s : c->shapes) {
         s->ring.release(); s->body_offs.release(); s->A64.release(); s->S64.release(); s->S32.release();
         delete s;
@@ -126,6 +130,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
+    cudaGetLastError();
     return HZB_OK;
 }
 

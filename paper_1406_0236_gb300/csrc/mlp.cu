@@ -294,12 +294,13 @@ hzb_status hzb_mlp_destroy(hzb_mlp *m)
 {
     if (!m) return HZB_EINVAL;
     cudaSetDevice(m->device);
-    cudaStreamSynchronize(m->stream);
+    cudaDeviceSynchronize();              // the caller's stream may already be gone
     for (float *p : m->act_a) cudaFree(p);
     for (float *p : m->act_h) cudaFree(p);
     cudaFree(m->gbuf0); cudaFree(m->gbuf1); cudaFree(m->xbuf); cudaFree(m->tbuf);
     cudaFree(m->master); cudaFree(m->grad); cudaFree(m->m); cudaFree(m->v); cudaFree(m->wbf); cudaFree(m->loss);
     delete m;
+    cudaGetLastError();
     return HZB_OK;
 }
 

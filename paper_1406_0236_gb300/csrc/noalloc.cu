@@ -61,6 +61,7 @@ extern "C" hzb_status hzb_local_inverse_noalloc(hzb_ctx *c, int R, const double 
 {
     if (!c) return HZB_EINVAL;
     if (cudaSetDevice(c->opt.device) != cudaSuccess) return fail(c, HZB_ECUDA, "cudaSetDevice failed");
+    cudaGetLastError();                   // a stale error of an unrelated earlier call is not ours
     if (c->state != 3) return fail(c, HZB_ESTATE, "scattering matrices not built");
     if (R < 1 || R > 4096 || !y || !tau) return fail(c, HZB_EINVAL, "bad R or null pointer");
     if (alpha != 0.0 && !sigma) return fail(c, HZB_EINVAL, "sigma is required when alpha != 0");

@@ -205,6 +205,7 @@ def test_graph_replay_and_chunked_steps_match_plain_gmres(precision):
             assert st.converged and st.iterations == st0.iterations
             got = s.get_density()
             assert rel_l2(got, ref) < (1e-12 if precision == 0 else 1e-9)
+        s.close()                           # before its stream goes away
     torch.cuda.synchronize()
 
 

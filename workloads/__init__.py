@@ -19,6 +19,7 @@ from dataclasses import dataclass, field
 from typing import List
 
 import numpy as np
+from scipy.spatial import cKDTree
 
 SPHERE = 0
 SPHEROID = 1
@@ -138,6 +139,18 @@ def _surface_samples(body: Body, n: int = 1500) -> np.ndarray:
     return p @ body.rot.T + body.center
 
 
+def gap_to(bodies: List[Body], cand: Body, samples=None) -> float:
+    """Smallest envelope distance between `cand` and any of `bodies`."""
+    pc = _surface_samples(cand)
+    best = np.inf
+    for q, b in enumerate(bodies):
+        if np.linalg.norm(b.center - cand.center) > b.shape.bounding_radius() + cand.shape.bounding_radius() + best:
+            continue
+        pb = samples[q] if samples is not None else _surface_samples(b)
+        best = min(best, float(cKDTree(pb).query(pc)[0].min()))
+    return best
+
+
 def min_gap(bodies: List[Body]) -> float:
     pts = [_surface_samples(b) for b in bodies]
     best = np.inf
@@ -232,6 +245,7 @@ def mixed48(seed=DEFAULT_SEED, n_rhs=16, k=6.0, n_panels=24, gl_order=16, n_mode
         OPEN_SHELL: ShapeSpec(OPEN_SHELL, (1.0, 0.8, np.pi / 3.0, 0.1), n_panels, gl_order, n_modes),
     }
     bodies: List[Body] = []
+    samples = []
     idx = 0
     for ix in range(4):
         for iy in range(4):
@@ -241,11 +255,13 @@ def mixed48(seed=DEFAULT_SEED, n_rhs=16, k=6.0, n_panels=24, gl_order=16, n_mode
                     c = base + rng.uniform(-0.5, 0.5, 3)
                     rot = rotation_taking_z_to(rng.standard_normal(3))
                     cand = Body(shapes[int(kinds[idx])], c, rot)
-                    if not bodies or min_gap(bodies + [cand]) >= min_gap_required:
+                    # placed bodies already keep the gap among themselves
+                    if not bodies or gap_to(bodies, cand, samples) >= min_gap_required:
                         break
                 else:
                     raise RuntimeError("could not place body %d with the required gap" % idx)
                 bodies.append(cand)
+                samples.append(_surface_samples(cand))
                 idx += 1
     return Workload("mixed48_shells", bodies, k, k, uniform_directions(n_rhs, seed + 11),
                     gmres_tol=1e-10)
