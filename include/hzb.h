@@ -171,6 +171,12 @@ hzb_status hzb_autotune(hzb_ctx *ctx, int R, int which, double best_ms[2]);
  *                on when N x R <= 4e6; needs a non-default stream). */
 hzb_status hzb_set_execution(hzb_ctx *ctx, int check_every, int use_graphs);
 
+/* Engine of the FP32 per-mode scattering GEMM (Eq. (singleinverse) step (2)):
+ * 0 = CUDA cores; 1 = tensor cores, TF32 with a three-term hi/lo split and FP32
+ * accumulation (about FP32 accuracy); -1 (default) = tensor cores when a shape's
+ * panel has at least 32 columns (2 x bodies of the shape x right-hand sides). */
+hzb_status hzb_set_modal_engine(hzb_ctx *ctx, int engine);
+
 /* Copy A~_p (which = 0) or S_p (which = 1) of the shape of body `body`, mode p in
  * 0..M, to host out (N_G x N_G complex, row-major). */
 hzb_status hzb_get_modal_block(hzb_ctx *ctx, int body, int p, int which, double *out);

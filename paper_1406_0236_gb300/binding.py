@@ -128,6 +128,7 @@ def lib():
         "hzb_autotune": (i, [p, i, i, p]),
         "hzb_local_inverse_noalloc": (i, [p, i, p, p, d, d, p]),
         "hzb_set_execution": (i, [p, i, i]),
+        "hzb_set_modal_engine": (i, [p, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -195,6 +196,10 @@ class Solver:
     def set_execution(self, check_every: int = 0, use_graphs: int = -1):
         """GMRES steps between host checks (0 = auto) and CUDA graphs (-1 auto, 0 off, 1 on)."""
         self._check(lib().hzb_set_execution(self._h, int(check_every), int(use_graphs)))
+
+    def set_modal_engine(self, engine: int):
+        """FP32 modal GEMM engine: 0 CUDA cores, 1 tensor cores (TF32 x 3), -1 auto."""
+        self._check(lib().hzb_set_modal_engine(self._h, int(engine)))
 
     def set_options(self, **kw):
         for k_, v in kw.items():

@@ -154,6 +154,7 @@ struct hzb_ctx {
     // GMRES execution: steps between host checks (0 = auto) and CUDA graphs (-1 auto, 0 off, 1 on)
     int check_every = 0;
     int use_graphs = -1;
+    int modal_engine = -1;                     // FP32 modal GEMM: -1 auto, 0 CUDA cores, 1 tensor cores
     std::vector<cudaGraphExec_t> gexec;        // captured Arnoldi step j
     std::vector<long long> glaunch;            // kernels per captured step
     unsigned char gkey[256];

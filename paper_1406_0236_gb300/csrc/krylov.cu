@@ -489,13 +489,14 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
     return HZB_OK;
 }
 
-// max_r ||b - A x|| / ||b|| with the FP64 operator; r_out (N x R) receives b - A x
-static hzb_status true_residual(hzb_ctx *c, int R, const double2 *b, const double2 *x, double2 *r_out,
-                                std::vector<double> &rel)
+// ||b - A x|| / ||b|| per right-hand side with the operator of the given precision;
+// r_out (N x R) receives b - A x
+static hzb_status residual_with(hzb_ctx *c, int R, const double2 *b, const double2 *x, double2 *r_out,
+                                std::vector<double> &rel, int precision)
 {
     const size_t NR = (size_t)c->N * R;
     hzb_status st;
-    if ((st = apply_op(c, R, x, r_out, c->opt.residual))) return st;
+    if ((st = apply_op(c, R, x, r_out, precision))) return st;
     axpby_kernel<<<nblocks((long long)NR), 256, 0, c->stream>>>((long long)NR, 1.0, b, -1.0, r_out, r_out);
     c->launches++;
     DevBuf<double2> &tmp = c->tiny;
@@ -508,6 +509,13 @@ static hzb_status true_residual(hzb_ctx *c, int R, const double2 *b, const doubl
     rel.assign(R, 0.0);
     for (int r = 0; r < R; ++r) rel[r] = h[R + r].x > 0 ? std::sqrt(std::max(h[r].x, 0.0) / h[R + r].x) : 0.0;
     return HZB_OK;
+}
+
+// the refinement residual: FP64 operator (or double-float inter-body sum)
+static hzb_status true_residual(hzb_ctx *c, int R, const double2 *b, const double2 *x, double2 *r_out,
+                                std::vector<double> &rel)
+{
+    return residual_with(c, R, b, x, r_out, rel, c->opt.residual);
 }
 
 hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *stats)
@@ -547,7 +555,10 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
         }
         std::vector<double> rel(R, 1.0);
         if (x0) {
-            if ((st = true_residual(c, R, bbuf.ptr, x, rbuf.ptr, rel))) { cleanup(); return st; }
+            // A guess starts refinement with the inner (FP32) operator's residual: the first
+            // correction then lands on the FP32-operator solution, as from a zero start, and
+            // the high-precision residuals that follow are the same in number.
+            if ((st = residual_with(c, R, bbuf.ptr, x, rbuf.ptr, rel, HZB_PREC_MIXED_FP32))) { cleanup(); return st; }
         } else {
             if ((st = vec_zero(c, x, NR)) || (st = vec_copy(c, rbuf.ptr, bbuf.ptr, NR))) { cleanup(); return st; }
         }

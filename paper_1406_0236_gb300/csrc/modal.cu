@@ -20,6 +20,9 @@ template <> struct C2<float> { typedef float2 t; };
 
 static const int DFT_THREADS = 128;
 
+void launch_modal_gemm_tc(hzb_ctx *c, int n, int nc, int modes, const float2 *A, const float2 *B, float2 *C);
+
+
 // One block per (body of the shape, ring).  y is N x R (FP64); out is the shape's
 // panel array (M+1) x NG x ncols in precision T.
 template <typename T>
@@ -115,6 +118,18 @@ __global__ void dft_inverse_kernel(int NG, int NF, int R, int ncols, const long 
     }
 }
 
+// The DFT kernels' dynamic shared memory: beyond the default 48 KB, raise their
+// limit once to the largest size any call uses (200 KB).  The limit is never set
+// lower, so calls with different sizes (and both D^{-1} entry points) cannot
+// invalidate each other's launches.
+template <typename T>
+static void dft_smem_limit(size_t bytes)
+{
+    if (bytes <= 48 * 1024) return;
+    cudaFuncSetAttribute(dft_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(dft_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 // Batched complex GEMM C[p] = A[p] B[p], A: n x n, B and C: n x nc, row-major.
 // 32 x 32 output tile per block, 256 threads, 2 x 2 outputs per thread, K step 16.
 template <typename T>
@@ -205,12 +220,14 @@ static hzb_status local_inverse_t(hzb_ctx *c, int R, const double2 *y, const dou
         const long long *doff = sd.body_offs.ptr;        // first node of each body of the shape
         size_t smem = (size_t)NF * (R + 1) * sizeof(double2);
         if (smem > 200 * 1024) return fail(c, HZB_EINVAL, "n_modes * R too large for the modal apply");
-        if (smem > 48 * 1024) {        // opt-in beyond the default 48 KB (not needed, and not issued, below it)
-            cudaFuncSetAttribute(dft_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(dft_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        }
+        dft_smem_limit<T>(smem);
         dft_forward_kernel<T><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, y, yh);
-        modal_gemm_kernel<T><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(NG, ncols, S, yh, th);
+        // FP32 path: tensor cores (TF32 x 3) once the panels are wide enough to fill them
+        const bool tc = (sizeof(T) == 4) && (c->modal_engine == 1 || (c->modal_engine < 0 && ncols >= 32));
+        if (tc)
+            launch_modal_gemm_tc(c, NG, ncols, M + 1, (const float2 *)S, (const float2 *)yh, (float2 *)th);
+        else
+            modal_gemm_kernel<T><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(NG, ncols, S, yh, th);
         dft_inverse_kernel<T><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, th, sigma,
                                                                                alpha, beta, tau);
         c->launches += 3;
@@ -250,8 +267,7 @@ hzb_status local_inverse64_scratch(hzb_ctx *c, int R, const double2 *y, const do
         const long long *doff = sd.body_offs.ptr;
         size_t smem = (size_t)NF * (R + 1) * sizeof(double2);
         if (smem > 200 * 1024) return fail(c, HZB_EINVAL, "n_modes * R too large for the modal apply");
-        cudaFuncSetAttribute(dft_forward_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(dft_inverse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dft_smem_limit<double>(smem);
         dft_forward_kernel<double><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, y, yh);
         modal_gemm_kernel<double><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(
             NG, ncols, sd.S64.ptr, yh, th);
@@ -270,6 +286,125 @@ size_t modal_panel_elems(const hzb_ctx *c, int R)
     for (const ShapeDev *sp : c->shapes)
         mx = std::max(mx, (size_t)(sp->geom.M + 1) * sp->geom.NG * (2 * sp->bodies.size() * (size_t)R));
     return mx;
+}
+
+}  // namespace hzb
+
+namespace hzb {
+
+// ---------------------------------------------------------------- tensor-core modal GEMM
+// FP32 path, many columns: C = A B for complex A (n x n) and B (n x nc) through the
+// real embedding  [Cr; Ci] = [[Ar, -Ai], [Ai, Ar]] [Br; Bi]  (a 2n x 2n x nc real GEMM)
+// on the tensor cores in TF32 with a three-term split, x = hi + lo with hi, lo TF32:
+// A B ~ Ahi Bhi + Ahi Blo + Alo Bhi, FP32 accumulation (about FP32 accuracy).
+// mma.sync m16n8k8; 64 x 64 output tile per CTA, 4 warps of 32 x 32, K step 32.
+
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float *d, const uint32_t *a, const uint32_t *b)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128)
+modal_gemm_tc_kernel(int n, int nc, const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C)
+{
+    __shared__ float As[64][33];
+    __shared__ float Bs[32][72];
+    const int p = blockIdx.z;
+    const float2 *Ap = A + (size_t)p * n * n;
+    const float2 *Bp = B + (size_t)p * n * nc;
+    float2 *Cp = C + (size_t)p * n * nc;
+    const int n2 = 2 * n;
+    const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    for (int k0 = 0; k0 < n2; k0 += 32) {
+        for (int e = tid; e < 64 * 32; e += 128) {
+            const int r = e >> 5, kk = e & 31;
+            const int R = row0 + r, K = k0 + kk;
+            float v = 0.f;
+            if (R < n2 && K < n2) {
+                const float2 a = Ap[(size_t)(R < n ? R : R - n) * n + (K < n ? K : K - n)];
+                v = (R < n) ? (K < n ? a.x : -a.y) : (K < n ? a.y : a.x);
+            }
+            As[r][kk] = v;
+        }
+        for (int e = tid; e < 32 * 64; e += 128) {
+            const int kk = e >> 6, c = e & 63;
+            const int K = k0 + kk, col = col0 + c;
+            float v = 0.f;
+            if (K < n2 && col < nc) {
+                const float2 b = Bp[(size_t)(K < n ? K : K - n) * nc + col];
+                v = (K < n) ? b.x : b.y;
+            }
+            Bs[kk][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 8) {
+            uint32_t ah[2][4], al[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = wm * 32 + mt * 16 + g;
+                const float v[4] = {As[r][kk + t], As[r + 8][kk + t], As[r][kk + t + 4], As[r + 8][kk + t + 4]};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    ah[mt][q] = to_tf32(v[q]);
+                    al[mt][q] = to_tf32(v[q] - __uint_as_float(ah[mt][q]));
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int c = wn * 32 + nt * 8 + g;
+                const float v0 = Bs[kk + t][c], v1 = Bs[kk + t + 4][c];
+                uint32_t bh[2] = {to_tf32(v0), to_tf32(v1)};
+                uint32_t bl[2] = {to_tf32(v0 - __uint_as_float(bh[0])), to_tf32(v1 - __uint_as_float(bh[1]))};
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma_tf32(acc[mt][nt], al[mt], bh);
+                    mma_tf32(acc[mt][nt], ah[mt], bl);
+                    mma_tf32(acc[mt][nt], ah[mt], bh);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int R = row0 + wm * 32 + mt * 16 + g + 8 * h;
+                const int col = col0 + wn * 32 + nt * 8 + 2 * t;
+                if (R >= n2) continue;
+                float *base = (R < n) ? &Cp[(size_t)R * nc].x : &Cp[(size_t)(R - n) * nc].y;
+                if (col < nc) base[2 * col] = acc[mt][nt][2 * h];
+                if (col + 1 < nc) base[2 * (col + 1)] = acc[mt][nt][2 * h + 1];
+            }
+}
+
+void launch_modal_gemm_tc(hzb_ctx *c, int n, int nc, int modes, const float2 *A, const float2 *B, float2 *C)
+{
+    dim3 grid((nc + 63) / 64, (2 * n + 63) / 64, modes);
+    modal_gemm_tc_kernel<<<grid, 128, 0, c->stream>>>(n, nc, A, B, C);
 }
 
 }  // namespace hzb

@@ -3,7 +3,7 @@
     python -m paper_1406_0236_gb300.profile_case --workload spheroids8_258560 \
         --op interbody32 --repeat 2 [--rhs 1] [--autotune]
 
-ops: interbody32, interbody64 (B sigma), local_inverse64, local_inverse32 (D^{-1} y),
+ops: interbody32, interbody64, interbody_df (B sigma), local_inverse64, local_inverse32 (D^{-1} y),
 apply64, apply32, solve_mixed, solve_fp64.  Prints the mean time per call measured
 with CUDA events.  Inputs are seeded random densities (ops) or the workload's plane
 waves (solves).
@@ -36,14 +36,14 @@ def main():
     from paper_1406_0236_gb300 import Options, Solver
 
     wl = W.by_name(args.workload)
-    prec = 1 if args.op.endswith("32") or args.op == "solve_mixed" else 0
-    s = Solver.from_workload(wl, Options(precision=prec, gmres_tol=1e-8, verify_final=0),
+    prec = 1 if args.op.endswith("32") or args.op == "solve_mixed" else (2 if args.op.endswith("_df") else 0)
+    s = Solver.from_workload(wl, Options(precision=min(prec, 1), gmres_tol=1e-8, verify_final=0),
                              stream=torch.cuda.current_stream().cuda_stream)
     needs_build = not args.op.startswith("interbody")
     if needs_build:
         s.build_scattering_matrices()
     if args.autotune:
-        s.autotune(args.rhs, 1 if prec else 2)
+        s.autotune(args.rhs, 1 if prec == 1 else 2)
     N = s.N
     g = torch.Generator(device="cuda").manual_seed(7)
     x = torch.randn((N, args.rhs), dtype=torch.complex128, device="cuda", generator=g)

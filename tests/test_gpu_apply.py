@@ -50,6 +50,20 @@ def test_interbody_fp32(pair, R):
     assert rel_l2(got, ref) < 2e-6
 
 
+@pytest.mark.parametrize("R", [1, 3, 24])
+def test_local_inverse_tensor_cores(pair, R):
+    """FP32 modal GEMM on the tensor cores (TF32 with a three-term split)."""
+    s, P = pair
+    y = rand_c((P.N, R), 131 + R)
+    ref = P.local_inverse(y)
+    s.set_modal_engine(1)
+    try:
+        got = s.local_inverse(y, precision=1)
+    finally:
+        s.set_modal_engine(-1)
+    assert rel_l2(got, ref) < 1e-5
+
+
 @pytest.mark.parametrize("R", [1, 4])
 def test_local_inverse(pair, R):
     s, P = pair
