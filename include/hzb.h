@@ -177,6 +177,13 @@ hzb_status hzb_set_execution(hzb_ctx *ctx, int check_every, int use_graphs);
  * panel has at least 32 columns (2 x bodies of the shape x right-hand sides). */
 hzb_status hzb_set_modal_engine(hzb_ctx *ctx, int engine);
 
+/* Engine of the FP32 inter-body sum (Sec. 3.3): 0 = CUDA cores (one pair kernel per
+ * target-source pair, complex multiply-accumulate per right-hand side); 1 = tensor
+ * cores: pair kernels generated on the CUDA cores, the contraction with the densities
+ * of up to 32 right-hand sides on the tensor cores (TF32, three-term split, FP32
+ * accumulation); -1 (default) = tensor cores when R >= 16. */
+hzb_status hzb_set_interbody_engine(hzb_ctx *ctx, int engine);
+
 /* Copy A~_p (which = 0) or S_p (which = 1) of the shape of body `body`, mode p in
  * 0..M, to host out (N_G x N_G complex, row-major). */
 hzb_status hzb_get_modal_block(hzb_ctx *ctx, int body, int p, int which, double *out);

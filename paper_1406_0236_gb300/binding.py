@@ -129,6 +129,7 @@ def lib():
         "hzb_local_inverse_noalloc": (i, [p, i, p, p, d, d, p]),
         "hzb_set_execution": (i, [p, i, i]),
         "hzb_set_modal_engine": (i, [p, i]),
+        "hzb_set_interbody_engine": (i, [p, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -200,6 +201,10 @@ class Solver:
     def set_modal_engine(self, engine: int):
         """FP32 modal GEMM engine: 0 CUDA cores, 1 tensor cores (TF32 x 3), -1 auto."""
         self._check(lib().hzb_set_modal_engine(self._h, int(engine)))
+
+    def set_interbody_engine(self, engine: int):
+        """FP32 inter-body sum engine: 0 CUDA cores, 1 tensor cores (R >= 1), -1 auto (R >= 16)."""
+        self._check(lib().hzb_set_interbody_engine(self._h, int(engine)))
 
     def set_options(self, **kw):
         for k_, v in kw.items():

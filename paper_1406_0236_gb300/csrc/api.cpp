@@ -466,6 +466,14 @@ hzb_status hzb_set_modal_engine(hzb_ctx *c, int engine)
     return HZB_OK;
 }
 
+hzb_status hzb_set_interbody_engine(hzb_ctx *c, int engine)
+{
+    if (!c) return HZB_EINVAL;
+    if (engine < -1 || engine > 1) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1}");
+    c->nbody_engine = engine;
+    return HZB_OK;
+}
+
 hzb_status hzb_far_field(hzb_ctx *c, int n, const double *xhat, double *out)
 {
     return point_query(c, n, xhat, out, true);

@@ -155,6 +155,8 @@ struct hzb_ctx {
     int check_every = 0;
     int use_graphs = -1;
     int modal_engine = -1;                     // FP32 modal GEMM: -1 auto, 0 CUDA cores, 1 tensor cores
+    int nbody_engine = -1;                     // FP32 inter-body sum: -1 auto (tensor cores for R >= 16), 0, 1
+    int tunetc_split = 0;
     std::vector<cudaGraphExec_t> gexec;        // captured Arnoldi step j
     std::vector<long long> glaunch;            // kernels per captured step
     unsigned char gkey[256];
@@ -183,6 +185,8 @@ hzb_status build_shape_matrices(hzb_ctx *c, ShapeDev &s);
 hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   // nbody_df.cu
+hzb_status interbody_tc(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);  // nbody_tc.cu
+void split_reduce_f2(hzb_ctx *c, size_t n, int nsplit, const float2 *part, double2 *y);
 hzb_status interbody64_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit);
 hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit);
 int default_nsplit(hzb_ctx *c, int R, int tpt);

@@ -231,6 +231,11 @@ __global__ void split_reduce_kernel(size_t n, int nsplit, const P *__restrict__ 
     y[e] = make_double2(sx, sy);
 }
 
+void split_reduce_f2(hzb_ctx *c, size_t n, int nsplit, const float2 *part, double2 *y)
+{
+    split_reduce_kernel<float2><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, nsplit, part, y);
+}
+
 // Launch shape of the inter-body kernels.
 static int rc_of(int R) { return R == 1 ? 1 : (R <= 4 ? 4 : 8); }
 
@@ -363,6 +368,15 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 {
+    // many right-hand sides: contraction on the tensor cores (nbody_tc.cu)
+    if (c->nbody_engine == 1 || (c->nbody_engine < 0 && R >= 16)) {
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
+        const int rc = (R >= 32) ? 32 : 16;
+        const long long ctas = (long long)c->n_tblocks * 4 * ((R + rc - 1) / rc);
+        int ns = c->tunetc_split > 0 ? c->tunetc_split : (int)std::max<long long>(1, (4LL * sms + ctas - 1) / ctas);
+        return interbody_tc(c, R, sigma, y, std::min(ns, 64));
+    }
     int tpt = c->tune32_tpt > 0 ? c->tune32_tpt : 4;
     int ns = c->tune32_split > 0 ? c->tune32_split : default_nsplit(c, R, tpt);
     return interbody32_cfg(c, R, sigma, y, tpt, ns);

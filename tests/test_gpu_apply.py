@@ -134,3 +134,17 @@ def test_spheroids_258560_double_float_rows():
     ref = P.interbody(sig, targets=rows)
     ydf = s.interbody(sig, precision=2)
     assert np.abs(ydf[rows] - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("R", [1, 5, 16, 40])
+def test_interbody_tensor_cores(pair, R):
+    """FP32 inter-body sum with the contraction on the tensor cores (TF32, 3-term split)."""
+    s, P = pair
+    sig = rand_c((P.N, R), 141 + R)
+    ref = P.interbody(sig)
+    s.set_interbody_engine(1)
+    try:
+        got = s.interbody(sig, precision=1)
+    finally:
+        s.set_interbody_engine(-1)
+    assert rel_l2(got, ref) < 5e-6

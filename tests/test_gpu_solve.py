@@ -218,3 +218,19 @@ def test_mixed_with_double_float_residual(two_spheres_ref):
     st = s.solve_plane_waves(wl.directions)
     assert st.converged and st.n_nbodydf >= 1 and st.n_nbody64 == 0
     assert rel_l2(s.get_density()[:, 0], sig_ref) <= 1e-10
+
+
+def test_mixed_batch_on_tensor_cores(two_spheres_ref):
+    """20 right-hand sides: the inner FP32 applies take the tensor-core inter-body path
+    and the FP32 modal GEMM on tensor cores; the refined densities meet the FP64 bar."""
+    from oracle import fields, gmres
+    wl, P, _ = two_spheres_ref
+    dirs = W.uniform_directions(20, 77)
+    s = gpu_solver(wl, precision=1, tol=1e-11)
+    st = s.solve_plane_waves(dirs)
+    assert st.converged
+    got = s.get_density()
+    for r in (0, 13):
+        v = fields.plane_wave(P.nodes.x, dirs[r:r + 1], wl.k)[:, 0]
+        ref = gmres(P.apply, P.rhs(v), 1e-13).x
+        assert rel_l2(got[:, r], ref) <= 1e-9
