@@ -156,8 +156,10 @@ hzb_status hzb_build_scattering_matrices(hzb_ctx *ctx);
 /* Autotuner of the inter-body kernels' launch shape (targets per thread, source
  * chunks per target block) for R right-hand sides: times each candidate with CUDA
  * events on the context's stream and keeps the fastest for later calls.
- * which: bit 0 = FP32 kernel, bit 1 = FP64 kernel.  best_ms (may be NULL): the
- * fastest time per launch [FP32, FP64].  Not part of the paper: a GB300 tuning aid. */
+ * which: bit 0 = FP32 kernel, bit 1 = FP64 kernel.  For the FP32 sum with R >= 8 and
+ * the engine on automatic (hzb_set_interbody_engine -1) the tensor-core contraction
+ * is timed as well and, for this R, the faster engine is kept.  best_ms (may be NULL):
+ * the fastest time per launch [FP32, FP64].  Not part of the paper: a GB300 tuning aid. */
 hzb_status hzb_autotune(hzb_ctx *ctx, int R, int which, double best_ms[2]);
 
 /* GMRES execution controls (no effect on results beyond rounding of where a
@@ -178,11 +180,23 @@ hzb_status hzb_set_execution(hzb_ctx *ctx, int check_every, int use_graphs);
 hzb_status hzb_set_modal_engine(hzb_ctx *ctx, int engine);
 
 /* Engine of the FP32 inter-body sum (Sec. 3.3): 0 = CUDA cores (one pair kernel per
- * target-source pair, complex multiply-accumulate per right-hand side); 1 = tensor
- * cores: pair kernels generated on the CUDA cores, the contraction with the densities
- * of up to 32 right-hand sides on the tensor cores (TF32, three-term split, FP32
- * accumulation); -1 (default) = tensor cores when R >= 16. */
+ * target-source pair, complex multiply-accumulate per right-hand side; the kernel
+ * variant the autotuner picked, else the packed-pair one); 1 = tensor cores: pair
+ * kernels generated on the CUDA cores, the contraction with the densities of up to 32
+ * right-hand sides on the tensor cores (TF32, three-term split, FP32 accumulation);
+ * 2 = CUDA cores, scalar FP32 kernel; 3 = CUDA cores, packed-pair kernel (two sources
+ * per f32x2 instruction); -1 (default) = tensor cores when R >= 16 (or as tuned),
+ * else as 0.  Returns HZB_EINVAL for other values. */
 hzb_status hzb_set_interbody_engine(hzb_ctx *ctx, int engine);
+
+/* Engine of the FP64 inter-body sum (Sec. 3.3): 0 = one-directional kernel (each
+ * ordered pair on its own, source chunks added in a fixed order: bit-reproducible);
+ * 1 = pair-symmetric kernel: each unordered pair of nodes on different bodies is
+ * evaluated once for both directions (r, 1/r and e^{ikr} are shared), about 1.5x
+ * fewer FP64 operations; both directions are added into y with FP64 atomics, so runs
+ * agree to rounding but not bit for bit; -1 (default) = 1.  Returns HZB_EINVAL for
+ * other values.  Not part of the paper: a GB300 choice (FP64 runs at 1/64 rate). */
+hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *ctx, int engine);
 
 /* Copy A~_p (which = 0) or S_p (which = 1) of the shape of body `body`, mode p in
  * 0..M, to host out (N_G x N_G complex, row-major). */

@@ -130,6 +130,7 @@ def lib():
         "hzb_set_execution": (i, [p, i, i]),
         "hzb_set_modal_engine": (i, [p, i]),
         "hzb_set_interbody_engine": (i, [p, i]),
+        "hzb_set_fp64_interbody_engine": (i, [p, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -203,8 +204,13 @@ class Solver:
         self._check(lib().hzb_set_modal_engine(self._h, int(engine)))
 
     def set_interbody_engine(self, engine: int):
-        """FP32 inter-body sum engine: 0 CUDA cores, 1 tensor cores (R >= 1), -1 auto (R >= 16)."""
+        """FP32 inter-body sum engine: 0 CUDA cores, 1 tensor cores, 2 scalar CUDA-core kernel,
+        3 packed-pair CUDA-core kernel, -1 auto (tensor cores for R >= 16 or as tuned)."""
         self._check(lib().hzb_set_interbody_engine(self._h, int(engine)))
+
+    def set_fp64_interbody_engine(self, engine: int):
+        """FP64 inter-body sum engine: 0 one-directional, 1 pair-symmetric, -1 auto (1)."""
+        self._check(lib().hzb_set_fp64_interbody_engine(self._h, int(engine)))
 
     def set_options(self, **kw):
         for k_, v in kw.items():

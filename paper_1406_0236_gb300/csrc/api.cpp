@@ -122,7 +122,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     c->yhat32.release(); c->that32.release(); c->s_b.release(); c->s_r.release(); c->s_d.release();
     c->io_in.release(); c->io_out.release(); c->io_small.release(); c->tiny.release(); c->sol.release();
     c->red.release(); c->krylov.release(); c->small.release();
-    c->sctab.release(); c->nb_part64.release(); c->nb_part32.release();
+    c->sctab.release(); c->nb_part64.release(); c->nb_part32.release(); c->sig32.release(); c->blockpairs.release();
     c->dfa.release(); c->dfb.release(); c->dfc.release(); c->dftab.release();
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
     release_graphs(c);
@@ -466,10 +466,18 @@ hzb_status hzb_set_modal_engine(hzb_ctx *c, int engine)
     return HZB_OK;
 }
 
-hzb_status hzb_set_interbody_engine(hzb_ctx *c, int engine)
+hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *c, int engine)
 {
     if (!c) return HZB_EINVAL;
     if (engine < -1 || engine > 1) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1}");
+    c->nbody64_engine = engine;
+    return HZB_OK;
+}
+
+hzb_status hzb_set_interbody_engine(hzb_ctx *c, int engine)
+{
+    if (!c) return HZB_EINVAL;
+    if (engine < -1 || engine > 3) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1, 2, 3}");
     c->nbody_engine = engine;
     return HZB_OK;
 }

@@ -267,11 +267,13 @@ static hzb_status ensure_pinned(hzb_ctx *c, size_t n)
 
 // Pointers and sizes a captured Arnoldi step depends on: a change invalidates the graphs.
 struct GraphKey {
-    const void *p[14];
+    static const int NP = 21;
+    const void *p[NP];
     long long N;
-    int R, m, precision, tpt32, split32, tpt64, split64;
+    int R, m, precision, tpt32, split32, tpt64, split64, modal_engine, nbody_engine, splittc, tc32, x2, engine64;
     bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
+static_assert(sizeof(GraphKey) <= sizeof(((hzb_ctx *)nullptr)->gkey), "graph key storage");
 
 static void drop_graphs(hzb_ctx *c)
 {
@@ -377,17 +379,24 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
     // CUDA graphs need a capturable (non-legacy) stream; auto = small problems only
     bool graphs = c->use_graphs > 0 || (c->use_graphs < 0 && (long long)NR <= 4000000);
     if (c->stream == nullptr) graphs = false;
+    // The key is taken right before each captured step, after the eager step 0 has
+    // made every allocation the step needs, so it names the buffers the graph uses.
     GraphKey graph_key;
-    std::memset(&graph_key, 0, sizeof(graph_key));
-    {
-        const void *ps[14] = {V, w, c->small.ptr, c->w_c.ptr, c->w_d.ptr, c->yhat64.ptr, c->that64.ptr,
-                              c->yhat32.ptr, c->that32.ptr, c->nb_part32.ptr, c->nb_part64.ptr, c->sctab.ptr,
-                              (const void *)c->stream, c->tblocks.ptr};
+    auto make_key = [&]() {
+        std::memset(&graph_key, 0, sizeof(graph_key));
+        const void *ps[GraphKey::NP] = {V, w, c->small.ptr, c->w_c.ptr, c->w_d.ptr, c->yhat64.ptr, c->that64.ptr,
+                                        c->yhat32.ptr, c->that32.ptr, c->nb_part32.ptr, c->nb_part64.ptr,
+                                        c->sctab.ptr, (const void *)c->stream, c->tblocks.ptr, c->sig32.ptr,
+                                        c->w_a.ptr, c->w_b.ptr, c->f_a.ptr, c->f_b.ptr, c->dfa.ptr,
+                                        c->blockpairs.ptr};
         std::memcpy(graph_key.p, ps, sizeof(ps));
         graph_key.N = N; graph_key.R = R; graph_key.m = m; graph_key.precision = precision;
         graph_key.tpt32 = c->tune32_tpt; graph_key.split32 = c->tune32_split;
         graph_key.tpt64 = c->tune64_tpt; graph_key.split64 = c->tune64_split;
-    }
+        graph_key.modal_engine = c->modal_engine; graph_key.nbody_engine = c->nbody_engine;
+        graph_key.splittc = c->tunetc_split; graph_key.tc32 = c->tune32_tc * 1000000 + c->tune32_tc_R;
+        graph_key.x2 = c->tune32_x2; graph_key.engine64 = c->nbody64_engine;
+    };
     if (x_is_zero && (st = vec_zero(c, x, NR))) return st;
     // ||b|| once
     if ((st = cdots(c, R, 1, b, 0, b, s.nrm2))) return st;
@@ -445,6 +454,7 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
             const int q = std::min(every, std::min(m - j, maxit - total));
             for (int t = 0; t < q; ++t, ++j, ++total) {
                 if (graphs && j > 0) {
+                    make_key();
                     if ((st = graph_step(c, j, arnoldi_step, graph_key))) return st;
                 } else if ((st = arnoldi_step(j))) {
                     return st;

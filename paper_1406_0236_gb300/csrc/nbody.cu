@@ -18,53 +18,34 @@
 #include <vector>
 
 #include "hzb_internal.h"
+#include "f32x2.cuh"
+#include "fp64_pair.cuh"
 #include "kernel_math.cuh"
 
 namespace hzb {
 
 static const int TBLOCK = 512;          // targets per TargetBlock (make_nodes)
-static const int SC_N = 256;            // entries of the FP64 cos/sin table
-
-// FP64 e^{ix} for x >= 0 (table-driven, after Tang): t = x 256/(2pi), j = rint(t),
-// delta = (t - j) 2pi/256 in [-pi/256, pi/256]; (cos, sin)(delta) by their Taylor
-// series to delta^8 / delta^7 (truncation < 2e-20); (cos, sin)(x) by angle addition
-// with the tabulated (cos, sin)(2 pi j / 256).  Reduction error ~ x * 1.1e-16 rad.
-__device__ inline void sincos_table(double x, const double2 *__restrict__ tab, double &s, double &c)
-{
-    const double t = x * (SC_N / (2.0 * M_PI));
-    const double j = rint(t);
-    const double d = (t - j) * (2.0 * M_PI / SC_N);
-    const double d2 = d * d;
-    const double sd = d * fma(d2, fma(d2, fma(d2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
-    const double cd = fma(d2, fma(d2, fma(d2, fma(d2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
-    const double2 cs = tab[((long long)j) & (SC_N - 1)];
-    c = fma(cs.x, cd, -cs.y * sd);
-    s = fma(cs.y, cd, cs.x * sd);
-}
-
 // ------------------------------------------------------------------ FP64
 
 template <int RC, int TPT>
 __global__ void __launch_bounds__(TBLOCK / TPT)
 nbody64_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const double4 *__restrict__ pos,
                const double4 *__restrict__ nrm, const double2 *__restrict__ sigma, const double2 *__restrict__ sctab,
-               double k, double eta, double2 *__restrict__ y, size_t split_stride)
+               double k, double eta, double kt, double2 *__restrict__ y, size_t split_stride)
 {
     constexpr int NT = TBLOCK / TPT;
     __shared__ double4 s_pos[NT];
     __shared__ double4 s_nrm[NT];
     __shared__ double2 s_sig[NT * RC];
-    __shared__ double2 s_tab[SC_N];
     const TargetBlock tb = blocks[blockIdx.x];
     const int r0 = blockIdx.y * RC;
     const int tid = threadIdx.x;
-    for (int q = tid; q < SC_N; q += NT) s_tab[q] = sctab[q];
     double tx[TPT], ty[TPT], tz[TPT];
     double2 acc[TPT][RC];
 #pragma unroll
     for (int m = 0; m < TPT; ++m) {
         int t = tid + m * NT;
-        double4 p = (t < tb.count) ? pos[tb.start + t] : make_double4(1e30, 1e30, 1e30, 0.0);
+        double4 p = (t < tb.count) ? pos[tb.start + t] : make_double4(1e6, 1e6, 1e6, 0.0);   // padding: far, finite
         tx[m] = p.x; ty[m] = p.y; tz[m] = p.z;
 #pragma unroll
         for (int c = 0; c < RC; ++c) acc[m][c] = make_double2(0.0, 0.0);
@@ -95,14 +76,13 @@ nbody64_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, 
                 for (int m = 0; m < TPT; ++m) {
                     const double dx = tx[m] - p.x, dy = ty[m] - p.y, dz = tz[m] - p.z;
                     const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    const double ir = rsqrt(r2);
-                    const double r = r2 * ir;
+                    const double ir = rsqrt_fp64(r2);
                     const double nd = fma(n.x, dx, fma(n.y, dy, n.z * dz));
-                    const double ndir2 = nd * ir * ir;
+                    const double ndir2 = nd * (ir * ir);
                     const double A = ndir2 * ir;
                     const double B = fma(k, ndir2, eta * ir);
                     double s, c;
-                    sincos_table(k * r, s_tab, s, c);
+                    cis_turns((r2 * ir) * kt, sctab, c, s);              // e^{ikr}, kr in units of 2 pi / SC_N
                     const double gre = fma(c, A, s * B);
                     const double gim = fma(s, A, -c * B);
 #pragma unroll
@@ -133,7 +113,7 @@ nbody64_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, 
 template <int RC, int TPT>
 __global__ void __launch_bounds__(TBLOCK / TPT)
 nbody32_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pos,
-               const float4 *__restrict__ nrm, const double2 *__restrict__ sigma, float k, float eta,
+               const float4 *__restrict__ nrm, const float2 *__restrict__ sw, float k, float eta,
                float k_turns, float2 *__restrict__ ypart, double2 *__restrict__ y, size_t split_stride)
 {
     constexpr int NT = TBLOCK / TPT;
@@ -165,12 +145,9 @@ nbody32_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, 
                 const float4 n = nrm[j0 + tid];
                 s_a[tid] = make_float4(p.x, p.y, p.z, n.x);
                 s_b[tid] = make_float2(n.y, n.z);
-                const double wq = (double)p.w * HZB_INV4PI;
 #pragma unroll
-                for (int c = 0; c < RC; ++c) {
-                    double2 s = (r0 + c < R) ? sigma[(size_t)(j0 + tid) * R + r0 + c] : make_double2(0.0, 0.0);
-                    s_sig[tid * RC + c] = make_float2((float)(s.x * wq), (float)(s.y * wq));
-                }
+                for (int c = 0; c < RC; ++c)
+                    s_sig[tid * RC + c] = (r0 + c < R) ? sw[(size_t)(j0 + tid) * R + r0 + c] : make_float2(0.f, 0.f);
             }
             __syncthreads();
 #pragma unroll 2
@@ -216,6 +193,143 @@ nbody32_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, 
     }
 }
 
+// The same sum with packed FP32 pairs (f32x2.cuh): each thread takes two sources
+// (an even and an odd one of the tile) per step, so every add/mul/fma of the pair
+// kernel is one instruction for two pairs; the two accumulators of a target (even
+// and odd sources) are added at the end.  Source tiles of 128 are stored as packed
+// (even, odd) pairs; an odd tile end is padded with a far source of zero density.
+// The phase is reduced with the 1.5 * 2^23 rounding constant (valid while
+// k r / (2 pi) < 2^22 turns); rsqrt, sin and cos run per element on the
+// transcendental unit.
+static const int TS2 = 128;           // sources per tile of the packed kernel
+
+template <int RC, int TPT>
+__global__ void __launch_bounds__(TBLOCK / TPT)
+nbody32x2_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pos,
+                 const float4 *__restrict__ nrm, const float2 *__restrict__ sw, float k, float eta,
+                 float k_turns, float2 *__restrict__ ypart, double2 *__restrict__ y, size_t split_stride)
+{
+    constexpr int NT = TBLOCK / TPT;
+    constexpr int NP = TS2 / 2;                  // source pairs per tile
+    __shared__ ulonglong2 s_g[3][NP];            // {x, y}, {z, nx}, {ny, nz} of (even, odd) sources
+    __shared__ ulonglong2 s_sg[NP][RC];          // {sr, si}
+    __shared__ f2x s_ns[NP][RC];                 // -si
+    const TargetBlock tb = blocks[blockIdx.x];
+    const int r0 = blockIdx.y * RC;
+    const int tid = threadIdx.x;
+    f2x tx[TPT], ty[TPT], tz[TPT];
+    f2x ax[TPT][RC], ay[TPT][RC];
+#pragma unroll
+    for (int m = 0; m < TPT; ++m) {
+        int t = tid + m * NT;
+        float4 p = (t < tb.count) ? pos[tb.start + t] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        tx[m] = f2_splat(p.x); ty[m] = f2_splat(p.y); tz[m] = f2_splat(p.z);
+#pragma unroll
+        for (int c = 0; c < RC; ++c) ax[m][c] = ay[m][c] = 0ull;
+    }
+    const f2x k2 = f2_splat(k), eta2 = f2_splat(eta), kt2 = f2_splat(k_turns);
+    const f2x rnd2 = f2_splat(12582912.0f), twopi2 = f2_splat(6.283185307179586f);
+    const int c0 = blockIdx.z * chunk, c1 = min(N, c0 + chunk);
+    for (int range = 0; range < 2; ++range) {
+        const int lo = range ? max(c0, tb.excl_hi) : c0;
+        const int hi = range ? c1 : min(c1, tb.excl_lo);
+        for (int j0 = lo; j0 < hi; j0 += TS2) {
+            const int cnt = min(TS2, hi - j0);
+            __syncthreads();
+            if (tid < TS2) {
+                const int pp = tid >> 1, h = tid & 1;
+                float4 p = make_float4(-1e18f, -1e18f, -1e18f, 0.f), n = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (tid < cnt) { p = pos[j0 + tid]; n = nrm[j0 + tid]; }
+                float *g0 = reinterpret_cast<float *>(&s_g[0][pp]);
+                float *g1 = reinterpret_cast<float *>(&s_g[1][pp]);
+                float *g2 = reinterpret_cast<float *>(&s_g[2][pp]);
+                g0[h] = p.x; g0[2 + h] = p.y;
+                g1[h] = p.z; g1[2 + h] = n.x;
+                g2[h] = n.y; g2[2 + h] = n.z;
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const float2 sv = (tid < cnt && r0 + c < R) ? sw[(size_t)(j0 + tid) * R + r0 + c]
+                                                                : make_float2(0.f, 0.f);
+                    float *sg = reinterpret_cast<float *>(&s_sg[pp][c]);
+                    sg[h] = sv.x; sg[2 + h] = sv.y;
+                    reinterpret_cast<float *>(&s_ns[pp][c])[h] = -sv.y;
+                }
+            }
+            __syncthreads();
+            const int npair = (cnt + 1) >> 1;
+#pragma unroll 2
+            for (int jp = 0; jp < npair; ++jp) {
+                const ulonglong2 g0 = s_g[0][jp], g1 = s_g[1][jp], g2 = s_g[2][jp];
+#pragma unroll
+                for (int m = 0; m < TPT; ++m) {
+                    const f2x dx = f2_sub(tx[m], g0.x), dy = f2_sub(ty[m], g0.y), dz = f2_sub(tz[m], g1.x);
+                    const f2x r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+                    float r2a, r2b;
+                    f2_unpack(r2, r2a, r2b);
+                    const f2x ir = f2_pack(rsqrtf(r2a), rsqrtf(r2b));
+                    const f2x nd = f2_fma(g1.y, dx, f2_fma(g2.x, dy, f2_mul(g2.y, dz)));
+                    const f2x X = f2_mul(nd, f2_mul(ir, ir));
+                    const f2x A = f2_mul(X, ir);
+                    const f2x B = f2_fma(k2, X, f2_mul(eta2, ir));
+                    const f2x t = f2_mul(f2_mul(r2, ir), kt2);
+                    const f2x th = f2_mul(f2_sub(t, f2_sub(f2_add(t, rnd2), rnd2)), twopi2);
+                    float tha, thb, sa, ca, sb, cb;
+                    f2_unpack(th, tha, thb);
+                    __sincosf(tha, &sa, &ca);
+                    __sincosf(thb, &sb, &cb);
+                    const f2x s2 = f2_pack(sa, sb), c2 = f2_pack(ca, cb);
+                    const f2x gre = f2_fma(c2, A, f2_mul(s2, B));
+                    const f2x gim = f2_sub(f2_mul(s2, A), f2_mul(c2, B));
+#pragma unroll
+                    for (int q = 0; q < RC; ++q) {
+                        const ulonglong2 sg = s_sg[jp][q];
+                        const f2x ns = s_ns[jp][q];
+                        ax[m][q] = f2_fma(gre, sg.x, f2_fma(gim, ns, ax[m][q]));
+                        ay[m][q] = f2_fma(gre, sg.y, f2_fma(gim, sg.x, ay[m][q]));
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < TPT; ++m) {
+        int t = tid + m * NT;
+        if (t < tb.count)
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                if (r0 + c < R) {
+                    float xa, xb, ya, yb;
+                    f2_unpack(ax[m][c], xa, xb);
+                    f2_unpack(ay[m][c], ya, yb);
+                    const float2 v = make_float2(xa + xb, ya + yb);
+                    size_t e = (size_t)(tb.start + t) * R + r0 + c;
+                    if (ypart) ypart[blockIdx.z * split_stride + e] = v;
+                    else y[e] = make_double2((double)v.x, (double)v.y);
+                }
+    }
+}
+
+// sigma'_{j,r} = w_j sigma_{j,r} / (4 pi), formed in FP64 and rounded once to FP32:
+// the FP32 kernels stage it without per-tile FP64 work.
+__global__ void weight_sigma32_kernel(size_t n, int R, const double4 *__restrict__ pos64,
+                                      const double2 *__restrict__ sigma, float2 *__restrict__ out)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double wq = pos64[e / R].w * HZB_INV4PI;
+    const double2 v = sigma[e];
+    out[e] = make_float2((float)(v.x * wq), (float)(v.y * wq));
+}
+
+const float2 *weighted_sigma32(hzb_ctx *c, int R, const double2 *sigma)
+{
+    const size_t n = (size_t)c->N * R;
+    if (check_cuda(c, c->sig32.ensure(n), "alloc weighted densities")) return nullptr;
+    weight_sigma32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, R, c->pos64.ptr, sigma, c->sig32.ptr);
+    c->launches++;
+    return c->sig32.ptr;
+}
+
 // y = sum over the nsplit partial sums (fixed order)
 template <typename P>
 __global__ void split_reduce_kernel(size_t n, int nsplit, const P *__restrict__ part, double2 *__restrict__ y)
@@ -250,11 +364,15 @@ int default_nsplit(hzb_ctx *c, int R, int tpt)
     return std::min(ns, 64);
 }
 
-static hzb_status ensure_sctab(hzb_ctx *c)
+hzb_status ensure_sctab(hzb_ctx *c)
 {
     if (c->sctab.ptr) return HZB_OK;
     std::vector<double2> tab(SC_N);
-    for (int q = 0; q < SC_N; ++q) tab[q] = make_double2(std::cos(2.0 * M_PI * q / SC_N), std::sin(2.0 * M_PI * q / SC_N));
+    // angles in long double so each entry is the correctly rounded value to within an ulp
+    for (int q = 0; q < SC_N; ++q) {
+        const long double a = 6.283185307179586476925286766559L * q / SC_N;
+        tab[q] = make_double2((double)std::cos(a), (double)std::sin(a));
+    }
     if (check_cuda(c, c->sctab.ensure(SC_N), "alloc table")) return HZB_ENOMEM;
     return check_cuda(c, cudaMemcpyAsync(c->sctab.ptr, tab.data(), SC_N * sizeof(double2), cudaMemcpyHostToDevice,
                                          c->stream), "copy table");
@@ -265,11 +383,11 @@ static void launch64(hzb_ctx *c, dim3 g, int N, int R, int chunk, const double2 
 {
     nbody64_kernel<RC, TPT><<<g, TBLOCK / TPT, 0, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos64.ptr,
                                                                c->nrm64.ptr, sigma, c->sctab.ptr, c->k, c->eta,
-                                                               out, stride);
+                                                               c->k * (SC_N / (2.0 * M_PI)), out, stride);
 }
 
 template <int RC, int TPT>
-static void launch32(hzb_ctx *c, dim3 g, int N, int R, int chunk, const double2 *sigma, float2 *part, double2 *y,
+static void launch32(hzb_ctx *c, dim3 g, int N, int R, int chunk, const float2 *sigma, float2 *part, double2 *y,
                      size_t stride)
 {
     nbody32_kernel<RC, TPT><<<g, TBLOCK / TPT, 0, c->stream>>>(
@@ -285,10 +403,25 @@ static void dispatch64(hzb_ctx *c, int tpt, dim3 g, int N, int R, int chunk, con
     else launch64<RC, 4>(c, g, N, R, chunk, s, o, st);
 }
 
-template <int RC>
-static void dispatch32(hzb_ctx *c, int tpt, dim3 g, int N, int R, int chunk, const double2 *s, float2 *p, double2 *y,
-                       size_t st)
+template <int RC, int TPT>
+static void launch32x2(hzb_ctx *c, dim3 g, int N, int R, int chunk, const float2 *sigma, float2 *part, double2 *y,
+                       size_t stride)
 {
+    nbody32x2_kernel<RC, TPT><<<g, TBLOCK / TPT, 0, c->stream>>>(
+        c->tblocks.ptr, N, R, chunk, c->pos32.ptr, c->nrm32.ptr, sigma, (float)c->k, (float)c->eta,
+        (float)(c->k / (2.0 * M_PI)), part, y, stride);
+}
+
+template <int RC>
+static void dispatch32(hzb_ctx *c, int tpt, bool x2, dim3 g, int N, int R, int chunk, const float2 *s, float2 *p,
+                       double2 *y, size_t st)
+{
+    if (x2) {
+        if (tpt == 1) launch32x2<RC, 1>(c, g, N, R, chunk, s, p, y, st);
+        else if (tpt == 2) launch32x2<RC, 2>(c, g, N, R, chunk, s, p, y, st);
+        else launch32x2<RC, 4>(c, g, N, R, chunk, s, p, y, st);
+        return;
+    }
     if (tpt == 1) launch32<RC, 1>(c, g, N, R, chunk, s, p, y, st);
     else if (tpt == 2) launch32<RC, 2>(c, g, N, R, chunk, s, p, y, st);
     else launch32<RC, 4>(c, g, N, R, chunk, s, p, y, st);
@@ -331,7 +464,7 @@ hzb_status interbody64_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, 
     return check_cuda(c, e, "nbody64_kernel");
 }
 
-hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit)
+hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit, bool x2)
 {
     if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
     const int N = (int)c->N;
@@ -347,11 +480,13 @@ hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, 
     c->interbody_calls++;
     c->launches += (nsplit > 1) ? 2 : 1;
     const int slot = prof_begin(c, 1);
+    const float2 *sw = weighted_sigma32(c, R, sigma);
+    if (!sw) return HZB_ENOMEM;
     const int nb = (c->tune_limit_blocks > 0) ? std::min(c->tune_limit_blocks, c->n_tblocks) : c->n_tblocks;
     dim3 g(nb, (R + rc - 1) / rc, nsplit);
-    if (rc == 1) dispatch32<1>(c, tpt, g, N, R, chunk, sigma, part, y, n);
-    else if (rc == 4) dispatch32<4>(c, tpt, g, N, R, chunk, sigma, part, y, n);
-    else dispatch32<8>(c, tpt, g, N, R, chunk, sigma, part, y, n);
+    if (rc == 1) dispatch32<1>(c, tpt, x2, g, N, R, chunk, sw, part, y, n);
+    else if (rc == 4) dispatch32<4>(c, tpt, x2, g, N, R, chunk, sw, part, y, n);
+    else dispatch32<8>(c, tpt, x2, g, N, R, chunk, sw, part, y, n);
     if (nsplit > 1)
         split_reduce_kernel<float2><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, nsplit, part, y);
     cudaError_t e = cudaGetLastError();
@@ -359,8 +494,18 @@ hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, 
     return check_cuda(c, e, "nbody32_kernel");
 }
 
+// Source split of the tensor-core kernel: about four CTAs per SM in all.
+static int default_nsplit_tc(hzb_ctx *c, int R)
+{
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
+    const long long ctas = (long long)c->n_tblocks * 4 * ((R + 15) / 16);
+    return (int)std::min<long long>(64, std::max<long long>(1, (4LL * sms + ctas - 1) / ctas));
+}
+
 hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 {
+    if (c->nbody64_engine != 0) return interbody64_sym(c, R, sigma, y);
     int tpt = c->tune64_tpt > 0 ? c->tune64_tpt : 2;
     int ns = c->tune64_split > 0 ? c->tune64_split : default_nsplit(c, R, tpt);
     return interbody64_cfg(c, R, sigma, y, tpt, ns);
@@ -369,17 +514,17 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 {
     // many right-hand sides: contraction on the tensor cores (nbody_tc.cu)
-    if (c->nbody_engine == 1 || (c->nbody_engine < 0 && R >= 16)) {
-        int sms = 152;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
-        const int rc = (R >= 32) ? 32 : 16;
-        const long long ctas = (long long)c->n_tblocks * 4 * ((R + rc - 1) / rc);
-        int ns = c->tunetc_split > 0 ? c->tunetc_split : (int)std::max<long long>(1, (4LL * sms + ctas - 1) / ctas);
-        return interbody_tc(c, R, sigma, y, std::min(ns, 64));
+    bool tc = c->nbody_engine == 1;
+    if (c->nbody_engine < 0) tc = (c->tune32_tc >= 0 && c->tune32_tc_R == R) ? c->tune32_tc == 1 : R >= 16;
+    if (tc) {
+        int ns = c->tunetc_split > 0 ? c->tunetc_split : default_nsplit_tc(c, R);
+        return interbody_tc(c, R, sigma, y, ns);
     }
+    // CUDA cores: packed-pair kernel unless the scalar one is asked for or tuned faster
+    const bool x2 = c->nbody_engine == 2 ? false : (c->nbody_engine == 3 ? true : c->tune32_x2 != 0);
     int tpt = c->tune32_tpt > 0 ? c->tune32_tpt : 4;
     int ns = c->tune32_split > 0 ? c->tune32_split : default_nsplit(c, R, tpt);
-    return interbody32_cfg(c, R, sigma, y, tpt, ns);
+    return interbody32_cfg(c, R, sigma, y, tpt, ns, x2);
 }
 
 // ------------------------------------------------------------------ fields at points
@@ -518,15 +663,28 @@ namespace hzb {
 
 // Time one inter-body configuration: one warm-up launch, then the mean of `reps`
 // launches between CUDA events on the context's stream.
-static float time_cfg(hzb_ctx *c, int prec, int R, int tpt, int ns, const double2 *x, double2 *y, int reps)
+static float time_cfg(hzb_ctx *c, int prec, int R, int tpt, int ns, bool x2, const double2 *x, double2 *y, int reps)
 {
-    hzb_status st = prec ? interbody32_cfg(c, R, x, y, tpt, ns) : interbody64_cfg(c, R, x, y, tpt, ns);
+    hzb_status st = prec ? interbody32_cfg(c, R, x, y, tpt, ns, x2) : interbody64_cfg(c, R, x, y, tpt, ns);
     if (st) return -1.f;
     cudaEventRecord(c->ev0, c->stream);
     for (int q = 0; q < reps; ++q) {
-        st = prec ? interbody32_cfg(c, R, x, y, tpt, ns) : interbody64_cfg(c, R, x, y, tpt, ns);
+        st = prec ? interbody32_cfg(c, R, x, y, tpt, ns, x2) : interbody64_cfg(c, R, x, y, tpt, ns);
         if (st) return -1.f;
     }
+    cudaEventRecord(c->ev1, c->stream);
+    if (cudaEventSynchronize(c->ev1) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    return ms / reps;
+}
+
+static float time_tc(hzb_ctx *c, int R, int ns, const double2 *x, double2 *y, int reps)
+{
+    if (interbody_tc(c, R, x, y, ns)) return -1.f;
+    cudaEventRecord(c->ev0, c->stream);
+    for (int q = 0; q < reps; ++q)
+        if (interbody_tc(c, R, x, y, ns)) return -1.f;
     cudaEventRecord(c->ev1, c->stream);
     if (cudaEventSynchronize(c->ev1) != cudaSuccess) return -1.f;
     float ms = 0.f;
@@ -546,23 +704,44 @@ hzb_status autotune(hzb_ctx *c, int R, int which, double *best_ms)
     const long long calls = c->interbody_calls, launches = c->launches;
     for (int prec = 1; prec >= 0; --prec) {
         if (!(which & (prec ? 1 : 2))) continue;
-        int bt = 0, bs = 0;
+        int bt = 0, bs = 0, bx = 0;
         float bm = 1e30f;
         const int tpts[3] = {1, 2, 4};
-        for (int a = 0; a < 3; ++a) {
-            int tpt = tpts[a];
-            if (prec == 0 && tpt == 4) continue;
-            int d = default_nsplit(c, R, tpt);
-            int cand[5] = {1, 2, d, 2 * d, 4 * d};
-            for (int b = 0; b < 5; ++b) {
-                if (b > 0 && cand[b] == cand[b - 1]) continue;
-                if (cand[b] > 64) continue;
-                float ms = time_cfg(c, prec, R, tpt, cand[b], c->io_in.ptr, c->io_out.ptr, prec ? 3 : 1);
-                if (ms < 0) return fail(c, HZB_ECUDA, "autotune launch failed");
-                if (ms < bm) { bm = ms; bt = tpt; bs = cand[b]; }
+        // FP32 kernel variants: 0 scalar, 1 packed pairs (unless the engine fixes one)
+        const int xmin = (prec && c->nbody_engine == 3) ? 1 : 0;
+        const int xmax = (prec && c->nbody_engine != 2) ? 1 : 0;
+        for (int xv = xmin; xv <= xmax; ++xv)
+            for (int a = 0; a < 3; ++a) {
+                int tpt = tpts[a];
+                if (prec == 0 && tpt == 4) continue;
+                int d = default_nsplit(c, R, tpt);
+                int cand[5] = {1, 2, d, 2 * d, 4 * d};
+                for (int b = 0; b < 5; ++b) {
+                    if (b > 0 && cand[b] == cand[b - 1]) continue;
+                    if (cand[b] > 64) continue;
+                    float ms = time_cfg(c, prec, R, tpt, cand[b], xv == 1, c->io_in.ptr, c->io_out.ptr, prec ? 3 : 1);
+                    if (ms < 0) return fail(c, HZB_ECUDA, "autotune launch failed");
+                    if (ms < bm) { bm = ms; bt = tpt; bs = cand[b]; bx = xv; }
+                }
             }
+        if (prec && R >= 8 && c->nbody_engine < 0) {
+            // the tensor-core contraction competes for the FP32 inter-body sum
+            const int d = default_nsplit_tc(c, R);
+            const int cand[4] = {1, 2, d, 2 * d};
+            int tbs = 0;
+            float tbm = 1e30f;
+            for (int b = 0; b < 4; ++b) {
+                if ((b > 0 && cand[b] == cand[b - 1]) || cand[b] > 64) continue;
+                float ms = time_tc(c, R, cand[b], c->io_in.ptr, c->io_out.ptr, 3);
+                if (ms < 0) return fail(c, HZB_ECUDA, "autotune launch failed");
+                if (ms < tbm) { tbm = ms; tbs = cand[b]; }
+            }
+            c->tunetc_split = tbs;
+            c->tune32_tc = (tbm < bm) ? 1 : 0;
+            c->tune32_tc_R = R;
+            bm = std::min(bm, tbm);
         }
-        if (prec) { c->tune32_tpt = bt; c->tune32_split = bs; }
+        if (prec) { c->tune32_tpt = bt; c->tune32_split = bs; c->tune32_x2 = bx; }
         else { c->tune64_tpt = bt; c->tune64_split = bs; }
         if (best_ms) best_ms[prec ? 0 : 1] = bm;
     }

@@ -1,0 +1,217 @@
+// FP64 inter-body sum y = B sigma (Sec. 3.3, Eq. (nystromnaive)) with each unordered
+// pair of nodes on different bodies evaluated once for both directions.
+//
+// For nodes i, j with d = x_i - x_j, r = |d|:
+//     w_j K(x_i, x_j) = w_j / (4 pi) e^{ikr} [ n_j.d / r^3 - i (k n_j.d / r^2 + eta / r) ]
+//     w_i K(x_j, x_i) = w_i / (4 pi) e^{ikr} [-n_i.d / r^3 - i (-k n_i.d / r^2 + eta / r) ]
+// share d, r, 1/r and e^{ikr}, which are two thirds of the FP64 work of a pair; the
+// two directions differ only in the normal projection.  About 27.5 FP64 operations
+// per ordered pair instead of 41 for the one-directional kernel (nbody64_kernel).
+//
+// Work: one CTA per unordered pair of TargetBlocks (I, J), I < J, on different
+// bodies (grid y: chunks of RC right-hand sides).  Thread t owns target i = I.start + t;
+// sources of J come in tiles of 32.  Inside a warp the 32 x 32 pairs of a tile run in
+// 32 steps: at step s lane l takes source (l + s) mod 32, adds the i <- j term to its
+// own sum and the j <- i term to a rotating sum that then moves to lane l - 1, so each
+// source's partial sum visits every lane once and no two lanes touch the same source
+// at a step.  The warps' partial sums of a tile are added in a fixed order in shared
+// memory.  Both directions reach y through FP64 atomic adds (y is zeroed first), so
+// the order of the additions into one y entry varies between runs: the result is
+// reproducible to rounding, not bit for bit.
+#include <algorithm>
+#include <vector>
+
+#include "fp64_pair.cuh"
+#include "hzb_internal.h"
+#include "kernel_math.cuh"
+
+namespace hzb {
+
+static const int SYM_T = 512;        // targets per CTA = TargetBlock size
+static const int SYM_S = 32;         // sources per tile (one per lane)
+
+template <int RC>
+__global__ void __launch_bounds__(SYM_T, 1)
+nbody64_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict__ blocks, int R,
+                   const double4 *__restrict__ pos, const double4 *__restrict__ nrm,
+                   const double2 *__restrict__ sigma, const double2 *__restrict__ sctab, double k, double eta,
+                   double kt, double2 *__restrict__ y)
+{
+    __shared__ double4 s_p[SYM_S];               // x, y, z, w
+    __shared__ double4 s_n[SYM_S];               // nx, ny, nz
+    __shared__ double2 s_w[SYM_S][RC];           // w_j sigma_j / (4 pi)
+    __shared__ double2 s_red[SYM_T / 32][RC][SYM_S];
+    const int2 pr = pairs[blockIdx.x];
+    const TargetBlock bi = blocks[pr.x], bj = blocks[pr.y];
+    const int r0 = blockIdx.y * RC;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool live = tid < bi.count;
+    // own target: position, normal, weighted densities (zero for padding threads)
+    double tx = 1e6 + tid, ty = 1e6, tz = 1e6, mx = 0.0, my = 0.0, mz = 0.0;
+    double2 wi[RC], acc_t[RC];
+    if (live) {
+        const double4 p = pos[bi.start + tid], n = nrm[bi.start + tid];
+        tx = p.x; ty = p.y; tz = p.z; mx = n.x; my = n.y; mz = n.z;
+        const double wq = p.w * HZB_INV4PI;
+#pragma unroll
+        for (int c = 0; c < RC; ++c) {
+            const double2 v = (r0 + c < R) ? sigma[(size_t)(bi.start + tid) * R + r0 + c] : make_double2(0.0, 0.0);
+            wi[c] = make_double2(v.x * wq, v.y * wq);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < RC; ++c) wi[c] = make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int c = 0; c < RC; ++c) acc_t[c] = make_double2(0.0, 0.0);
+    const bool warp_live = warp * 32 < bi.count;
+    const double eta_ = eta;
+    for (int j0 = 0; j0 < bj.count; j0 += SYM_S) {
+        const int cnt = min(SYM_S, bj.count - j0);
+        __syncthreads();
+        if (tid < SYM_S) {
+            if (tid < cnt) {
+                const double4 p = pos[bj.start + j0 + tid];
+                s_p[tid] = p;
+                s_n[tid] = nrm[bj.start + j0 + tid];
+                const double wq = p.w * HZB_INV4PI;
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const double2 v =
+                        (r0 + c < R) ? sigma[(size_t)(bj.start + j0 + tid) * R + r0 + c] : make_double2(0.0, 0.0);
+                    s_w[tid][c] = make_double2(v.x * wq, v.y * wq);
+                }
+            } else {                                   // far, zero density: contributes 0 both ways
+                s_p[tid] = make_double4(-1e6 - tid, -1e6, -1e6, 0.0);
+                s_n[tid] = make_double4(0.0, 0.0, 0.0, 0.0);
+#pragma unroll
+                for (int c = 0; c < RC; ++c) s_w[tid][c] = make_double2(0.0, 0.0);
+            }
+        }
+        __syncthreads();
+        double2 acc_s[RC];
+#pragma unroll
+        for (int c = 0; c < RC; ++c) acc_s[c] = make_double2(0.0, 0.0);
+        if (warp_live) {
+#pragma unroll 2
+            for (int s = 0; s < SYM_S; ++s) {
+                const int q = (lane + s) & (SYM_S - 1);
+                const double4 p = s_p[q];
+                const double4 n = s_n[q];
+                const double dx = tx - p.x, dy = ty - p.y, dz = tz - p.z;
+                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                const double ir = rsqrt_fp64(r2);
+                const double ir2 = ir * ir, eir = eta_ * ir;
+                double sn, cs;
+                cis_turns((r2 * ir) * kt, sctab, cs, sn);
+                // i <- j: normal of source j
+                const double X1 = fma(n.x, dx, fma(n.y, dy, n.z * dz)) * ir2;
+                const double A1 = X1 * ir, B1 = fma(k, X1, eir);
+                const double g1r = fma(cs, A1, sn * B1), g1i = fma(sn, A1, -cs * B1);
+                // j <- i: normal of target i, d reversed (X2 = -X2p)
+                const double X2p = fma(mx, dx, fma(my, dy, mz * dz)) * ir2;
+                const double A2n = X2p * ir, B2 = fma(-k, X2p, eir);
+                const double g2r = fma(-cs, A2n, sn * B2);            // Re K(x_j, x_i) w
+                const double h = fma(sn, A2n, cs * B2);                 // -Im K(x_j, x_i) w
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const double2 wj = s_w[q][c];
+                    acc_t[c].x = fma(g1r, wj.x, fma(-g1i, wj.y, acc_t[c].x));
+                    acc_t[c].y = fma(g1r, wj.y, fma(g1i, wj.x, acc_t[c].y));
+                    acc_s[c].x = fma(g2r, wi[c].x, fma(h, wi[c].y, acc_s[c].x));
+                    acc_s[c].y = fma(g2r, wi[c].y, fma(-h, wi[c].x, acc_s[c].y));
+                }
+                // the rotating sum of source (l + s + 1) mod 32 comes from lane l + 1
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    acc_s[c].x = __shfl_sync(0xffffffffu, acc_s[c].x, (lane + 1) & 31);
+                    acc_s[c].y = __shfl_sync(0xffffffffu, acc_s[c].y, (lane + 1) & 31);
+                }
+            }
+        }
+        // after 32 steps lane l holds the partial sum of source l
+#pragma unroll
+        for (int c = 0; c < RC; ++c) s_red[warp][c][lane] = acc_s[c];
+        __syncthreads();
+        if (tid < SYM_S * RC) {
+            const int src = tid & (SYM_S - 1), c = tid / SYM_S;
+            if (src < cnt && r0 + c < R) {
+                double sx = 0.0, sy = 0.0;
+                for (int w = 0; w < SYM_T / 32; ++w) {
+                    sx += s_red[w][c][src].x;
+                    sy += s_red[w][c][src].y;
+                }
+                double2 *o = y + (size_t)(bj.start + j0 + src) * R + r0 + c;
+                atomicAdd(&o->x, sx);
+                atomicAdd(&o->y, sy);
+            }
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int c = 0; c < RC; ++c)
+            if (r0 + c < R) {
+                double2 *o = y + (size_t)(bi.start + tid) * R + r0 + c;
+                atomicAdd(&o->x, acc_t[c].x);
+                atomicAdd(&o->y, acc_t[c].y);
+            }
+    }
+}
+
+// Unordered pairs of target blocks on different bodies, built once per geometry.
+static hzb_status ensure_block_pairs(hzb_ctx *c)
+{
+    if (c->n_blockpairs > 0) return HZB_OK;
+    std::vector<TargetBlock> tb(c->n_tblocks);
+    if (check_cuda(c, cudaMemcpyAsync(tb.data(), c->tblocks.ptr, tb.size() * sizeof(TargetBlock),
+                                      cudaMemcpyDeviceToHost, c->stream), "copy blocks") ||
+        check_cuda(c, cudaStreamSynchronize(c->stream), "copy blocks"))
+        return HZB_ECUDA;
+    std::vector<int2> pr;
+    for (int i = 0; i < (int)tb.size(); ++i)
+        for (int j = i + 1; j < (int)tb.size(); ++j)
+            if (tb[i].excl_lo != tb[j].excl_lo) pr.push_back(make_int2(i, j));
+    if (pr.empty()) {
+        c->n_blockpairs = -1;                   // one body: B = 0
+        return HZB_OK;
+    }
+    if (check_cuda(c, c->blockpairs.ensure(pr.size()), "alloc block pairs")) return HZB_ENOMEM;
+    if (check_cuda(c, cudaMemcpyAsync(c->blockpairs.ptr, pr.data(), pr.size() * sizeof(int2),
+                                      cudaMemcpyHostToDevice, c->stream), "copy block pairs") ||
+        check_cuda(c, cudaStreamSynchronize(c->stream), "copy block pairs"))
+        return HZB_ECUDA;
+    c->n_blockpairs = (long long)pr.size();
+    return HZB_OK;
+}
+
+hzb_status interbody64_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
+{
+    if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
+    if (c->capturing && c->n_blockpairs == 0) return fail(c, HZB_ESTATE, "block pairs not built before capture");
+    hzb_status st = ensure_sctab(c);
+    if (st || (st = ensure_block_pairs(c))) return st;
+    const size_t n = (size_t)c->N * R;
+    if (check_cuda(c, cudaMemsetAsync(y, 0, n * sizeof(double2), c->stream), "zero y")) return HZB_ECUDA;
+    c->interbody_calls++;
+    if (c->n_blockpairs < 0) return HZB_OK;
+    if (c->n_blockpairs > 0x7fffffffLL) return fail(c, HZB_EINVAL, "too many block pairs for one launch");
+    c->launches += 1;
+    const int slot = prof_begin(c, 0);
+    const int rc = (R == 1) ? 1 : (R == 2 ? 2 : 4);
+    dim3 g((unsigned)c->n_blockpairs, (R + rc - 1) / rc, 1);
+    const double kt = c->k * (SC_N / (2.0 * M_PI));
+    if (rc == 1)
+        nbody64_sym_kernel<1><<<g, SYM_T, 0, c->stream>>>(c->blockpairs.ptr, c->tblocks.ptr, R, c->pos64.ptr,
+                                                          c->nrm64.ptr, sigma, c->sctab.ptr, c->k, c->eta, kt, y);
+    else if (rc == 2)
+        nbody64_sym_kernel<2><<<g, SYM_T, 0, c->stream>>>(c->blockpairs.ptr, c->tblocks.ptr, R, c->pos64.ptr,
+                                                          c->nrm64.ptr, sigma, c->sctab.ptr, c->k, c->eta, kt, y);
+    else
+        nbody64_sym_kernel<4><<<g, SYM_T, 0, c->stream>>>(c->blockpairs.ptr, c->tblocks.ptr, R, c->pos64.ptr,
+                                                          c->nrm64.ptr, sigma, c->sctab.ptr, c->k, c->eta, kt, y);
+    cudaError_t e = cudaGetLastError();
+    prof_end(c, slot);
+    return check_cuda(c, e, "nbody64_sym_kernel");
+}
+
+}  // namespace hzb

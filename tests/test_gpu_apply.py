@@ -41,12 +41,44 @@ def test_interbody_fp64(pair, R):
     assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("R", [1, 2, 5])
+def test_interbody_fp64_engines(pair, R, engine):
+    """One-directional (0) and pair-symmetric (1) FP64 kernels, each forced; R = 5
+    takes two right-hand-side chunks of the symmetric kernel, the second ragged."""
+    s, P = pair
+    sig = rand_c((P.N, R), 161 + R)
+    ref = P.interbody(sig)
+    s.set_fp64_interbody_engine(engine)
+    try:
+        got = s.interbody(sig)
+    finally:
+        s.set_fp64_interbody_engine(-1)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("R", [1, 5])
 def test_interbody_fp32(pair, R):
     s, P = pair
     sig = rand_c((P.N, R), 21 + R)
     got = s.interbody(sig, precision=1)
     ref = P.interbody(sig)
+    assert rel_l2(got, ref) < 2e-6
+
+
+@pytest.mark.parametrize("engine", [2, 3])
+@pytest.mark.parametrize("R", [1, 5, 9])
+def test_interbody_fp32_kernel_variants(pair, R, engine):
+    """Scalar (2) and packed-pair f32x2 (3) FP32 CUDA-core kernels, each forced, over
+    ragged source tiles (odd node counts) and ragged right-hand-side chunks (R = 5, 9)."""
+    s, P = pair
+    sig = rand_c((P.N, R), 151 + R)
+    ref = P.interbody(sig)
+    s.set_interbody_engine(engine)
+    try:
+        got = s.interbody(sig, precision=1)
+    finally:
+        s.set_interbody_engine(-1)
     assert rel_l2(got, ref) < 2e-6
 
 
@@ -106,11 +138,20 @@ def test_spheroids_258560_sampled_rows():
     rows = np.sort(np.random.default_rng(72).choice(P.N, 96, replace=False)).astype(np.int32)
     ref = P.interbody(sig, targets=rows)
     y64 = s.interbody(sig)
-    y32 = s.interbody(sig, precision=1)
     assert np.abs(y64[rows] - ref).max() < 1e-11 * np.abs(ref).max()
     # FP32: the phase k r carries the relative error of r (~2 ulp after the hardware
     # reciprocal square root) times k r <= 4 x 14 here, ~1e-5 per term at most.
-    assert rel_l2(y32[rows], ref) < 3e-5
+    for engine in (2, 3):
+        s.set_interbody_engine(engine)
+        y32 = s.interbody(sig, precision=1)
+        assert rel_l2(y32[rows], ref) < 3e-5, engine
+    # tensor-core contraction, 16 right-hand sides: 258,560 sources per target
+    sig16 = rand_c((P.N, 16), 73)
+    ref16 = P.interbody(sig16, targets=rows)
+    s.set_interbody_engine(1)
+    ytc = s.interbody(sig16, precision=1)
+    s.set_interbody_engine(-1)
+    assert rel_l2(ytc[rows], ref16) < 3e-5
 
 
 @pytest.mark.parametrize("R", [1, 3, 9])
