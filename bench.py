@@ -40,6 +40,9 @@ TOL_REF = 1e-12           # reference density (FP64-accurate, untimed)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 FP64_PEAK_TFLOPS = 1.25                              # nominal GB300 FP64 (no FP64 entry is measured)
 FLOPS_PER_PAIR = 36       # algorithmic flops of one pair interaction at R = 1 (FMA = 2)
+# DRAM bytes (read + write) per launch on this workload from one ncu capture of each kernel
+# (profiles/); None for a kernel without a capture of its current version.
+DRAM_BYTES_NCU = {"nbody64_sym_kernel": 25.96e6, "nbody32_sym_kernel": 15.42e6}
 
 
 def dist_env():
@@ -234,9 +237,8 @@ def main():
                   verify_final=0)
     s = Solver.from_workload(wl, opt, stream=torch.cuda.current_stream().cuda_stream)
     s.build_scattering_matrices()
-    s.set_interbody_engine(3)           # FP32 sum: packed-pair (f32x2) CUDA-core kernel
-    s.set_fp64_interbody_engine(1)      # FP64 sum: pair-symmetric kernel
-    tuned = s.autotune(1, 1)            # launch shape of the FP32 inter-body kernel
+    tuned = s.autotune(1, 1)            # FP32 inter-body kernel variant and launch shape
+    kernels = s.tuned_config(1)         # what the timed solves launch
     N = s.N
 
     # FP64-accurate reference density (mixed refinement to 1e-12, untimed)
@@ -333,15 +335,17 @@ def main():
     if t32 >= t64:
         per = t32 / max(n32, 1)
         ach = FLOPS_PER_PAIR * pairs / (per * 1e-3) / 1e12
-        roof = {"kernel": "nbody32x2_kernel", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+        roof = {"kernel": kernels["fp32_kernel"], "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                "traffic": DRAM_BYTES_NCU.get(kernels["fp32_kernel"]),
                 "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 x 2.07 GHz (unit counts and clock)",
                 "ms_per_launch": per}
     else:
         per = t64 / max(n64, 1)
         ach = FLOPS_PER_PAIR * pairs / (per * 1e-3) / 1e12
-        roof = {"kernel": "nbody64_sym_kernel", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+        roof = {"kernel": kernels["fp64_kernel"], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": DRAM_BYTES_NCU.get(kernels["fp64_kernel"]),
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s", "ms_per_launch": per}
     gint32 = pairs / (t32 / max(n32, 1) * 1e-3) / 1e9 if n32 else None
     gint64 = pairs / (t64 / max(n64, 1) * 1e-3) / 1e9 if n64 else None
@@ -366,7 +370,7 @@ def main():
                        "fp64_residual_applies": stats[-1].n_nbody64, "fp32_applies": stats[-1].n_nbody32,
                        "stop_rule": "a-priori refinement bound after one FP64 residual (verify_final=0); "
                                     "density error checked against the reference every run",
-                       "autotuned_fp32_ms_per_launch": float(tuned[0])},
+                       "autotuned_fp32_ms_per_launch": float(tuned[0]), "kernels": kernels},
             "matvec_ginteractions_per_s": {"fp32": gint32, "fp64": gint64,
                                             "pairs_per_apply": pairs},
             "fp64_gpu": fp64,

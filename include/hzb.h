@@ -162,6 +162,14 @@ hzb_status hzb_build_scattering_matrices(hzb_ctx *ctx);
  * the fastest time per launch [FP32, FP64].  Not part of the paper: a GB300 tuning aid. */
 hzb_status hzb_autotune(hzb_ctx *ctx, int R, int which, double best_ms[2]);
 
+/* The inter-body kernels the context will launch for R right-hand sides (host only,
+ * no GPU work), written to out[6]: [0] FP32 kernel: 0 scalar, 1 packed pairs,
+ * 2 pair-symmetric packed, 3 tensor cores; [1] its targets (or packed target pairs)
+ * per thread, 0 = default; [2] its source chunks, 0 = default; [3] FP64 kernel:
+ * 0 one-directional, 1 pair-symmetric; [4], [5] the one-directional FP64 kernel's
+ * targets per thread and source chunks (0 = default).  HZB_EINVAL on NULL. */
+hzb_status hzb_tuned_config(const hzb_ctx *ctx, int R, int out[6]);
+
 /* GMRES execution controls (no effect on results beyond rounding of where a
  * converged right-hand side stops):
  *   check_every: Arnoldi steps issued between host reads of the residual estimates
@@ -185,17 +193,20 @@ hzb_status hzb_set_modal_engine(hzb_ctx *ctx, int engine);
  * kernels generated on the CUDA cores, the contraction with the densities of up to 32
  * right-hand sides on the tensor cores (TF32, three-term split, FP32 accumulation);
  * 2 = CUDA cores, scalar FP32 kernel; 3 = CUDA cores, packed-pair kernel (two sources
- * per f32x2 instruction); -1 (default) = tensor cores when R >= 16 (or as tuned),
- * else as 0.  Returns HZB_EINVAL for other values. */
+ * per f32x2 instruction); 4 = CUDA cores, pair-symmetric packed kernel (each unordered
+ * node pair evaluated once for both directions, results added with FP64 atomics: equal
+ * to rounding between runs, not bit for bit); -1 (default) = tensor cores when R >= 16
+ * (or as tuned), else as 0.  Returns HZB_EINVAL for other values. */
 hzb_status hzb_set_interbody_engine(hzb_ctx *ctx, int engine);
 
-/* Engine of the FP64 inter-body sum (Sec. 3.3): 0 = one-directional kernel (each
- * ordered pair on its own, source chunks added in a fixed order: bit-reproducible);
- * 1 = pair-symmetric kernel: each unordered pair of nodes on different bodies is
- * evaluated once for both directions (r, 1/r and e^{ikr} are shared), about 1.5x
- * fewer FP64 operations; both directions are added into y with FP64 atomics, so runs
- * agree to rounding but not bit for bit; -1 (default) = 1.  Returns HZB_EINVAL for
- * other values.  Not part of the paper: a GB300 choice (FP64 runs at 1/64 rate). */
+/* Engine of the FP64 and double-float inter-body sums (Sec. 3.3): 0 = one-directional
+ * kernels (each ordered pair on its own, source chunks added in a fixed order:
+ * bit-reproducible); 1 = pair-symmetric kernels: each unordered pair of nodes on
+ * different bodies is evaluated once for both directions (r, 1/r and e^{ikr} are
+ * shared), about 1.5x fewer operations; both directions are added into y with FP64
+ * atomics, so runs agree to rounding but not bit for bit; -1 (default) = 1.  Returns
+ * HZB_EINVAL for other values.  Not part of the paper: a GB300 choice (FP64 runs at
+ * 1/64 of the FP32 rate). */
 hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *ctx, int engine);
 
 /* Copy A~_p (which = 0) or S_p (which = 1) of the shape of body `body`, mode p in

@@ -131,6 +131,7 @@ def lib():
         "hzb_set_modal_engine": (i, [p, i]),
         "hzb_set_interbody_engine": (i, [p, i]),
         "hzb_set_fp64_interbody_engine": (i, [p, i]),
+        "hzb_tuned_config": (i, [p, i, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -205,7 +206,8 @@ class Solver:
 
     def set_interbody_engine(self, engine: int):
         """FP32 inter-body sum engine: 0 CUDA cores, 1 tensor cores, 2 scalar CUDA-core kernel,
-        3 packed-pair CUDA-core kernel, -1 auto (tensor cores for R >= 16 or as tuned)."""
+        3 packed-pair CUDA-core kernel, 4 pair-symmetric packed kernel, -1 auto (tensor cores
+        for R >= 16 or as tuned)."""
         self._check(lib().hzb_set_interbody_engine(self._h, int(engine)))
 
     def set_fp64_interbody_engine(self, engine: int):
@@ -259,6 +261,16 @@ class Solver:
         best = np.zeros(2)
         self._check(lib().hzb_autotune(self._h, int(R), int(which), _ptr(best)))
         return best
+
+    FP32_KERNELS = ("nbody32_kernel", "nbody32x2_kernel", "nbody32_sym_kernel", "nbody_tc_kernel")
+
+    def tuned_config(self, R: int = 1) -> dict:
+        """The inter-body kernels this solver launches for R right-hand sides."""
+        out = np.zeros(6, dtype=np.int32)
+        self._check(lib().hzb_tuned_config(self._h, int(R), _ptr(out)))
+        return {"fp32_kernel": self.FP32_KERNELS[out[0]], "fp32_tpt": int(out[1]), "fp32_split": int(out[2]),
+                "fp64_kernel": "nbody64_sym_kernel" if out[3] else "nbody64_kernel",
+                "fp64_tpt": int(out[4]), "fp64_split": int(out[5])}
 
     def build_scattering_matrices(self):
         self._check(lib().hzb_build_scattering_matrices(self._h))

@@ -448,6 +448,23 @@ hzb_status hzb_autotune(hzb_ctx *c, int R, int which, double best_ms[2])
     return autotune(c, R, which, best_ms);
 }
 
+hzb_status hzb_tuned_config(const hzb_ctx *c, int R, int out[6])
+{
+    if (!c || !out) return HZB_EINVAL;
+    // the FP32 engine interbody32 takes for R right-hand sides
+    bool tc = c->nbody_engine == 1;
+    if (c->nbody_engine < 0) tc = (c->tune32_tc >= 0 && c->tune32_tc_R == R) ? c->tune32_tc == 1 : R >= 16;
+    int v = c->tune32_x2 >= 0 ? c->tune32_x2 : 1;
+    if (c->nbody_engine >= 2) v = c->nbody_engine - 2;
+    out[0] = tc ? 3 : v;
+    out[1] = c->tune32_tpt;
+    out[2] = c->tune32_split;
+    out[3] = c->nbody64_engine == 0 ? 0 : 1;
+    out[4] = c->tune64_tpt;
+    out[5] = c->tune64_split;
+    return HZB_OK;
+}
+
 hzb_status hzb_set_execution(hzb_ctx *c, int check_every, int use_graphs)
 {
     if (!c) return HZB_EINVAL;
@@ -477,7 +494,7 @@ hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *c, int engine)
 hzb_status hzb_set_interbody_engine(hzb_ctx *c, int engine)
 {
     if (!c) return HZB_EINVAL;
-    if (engine < -1 || engine > 3) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1, 2, 3}");
+    if (engine < -1 || engine > 4) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1, 2, 3, 4}");
     c->nbody_engine = engine;
     return HZB_OK;
 }

@@ -150,7 +150,8 @@ struct hzb_ctx {
     hzb::DevBuf<float2> sig32;                 // w_j sigma_j / (4 pi) in FP32, N x R (FP32 inter-body kernels)
     int tune64_tpt = 0, tune64_split = 0;      // 0: default
     int tune32_tpt = 0, tune32_split = 0;
-    int tune32_x2 = -1;                        // FP32 CUDA-core kernel: -1 default (packed), 0 scalar, 1 packed
+    int tune32_x2 = -1;                        // FP32 CUDA-core kernel: -1 default (packed), 0 scalar, 1 packed,
+                                               // 2 pair-symmetric packed
     int tune_limit_blocks = 0;                 // autotuner: time only the first blocks (0 = all)
     // double-float inter-body kernel: split positions/normals, cos/sin table, launch shape
     hzb::DevBuf<float4> dfa, dfb, dfc, dftab;
@@ -161,7 +162,8 @@ struct hzb_ctx {
     int use_graphs = -1;
     int modal_engine = -1;                     // FP32 modal GEMM: -1 auto, 0 CUDA cores, 1 tensor cores
     int nbody_engine = -1;                     // FP32 inter-body sum: -1 auto, 0 CUDA cores, 1 tensor cores,
-                                               // 2 CUDA cores scalar kernel, 3 CUDA cores packed-pair kernel
+                                               // 2 CUDA cores scalar kernel, 3 CUDA cores packed-pair kernel,
+                                               // 4 CUDA cores pair-symmetric packed kernel
     int tunetc_split = 0;                      // tensor-core inter-body source split (0: default)
     int tune32_tc = -1, tune32_tc_R = 0;       // autotuner's engine choice for R = tune32_tc_R (-1: none)
     std::vector<cudaGraphExec_t> gexec;        // captured Arnoldi step j
@@ -195,7 +197,9 @@ hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   
 hzb_status interbody_tc(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);
 const float2 *weighted_sigma32(hzb_ctx *c, int R, const double2 *sigma);      // nbody.cu; nullptr on failure
 hzb_status ensure_sctab(hzb_ctx *c);                                          // nbody.cu: FP64 cos/sin table
-hzb_status interbody64_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y);  // nbody_sym.cu  // nbody_tc.cu
+hzb_status interbody64_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y);  // nbody_sym.cu
+hzb_status interbody32_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tp);  // nbody_sym.cu
+hzb_status ensure_block_pairs(hzb_ctx *c);                                    // nbody_sym.cu  // nbody_tc.cu
 void split_reduce_f2(hzb_ctx *c, size_t n, int nsplit, const float2 *part, double2 *y);
 hzb_status interbody64_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit);
 hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tpt, int nsplit, bool x2);

@@ -520,8 +520,11 @@ hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
         int ns = c->tunetc_split > 0 ? c->tunetc_split : default_nsplit_tc(c, R);
         return interbody_tc(c, R, sigma, y, ns);
     }
-    // CUDA cores: packed-pair kernel unless the scalar one is asked for or tuned faster
-    const bool x2 = c->nbody_engine == 2 ? false : (c->nbody_engine == 3 ? true : c->tune32_x2 != 0);
+    // CUDA cores: variant 0 scalar, 1 packed pairs, 2 pair-symmetric packed
+    int v = c->tune32_x2 >= 0 ? c->tune32_x2 : 1;
+    if (c->nbody_engine >= 2) v = c->nbody_engine - 2;
+    if (v == 2) return interbody32_sym(c, R, sigma, y, (c->tune32_x2 == 2 && c->tune32_tpt == 1) ? 1 : 2);
+    const bool x2 = v == 1;
     int tpt = c->tune32_tpt > 0 ? c->tune32_tpt : 4;
     int ns = c->tune32_split > 0 ? c->tune32_split : default_nsplit(c, R, tpt);
     return interbody32_cfg(c, R, sigma, y, tpt, ns, x2);
@@ -663,13 +666,20 @@ namespace hzb {
 
 // Time one inter-body configuration: one warm-up launch, then the mean of `reps`
 // launches between CUDA events on the context's stream.
-static float time_cfg(hzb_ctx *c, int prec, int R, int tpt, int ns, bool x2, const double2 *x, double2 *y, int reps)
+static hzb_status run_cfg(hzb_ctx *c, int prec, int R, int tpt, int ns, int xv, const double2 *x, double2 *y)
 {
-    hzb_status st = prec ? interbody32_cfg(c, R, x, y, tpt, ns, x2) : interbody64_cfg(c, R, x, y, tpt, ns);
+    if (!prec) return interbody64_cfg(c, R, x, y, tpt, ns);
+    if (xv == 2) return interbody32_sym(c, R, x, y, tpt);
+    return interbody32_cfg(c, R, x, y, tpt, ns, xv == 1);
+}
+
+static float time_cfg(hzb_ctx *c, int prec, int R, int tpt, int ns, int xv, const double2 *x, double2 *y, int reps)
+{
+    hzb_status st = run_cfg(c, prec, R, tpt, ns, xv, x, y);
     if (st) return -1.f;
     cudaEventRecord(c->ev0, c->stream);
     for (int q = 0; q < reps; ++q) {
-        st = prec ? interbody32_cfg(c, R, x, y, tpt, ns, x2) : interbody64_cfg(c, R, x, y, tpt, ns);
+        st = run_cfg(c, prec, R, tpt, ns, xv, x, y);
         if (st) return -1.f;
     }
     cudaEventRecord(c->ev1, c->stream);
@@ -707,10 +717,19 @@ hzb_status autotune(hzb_ctx *c, int R, int which, double *best_ms)
         int bt = 0, bs = 0, bx = 0;
         float bm = 1e30f;
         const int tpts[3] = {1, 2, 4};
-        // FP32 kernel variants: 0 scalar, 1 packed pairs (unless the engine fixes one)
-        const int xmin = (prec && c->nbody_engine == 3) ? 1 : 0;
-        const int xmax = (prec && c->nbody_engine != 2) ? 1 : 0;
-        for (int xv = xmin; xv <= xmax; ++xv)
+        // FP32 kernel variants: 0 scalar, 1 packed pairs, 2 pair-symmetric packed
+        // (one of them when the engine fixes it)
+        int xmin = 0, xmax = prec ? 2 : 0;
+        if (prec && c->nbody_engine >= 2) xmin = xmax = c->nbody_engine - 2;
+        for (int xv = xmin; xv <= xmax; ++xv) {
+            if (xv == 2) {                  // no source split; TP = 1 or 2 packed target pairs
+                for (int tp = 1; tp <= 2; ++tp) {
+                    float ms = time_cfg(c, prec, R, tp, 1, xv, c->io_in.ptr, c->io_out.ptr, 3);
+                    if (ms < 0) return fail(c, HZB_ECUDA, "autotune launch failed");
+                    if (ms < bm) { bm = ms; bt = tp; bs = 1; bx = xv; }
+                }
+                continue;
+            }
             for (int a = 0; a < 3; ++a) {
                 int tpt = tpts[a];
                 if (prec == 0 && tpt == 4) continue;
@@ -719,11 +738,12 @@ hzb_status autotune(hzb_ctx *c, int R, int which, double *best_ms)
                 for (int b = 0; b < 5; ++b) {
                     if (b > 0 && cand[b] == cand[b - 1]) continue;
                     if (cand[b] > 64) continue;
-                    float ms = time_cfg(c, prec, R, tpt, cand[b], xv == 1, c->io_in.ptr, c->io_out.ptr, prec ? 3 : 1);
+                    float ms = time_cfg(c, prec, R, tpt, cand[b], xv, c->io_in.ptr, c->io_out.ptr, prec ? 3 : 1);
                     if (ms < 0) return fail(c, HZB_ECUDA, "autotune launch failed");
                     if (ms < bm) { bm = ms; bt = tpt; bs = cand[b]; bx = xv; }
                 }
             }
+        }
         if (prec && R >= 8 && c->nbody_engine < 0) {
             // the tensor-core contraction competes for the FP32 inter-body sum
             const int d = default_nsplit_tc(c, R);

@@ -44,6 +44,60 @@ __global__ void df_nodes_kernel(long long N, const double4 *__restrict__ pos, co
     cn[i] = make_float4(ny.hi, nz.hi, ny.lo, nz.lo);
 }
 
+// Geometry of a pair in double-float: d = x_i - x_j, r^2, 1/r (hardware estimate and one
+// Newton step) and r.
+struct DfGeom {
+    dfl dx, dy, dz, ir, r;
+};
+
+__device__ __forceinline__ DfGeom df_geom(dfl tx, dfl ty, dfl tz, float4 A4, float4 B4)
+{
+    DfGeom G;
+    const dfl sx = df_two_sum(tx.hi, -A4.x), sy = df_two_sum(ty.hi, -A4.y), sz = df_two_sum(tz.hi, -A4.z);
+    G.dx = df_fast_two_sum(sx.hi, sx.lo + (tx.lo - B4.x));
+    G.dy = df_fast_two_sum(sy.hi, sy.lo + (ty.lo - B4.y));
+    G.dz = df_fast_two_sum(sz.hi, sz.lo + (tz.lo - B4.z));
+    // r^2 (three positive squares)
+    const float px = G.dx.hi * G.dx.hi, py = G.dy.hi * G.dy.hi, pz = G.dz.hi * G.dz.hi;
+    const float ex = fmaf(2.f * G.dx.hi, G.dx.lo, fmaf(G.dx.hi, G.dx.hi, -px));
+    const float ey = fmaf(2.f * G.dy.hi, G.dy.lo, fmaf(G.dy.hi, G.dy.hi, -py));
+    const float ez = fmaf(2.f * G.dz.hi, G.dz.lo, fmaf(G.dz.hi, G.dz.hi, -pz));
+    const dfl s1 = df_two_sum(px, py), s2 = df_two_sum(s1.hi, pz);
+    const dfl r2 = df_fast_two_sum(s2.hi, s2.lo + s1.lo + ((ex + ey) + ez));
+    // 1/r: hardware estimate, one Newton step in double-float
+    const float y0 = rsqrtf(r2.hi);
+    const dfl y0sq = df_fast_two_sum(y0 * y0, fmaf(y0, y0, -(y0 * y0)));
+    const dfl u = df_mul(r2, y0sq);
+    const float e = (1.f - u.hi) - u.lo;
+    G.ir = df_fast_two_sum(y0, 0.5f * y0 * e);
+    G.r = df_mul(r2, G.ir);
+    return G;
+}
+
+// e^{ikr} in double-float: kr/(2 pi) reduced to [-1/2, 1/2] turns, then to the nearest
+// of DF_TAB table angles, Taylor series of the remainder (leading terms in
+// double-float, the tail in FP32) and angle addition with the table entry.
+__device__ __forceinline__ void df_cis(const DfConst &K, dfl r, const float4 *__restrict__ s_tab, dfl &cs, dfl &sn)
+{
+    const dfl turns = df_mul(df_mul(K.k, r), K.inv2pi);
+    const float n0 = rintf(turns.hi);
+    const dfl f = df_fast_two_sum(turns.hi - n0, turns.lo);            // [-1/2, 1/2] turns
+    const float mm = rintf(f.hi * (float)DF_TAB);
+    const dfl g = df_fast_two_sum(f.hi - mm * (1.f / DF_TAB), f.lo);    // |g| <= 1/256
+    const dfl dl = df_mul(g, K.twopi);                                  // |dl| <= pi/128
+    const dfl d2 = df_mul(dl, dl);
+    const dfl d3 = df_mul(d2, dl);
+    const float d2f = d2.hi;
+    dfl sd = df_sub(dl, df_mul(d3, K.inv6));
+    sd = df_addf(sd, dl.hi * d2f * d2f * fmaf(-d2f, 1.f / 5040.f, 1.f / 120.f));
+    dfl cd = df_add({1.f, 0.f}, {-0.5f * d2.hi, -0.5f * d2.lo});
+    cd = df_addf(cd, d2f * d2f * fmaf(-d2f, 1.f / 720.f, 1.f / 24.f));
+    const float4 T = s_tab[((int)mm) & (DF_TAB - 1)];
+    const dfl Ct = {T.x, T.y}, St = {T.z, T.w};
+    cs = df_sub(df_mul(Ct, cd), df_mul(St, sd));
+    sn = df_add(df_mul(St, cd), df_mul(Ct, sd));
+}
+
 template <int RC, int TPT>
 __global__ void __launch_bounds__(DF_TBLOCK / TPT)
 nbody_df_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pa,
@@ -95,49 +149,16 @@ nbody_df_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk,
                 const dfl nx = {A4.w, B4.w}, ny = {C4.x, C4.z}, nz = {C4.y, C4.w};
 #pragma unroll
                 for (int m = 0; m < TPT; ++m) {
-                    // d = x_i - x_j
-                    dfl sx = df_two_sum(tx[m].hi, -A4.x), sy = df_two_sum(ty[m].hi, -A4.y), sz = df_two_sum(tz[m].hi, -A4.z);
-                    const dfl dx = df_fast_two_sum(sx.hi, sx.lo + (tx[m].lo - B4.x));
-                    const dfl dy = df_fast_two_sum(sy.hi, sy.lo + (ty[m].lo - B4.y));
-                    const dfl dz = df_fast_two_sum(sz.hi, sz.lo + (tz[m].lo - B4.z));
-                    // r^2 (three positive squares)
-                    const float px = dx.hi * dx.hi, py = dy.hi * dy.hi, pz = dz.hi * dz.hi;
-                    const float ex = fmaf(2.f * dx.hi, dx.lo, fmaf(dx.hi, dx.hi, -px));
-                    const float ey = fmaf(2.f * dy.hi, dy.lo, fmaf(dy.hi, dy.hi, -py));
-                    const float ez = fmaf(2.f * dz.hi, dz.lo, fmaf(dz.hi, dz.hi, -pz));
-                    const dfl s1 = df_two_sum(px, py), s2 = df_two_sum(s1.hi, pz);
-                    const dfl r2 = df_fast_two_sum(s2.hi, s2.lo + s1.lo + ((ex + ey) + ez));
-                    // 1/r: hardware estimate, one Newton step in double-float
-                    const float y0 = rsqrtf(r2.hi);
-                    const dfl y0sq = df_fast_two_sum(y0 * y0, fmaf(y0, y0, -(y0 * y0)));
-                    const dfl u = df_mul(r2, y0sq);
-                    const float e = (1.f - u.hi) - u.lo;
-                    const dfl ir = df_fast_two_sum(y0, 0.5f * y0 * e);
-                    const dfl r = df_mul(r2, ir);
+                    const DfGeom G = df_geom(tx[m], ty[m], tz[m], A4, B4);
+                    const dfl dx = G.dx, dy = G.dy, dz = G.dz, ir = G.ir;
                     // n.d, A = n.d / r^3, B = k n.d / r^2 + eta / r
                     const dfl nd = df_add(df_add(df_mul(nx, dx), df_mul(ny, dy)), df_mul(nz, dz));
                     const dfl ir2 = df_mul(ir, ir);
                     const dfl ndir2 = df_mul(nd, ir2);
                     const dfl A = df_mul(ndir2, ir);
                     const dfl B = df_add(df_mul(K.k, ndir2), df_mul(K.eta, ir));
-                    // e^{ikr}
-                    const dfl turns = df_mul(df_mul(K.k, r), K.inv2pi);
-                    const float n0 = rintf(turns.hi);
-                    const dfl f = df_fast_two_sum(turns.hi - n0, turns.lo);            // [-1/2, 1/2] turns
-                    const float mm = rintf(f.hi * (float)DF_TAB);
-                    const dfl g = df_fast_two_sum(f.hi - mm * (1.f / DF_TAB), f.lo);    // |g| <= 1/256
-                    const dfl dl = df_mul(g, K.twopi);                                  // |dl| <= pi/128
-                    const dfl d2 = df_mul(dl, dl);
-                    const dfl d3 = df_mul(d2, dl);
-                    const float d2f = d2.hi;
-                    dfl sd = df_sub(dl, df_mul(d3, K.inv6));
-                    sd = df_addf(sd, dl.hi * d2f * d2f * fmaf(-d2f, 1.f / 5040.f, 1.f / 120.f));
-                    dfl cd = df_add({1.f, 0.f}, {-0.5f * d2.hi, -0.5f * d2.lo});
-                    cd = df_addf(cd, d2f * d2f * fmaf(-d2f, 1.f / 720.f, 1.f / 24.f));
-                    const float4 T = s_tab[((int)mm) & (DF_TAB - 1)];
-                    const dfl Ct = {T.x, T.y}, St = {T.z, T.w};
-                    const dfl cs = df_sub(df_mul(Ct, cd), df_mul(St, sd));
-                    const dfl sn = df_add(df_mul(St, cd), df_mul(Ct, sd));
+                    dfl cs, sn;
+                    df_cis(K, G.r, s_tab, cs, sn);
                     const dfl gre = df_add(df_mul(cs, A), df_mul(sn, B));
                     const dfl gim = df_sub(df_mul(sn, A), df_mul(cs, B));
 #pragma unroll
@@ -160,6 +181,144 @@ nbody_df_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk,
             for (int c = 0; c < RC; ++c)
                 if (r0 + c < R)
                     yo[(size_t)(tb.start + t) * R + r0 + c] = make_double2(df_to_double(ar[m][c]), df_to_double(ai[m][c]));
+    }
+}
+
+// Pair-symmetric version (as nbody64_sym_kernel, nbody_sym.cu): one CTA per unordered
+// pair of TargetBlocks on different bodies; d, 1/r and e^{ikr} of a node pair serve
+// both directions; a warp meets a 32-source tile in 32 rotation steps, the source-side
+// sums travel one lane down per step; FP64 atomic adds into y (zeroed first).
+static const int DFS_T = 512, DFS_S = 32;
+
+template <int RC>
+__global__ void __launch_bounds__(DFS_T, 1)
+nbody_df_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict__ blocks, int R,
+                    const float4 *__restrict__ pa, const float4 *__restrict__ pb, const float4 *__restrict__ pc,
+                    const double4 *__restrict__ pos64, const double2 *__restrict__ sigma,
+                    const float4 *__restrict__ tab, DfConst K, double2 *__restrict__ y)
+{
+    __shared__ float4 s_a[DFS_S], s_b[DFS_S], s_c[DFS_S];
+    __shared__ float4 s_sig[DFS_S][RC];              // re.hi, re.lo, im.hi, im.lo of w sigma / (4 pi)
+    __shared__ float4 s_tab[DF_TAB];
+    __shared__ float4 s_red[DFS_T / 32][RC][DFS_S];
+    const int2 pr = pairs[blockIdx.x];
+    const TargetBlock bi = blocks[pr.x], bj = blocks[pr.y];
+    const int r0 = blockIdx.y * RC;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int q = tid; q < DF_TAB; q += DFS_T) s_tab[q] = tab[q];
+    const bool live = tid < bi.count;
+    dfl tx = {1e5f + tid, 0.f}, ty = {1e5f, 0.f}, tz = {1e5f, 0.f};
+    dfl mx = {0.f, 0.f}, my = {0.f, 0.f}, mz = {0.f, 0.f};
+    dfl wr[RC], wi[RC], atr[RC], ati[RC];
+#pragma unroll
+    for (int c = 0; c < RC; ++c) { wr[c] = wi[c] = atr[c] = ati[c] = {0.f, 0.f}; }
+    if (live) {
+        const int g = bi.start + tid;
+        const float4 A = pa[g], B = pb[g], C = pc[g];
+        tx = {A.x, B.x}; ty = {A.y, B.y}; tz = {A.z, B.z};
+        mx = {A.w, B.w}; my = {C.x, C.z}; mz = {C.y, C.w};
+        const double wq = pos64[g].w * 0.07957747154594767;
+#pragma unroll
+        for (int c = 0; c < RC; ++c)
+            if (r0 + c < R) {
+                const double2 v = sigma[(size_t)g * R + r0 + c];
+                wr[c] = df_from_double(v.x * wq);
+                wi[c] = df_from_double(v.y * wq);
+            }
+    }
+    const bool warp_live = warp * 32 < bi.count;
+    for (int j0 = 0; j0 < bj.count; j0 += DFS_S) {
+        const int cnt = min(DFS_S, bj.count - j0);
+        __syncthreads();
+        if (tid < DFS_S) {
+            if (tid < cnt) {
+                const int g = bj.start + j0 + tid;
+                s_a[tid] = pa[g];
+                s_b[tid] = pb[g];
+                s_c[tid] = pc[g];
+                const double wq = pos64[g].w * 0.07957747154594767;
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const double2 v = (r0 + c < R) ? sigma[(size_t)g * R + r0 + c] : make_double2(0.0, 0.0);
+                    const dfl re = df_from_double(v.x * wq), im = df_from_double(v.y * wq);
+                    s_sig[tid][c] = make_float4(re.hi, re.lo, im.hi, im.lo);
+                }
+            } else {                                   // far, zero density: contributes 0 both ways
+                s_a[tid] = make_float4(-1e5f - tid, -1e5f, -1e5f, 0.f);
+                s_b[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                s_c[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < RC; ++c) s_sig[tid][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        dfl asr[RC], asi[RC];
+#pragma unroll
+        for (int c = 0; c < RC; ++c) asr[c] = asi[c] = {0.f, 0.f};
+        if (warp_live) {
+            for (int s = 0; s < DFS_S; ++s) {
+                const int q = (lane + s) & (DFS_S - 1);
+                const float4 A4 = s_a[q], B4 = s_b[q], C4 = s_c[q];
+                const DfGeom G = df_geom(tx, ty, tz, A4, B4);
+                const dfl ir2 = df_mul(G.ir, G.ir), eir = df_mul(K.eta, G.ir);
+                dfl cs, sn;
+                df_cis(K, G.r, s_tab, cs, sn);
+                // i <- j: normal of source j
+                const dfl nx = {A4.w, B4.w}, ny = {C4.x, C4.z}, nz = {C4.y, C4.w};
+                const dfl X1 = df_mul(df_add(df_add(df_mul(nx, G.dx), df_mul(ny, G.dy)), df_mul(nz, G.dz)), ir2);
+                const dfl A1 = df_mul(X1, G.ir), B1 = df_add(df_mul(K.k, X1), eir);
+                const dfl g1r = df_add(df_mul(cs, A1), df_mul(sn, B1));
+                const dfl g1i = df_sub(df_mul(sn, A1), df_mul(cs, B1));
+                // j <- i: normal of target i, d reversed
+                const dfl X2p = df_mul(df_add(df_add(df_mul(mx, G.dx), df_mul(my, G.dy)), df_mul(mz, G.dz)), ir2);
+                const dfl A2n = df_mul(X2p, G.ir), B2 = df_sub(eir, df_mul(K.k, X2p));
+                const dfl g2r = df_sub(df_mul(sn, B2), df_mul(cs, A2n));
+                const dfl h = df_add(df_mul(sn, A2n), df_mul(cs, B2));
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const float4 S = s_sig[q][c];
+                    const dfl sr = {S.x, S.y}, si = {S.z, S.w};
+                    atr[c] = df_add(atr[c], df_sub(df_mul(g1r, sr), df_mul(g1i, si)));
+                    ati[c] = df_add(ati[c], df_add(df_mul(g1r, si), df_mul(g1i, sr)));
+                    asr[c] = df_add(asr[c], df_add(df_mul(g2r, wr[c]), df_mul(h, wi[c])));
+                    asi[c] = df_add(asi[c], df_sub(df_mul(g2r, wi[c]), df_mul(h, wr[c])));
+                }
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const int from = (lane + 1) & 31;
+                    asr[c].hi = __shfl_sync(0xffffffffu, asr[c].hi, from);
+                    asr[c].lo = __shfl_sync(0xffffffffu, asr[c].lo, from);
+                    asi[c].hi = __shfl_sync(0xffffffffu, asi[c].hi, from);
+                    asi[c].lo = __shfl_sync(0xffffffffu, asi[c].lo, from);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < RC; ++c) s_red[warp][c][lane] = make_float4(asr[c].hi, asr[c].lo, asi[c].hi, asi[c].lo);
+        __syncthreads();
+        if (tid < DFS_S * RC) {
+            const int src = tid & (DFS_S - 1), c = tid / DFS_S;
+            if (src < cnt && r0 + c < R) {
+                dfl sr = {0.f, 0.f}, si = {0.f, 0.f};
+                for (int w = 0; w < DFS_T / 32; ++w) {
+                    const float4 v = s_red[w][c][src];
+                    sr = df_add(sr, {v.x, v.y});
+                    si = df_add(si, {v.z, v.w});
+                }
+                double2 *o = y + (size_t)(bj.start + j0 + src) * R + r0 + c;
+                atomicAdd(&o->x, df_to_double(sr));
+                atomicAdd(&o->y, df_to_double(si));
+            }
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int c = 0; c < RC; ++c)
+            if (r0 + c < R) {
+                double2 *o = y + (size_t)(bi.start + tid) * R + r0 + c;
+                atomicAdd(&o->x, df_to_double(atr[c]));
+                atomicAdd(&o->y, df_to_double(ati[c]));
+            }
     }
 }
 
@@ -207,11 +366,49 @@ static void launch_df(hzb_ctx *c, dim3 g, int N, int R, int chunk, const double2
                                                                    c->dftab.ptr, K, o, st);
 }
 
+static DfConst df_constants(const hzb_ctx *c)
+{
+    DfConst K;
+    K.k = df_from_double(c->k);
+    K.eta = df_from_double(c->eta);
+    K.inv2pi = df_from_double(1.0 / (2.0 * M_PI));
+    K.twopi = df_from_double(2.0 * M_PI);
+    K.inv6 = df_from_double(1.0 / 6.0);
+    return K;
+}
+
+static hzb_status interbody_df_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
+{
+    if (c->capturing && c->n_blockpairs == 0) return fail(c, HZB_ESTATE, "block pairs not built before capture");
+    hzb_status st = ensure_block_pairs(c);
+    if (st) return st;
+    const size_t n = (size_t)c->N * R;
+    if (check_cuda(c, cudaMemsetAsync(y, 0, n * sizeof(double2), c->stream), "zero y")) return HZB_ECUDA;
+    c->interbody_calls++;
+    if (c->n_blockpairs < 0) return HZB_OK;
+    if (c->n_blockpairs > 0x7fffffffLL) return fail(c, HZB_EINVAL, "too many block pairs for one launch");
+    c->launches += 1;
+    const DfConst K = df_constants(c);
+    const int slot = prof_begin(c, 2);
+    const int rc = (R == 1) ? 1 : 2;
+    dim3 g((unsigned)c->n_blockpairs, (R + rc - 1) / rc, 1);
+    if (rc == 1)
+        nbody_df_sym_kernel<1><<<g, DFS_T, 0, c->stream>>>(c->blockpairs.ptr, c->tblocks.ptr, R, c->dfa.ptr, c->dfb.ptr,
+                                                           c->dfc.ptr, c->pos64.ptr, sigma, c->dftab.ptr, K, y);
+    else
+        nbody_df_sym_kernel<2><<<g, DFS_T, 0, c->stream>>>(c->blockpairs.ptr, c->tblocks.ptr, R, c->dfa.ptr, c->dfb.ptr,
+                                                           c->dfc.ptr, c->pos64.ptr, sigma, c->dftab.ptr, K, y);
+    cudaError_t e = cudaGetLastError();
+    prof_end(c, slot);
+    return check_cuda(c, e, "nbody_df_sym_kernel");
+}
+
 hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 {
     if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
     hzb_status st = ensure_df(c);
     if (st) return st;
+    if (c->nbody64_engine != 0) return interbody_df_sym(c, R, sigma, y);
     const int N = (int)c->N;
     const int rc = R == 1 ? 1 : (R <= 4 ? 4 : 8);
     const int tpt = c->tunedf_tpt > 0 ? c->tunedf_tpt : 1;
@@ -225,12 +422,7 @@ hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
         if (check_cuda(c, c->nb_part64.ensure(n * nsplit), "alloc partial sums")) return HZB_ENOMEM;
         out = c->nb_part64.ptr;
     }
-    DfConst K;
-    K.k = df_from_double(c->k);
-    K.eta = df_from_double(c->eta);
-    K.inv2pi = df_from_double(1.0 / (2.0 * M_PI));
-    K.twopi = df_from_double(2.0 * M_PI);
-    K.inv6 = df_from_double(1.0 / 6.0);
+    const DfConst K = df_constants(c);
     c->interbody_calls++;
     c->launches += (nsplit > 1) ? 2 : 1;
     const int slot = prof_begin(c, 2);

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "f32x2.cuh"
 #include "fp64_pair.cuh"
 #include "hzb_internal.h"
 #include "kernel_math.cuh"
@@ -158,8 +159,176 @@ nbody64_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict
     }
 }
 
+// FP32 version for the inner solve, with packed f32x2 pairs (f32x2.cuh): thread t
+// owns TP pairs of targets (t + 2p NT, t + (2p + 1) NT), packed in the two halves of
+// each register pair, and meets one source per step as above, so one f32x2
+// instruction serves two unordered node pairs.  The rotating source sums keep the
+// two halves apart and add them at the end of the tile.  Densities come pre-weighted
+// in FP32 (weighted_sigma32); the phase is reduced as in nbody32x2_kernel.
+template <int RC, int TP>
+__global__ void __launch_bounds__(SYM_T / (2 * TP), 1)
+nbody32_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict__ blocks, int R,
+                   const float4 *__restrict__ pos, const float4 *__restrict__ nrm, const float2 *__restrict__ sw,
+                   float k, float eta, float kt, double2 *__restrict__ y)
+{
+    constexpr int NT = SYM_T / (2 * TP);
+    constexpr int NW = NT / 32;
+    __shared__ float4 s_g0[SYM_S];               // x, y, z, nx
+    __shared__ float2 s_g1[SYM_S];               // ny, nz
+    __shared__ float2 s_w[SYM_S][RC];
+    __shared__ float2 s_red[NW][RC][SYM_S];
+    const int2 pr = pairs[blockIdx.x];
+    const TargetBlock bi = blocks[pr.x], bj = blocks[pr.y];
+    const int r0 = blockIdx.y * RC;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    f2x tx[TP], ty[TP], tz[TP], mx[TP], my[TP], mz[TP];
+    f2x wr[TP][RC], wi[TP][RC], nwr[TP][RC], atx[TP][RC], aty[TP][RC];
+#pragma unroll
+    for (int p = 0; p < TP; ++p) {
+        float4 P[2], Q[2];
+        float2 V[2][RC];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = tid + (2 * p + h) * NT;
+            const bool live = t < bi.count;
+            P[h] = live ? pos[bi.start + t] : make_float4(1e5f + t, 1e5f, 1e5f, 0.f);
+            Q[h] = live ? nrm[bi.start + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                V[h][c] = (live && r0 + c < R) ? sw[(size_t)(bi.start + t) * R + r0 + c] : make_float2(0.f, 0.f);
+        }
+        tx[p] = f2_pack(P[0].x, P[1].x); ty[p] = f2_pack(P[0].y, P[1].y); tz[p] = f2_pack(P[0].z, P[1].z);
+        mx[p] = f2_pack(Q[0].x, Q[1].x); my[p] = f2_pack(Q[0].y, Q[1].y); mz[p] = f2_pack(Q[0].z, Q[1].z);
+#pragma unroll
+        for (int c = 0; c < RC; ++c) {
+            wr[p][c] = f2_pack(V[0][c].x, V[1][c].x);
+            wi[p][c] = f2_pack(V[0][c].y, V[1][c].y);
+            nwr[p][c] = f2_pack(-V[0][c].x, -V[1][c].x);
+            atx[p][c] = aty[p][c] = 0ull;
+        }
+    }
+    const bool warp_live = warp * 32 < bi.count;
+    const f2x k2 = f2_splat(k), nk2 = f2_splat(-k), eta2 = f2_splat(eta), kt2 = f2_splat(kt);
+    const f2x rnd2 = f2_splat(12582912.0f), twopi2 = f2_splat(6.283185307179586f);
+    for (int j0 = 0; j0 < bj.count; j0 += SYM_S) {
+        const int cnt = min(SYM_S, bj.count - j0);
+        __syncthreads();
+        if (tid < SYM_S) {
+            if (tid < cnt) {
+                const float4 p = pos[bj.start + j0 + tid], n = nrm[bj.start + j0 + tid];
+                s_g0[tid] = make_float4(p.x, p.y, p.z, n.x);
+                s_g1[tid] = make_float2(n.y, n.z);
+#pragma unroll
+                for (int c = 0; c < RC; ++c)
+                    s_w[tid][c] = (r0 + c < R) ? sw[(size_t)(bj.start + j0 + tid) * R + r0 + c] : make_float2(0.f, 0.f);
+            } else {                                   // far, zero density: contributes 0 both ways
+                s_g0[tid] = make_float4(-1e5f - tid, -1e5f, -1e5f, 0.f);
+                s_g1[tid] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < RC; ++c) s_w[tid][c] = make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        f2x asx[RC], asy[RC];
+#pragma unroll
+        for (int c = 0; c < RC; ++c) asx[c] = asy[c] = 0ull;
+        if (warp_live) {
+#pragma unroll 2
+            for (int s = 0; s < SYM_S; ++s) {
+                const int q = (lane + s) & (SYM_S - 1);
+                const float4 g0 = s_g0[q];
+                const float2 g1 = s_g1[q];
+                const f2x sx = f2_splat(g0.x), sy = f2_splat(g0.y), sz = f2_splat(g0.z);
+                const f2x snx = f2_splat(g0.w), sny = f2_splat(g1.x), snz = f2_splat(g1.y);
+                f2x swr[RC], swi[RC], nswi[RC];
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const float2 v = s_w[q][c];
+                    swr[c] = f2_splat(v.x); swi[c] = f2_splat(v.y); nswi[c] = f2_splat(-v.y);
+                }
+#pragma unroll
+                for (int p = 0; p < TP; ++p) {
+                    const f2x dx = f2_sub(tx[p], sx), dy = f2_sub(ty[p], sy), dz = f2_sub(tz[p], sz);
+                    const f2x r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+                    float r2a, r2b;
+                    f2_unpack(r2, r2a, r2b);
+                    const f2x ir = f2_pack(rsqrtf(r2a), rsqrtf(r2b));
+                    const f2x ir2 = f2_mul(ir, ir), eir = f2_mul(eta2, ir);
+                    const f2x t = f2_mul(f2_mul(r2, ir), kt2);
+                    const f2x th = f2_mul(f2_sub(t, f2_sub(f2_add(t, rnd2), rnd2)), twopi2);
+                    float tha, thb, sa, ca, sb, cb;
+                    f2_unpack(th, tha, thb);
+                    __sincosf(tha, &sa, &ca);
+                    __sincosf(thb, &sb, &cb);
+                    const f2x s2 = f2_pack(sa, sb), c2 = f2_pack(ca, cb);
+                    // target <- source q
+                    const f2x X1 = f2_mul(f2_fma(snx, dx, f2_fma(sny, dy, f2_mul(snz, dz))), ir2);
+                    const f2x A1 = f2_mul(X1, ir), B1 = f2_fma(k2, X1, eir);
+                    const f2x g1r = f2_fma(c2, A1, f2_mul(s2, B1));
+                    const f2x g1i = f2_sub(f2_mul(s2, A1), f2_mul(c2, B1));
+                    // source q <- target (d reversed)
+                    const f2x X2p = f2_mul(f2_fma(mx[p], dx, f2_fma(my[p], dy, f2_mul(mz[p], dz))), ir2);
+                    const f2x A2n = f2_mul(X2p, ir), B2 = f2_fma(nk2, X2p, eir);
+                    const f2x g2r = f2_sub(f2_mul(s2, B2), f2_mul(c2, A2n));
+                    const f2x h = f2_fma(s2, A2n, f2_mul(c2, B2));
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) {
+                        atx[p][c] = f2_fma(g1r, swr[c], f2_fma(g1i, nswi[c], atx[p][c]));
+                        aty[p][c] = f2_fma(g1r, swi[c], f2_fma(g1i, swr[c], aty[p][c]));
+                        asx[c] = f2_fma(g2r, wr[p][c], f2_fma(h, wi[p][c], asx[c]));
+                        asy[c] = f2_fma(g2r, wi[p][c], f2_fma(h, nwr[p][c], asy[c]));
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    asx[c] = __shfl_sync(0xffffffffu, asx[c], (lane + 1) & 31);
+                    asy[c] = __shfl_sync(0xffffffffu, asy[c], (lane + 1) & 31);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < RC; ++c) {
+            float xa, xb, ya, yb;
+            f2_unpack(asx[c], xa, xb);
+            f2_unpack(asy[c], ya, yb);
+            s_red[warp][c][lane] = make_float2(xa + xb, ya + yb);
+        }
+        __syncthreads();
+        if (tid < SYM_S * RC) {
+            const int src = tid & (SYM_S - 1), c = tid / SYM_S;
+            if (src < cnt && r0 + c < R) {
+                float sx = 0.f, sy = 0.f;
+                for (int w = 0; w < NW; ++w) {
+                    sx += s_red[w][c][src].x;
+                    sy += s_red[w][c][src].y;
+                }
+                double2 *o = y + (size_t)(bj.start + j0 + src) * R + r0 + c;
+                atomicAdd(&o->x, (double)sx);
+                atomicAdd(&o->y, (double)sy);
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < TP; ++p)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = tid + (2 * p + h) * NT;
+            if (t >= bi.count) continue;
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                if (r0 + c < R) {
+                    float xa, xb, ya, yb;
+                    f2_unpack(atx[p][c], xa, xb);
+                    f2_unpack(aty[p][c], ya, yb);
+                    double2 *o = y + (size_t)(bi.start + t) * R + r0 + c;
+                    atomicAdd(&o->x, (double)(h ? xb : xa));
+                    atomicAdd(&o->y, (double)(h ? yb : ya));
+                }
+        }
+}
+
 // Unordered pairs of target blocks on different bodies, built once per geometry.
-static hzb_status ensure_block_pairs(hzb_ctx *c)
+hzb_status ensure_block_pairs(hzb_ctx *c)
 {
     if (c->n_blockpairs > 0) return HZB_OK;
     std::vector<TargetBlock> tb(c->n_tblocks);
@@ -212,6 +381,45 @@ hzb_status interbody64_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
     cudaError_t e = cudaGetLastError();
     prof_end(c, slot);
     return check_cuda(c, e, "nbody64_sym_kernel");
+}
+
+template <int RC, int TP>
+static void launch_sym32(hzb_ctx *c, dim3 g, int R, const float2 *sw, double2 *y)
+{
+    nbody32_sym_kernel<RC, TP><<<g, SYM_T / (2 * TP), 0, c->stream>>>(
+        c->blockpairs.ptr, c->tblocks.ptr, R, c->pos32.ptr, c->nrm32.ptr, sw, (float)c->k, (float)c->eta,
+        (float)(c->k / (2.0 * M_PI)), y);
+}
+
+hzb_status interbody32_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int tp)
+{
+    if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
+    if (c->capturing && c->n_blockpairs == 0) return fail(c, HZB_ESTATE, "block pairs not built before capture");
+    hzb_status st = ensure_block_pairs(c);
+    if (st) return st;
+    const size_t n = (size_t)c->N * R;
+    if (check_cuda(c, cudaMemsetAsync(y, 0, n * sizeof(double2), c->stream), "zero y")) return HZB_ECUDA;
+    c->interbody_calls++;
+    if (c->n_blockpairs < 0) return HZB_OK;
+    if (c->n_blockpairs > 0x7fffffffLL) return fail(c, HZB_EINVAL, "too many block pairs for one launch");
+    const int slot = prof_begin(c, 1);
+    const float2 *sw = weighted_sigma32(c, R, sigma);
+    if (!sw) return HZB_ENOMEM;
+    c->launches += 1;
+    const int rc = (R == 1) ? 1 : (R == 2 ? 2 : 4);
+    dim3 g((unsigned)c->n_blockpairs, (R + rc - 1) / rc, 1);
+    if (tp == 2) {
+        if (rc == 1) launch_sym32<1, 2>(c, g, R, sw, y);
+        else if (rc == 2) launch_sym32<2, 2>(c, g, R, sw, y);
+        else launch_sym32<4, 2>(c, g, R, sw, y);
+    } else {
+        if (rc == 1) launch_sym32<1, 1>(c, g, R, sw, y);
+        else if (rc == 2) launch_sym32<2, 1>(c, g, R, sw, y);
+        else launch_sym32<4, 1>(c, g, R, sw, y);
+    }
+    cudaError_t e = cudaGetLastError();
+    prof_end(c, slot);
+    return check_cuda(c, e, "nbody32_sym_kernel");
 }
 
 }  // namespace hzb

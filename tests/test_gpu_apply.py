@@ -66,11 +66,12 @@ def test_interbody_fp32(pair, R):
     assert rel_l2(got, ref) < 2e-6
 
 
-@pytest.mark.parametrize("engine", [2, 3])
-@pytest.mark.parametrize("R", [1, 5, 9])
+@pytest.mark.parametrize("engine", [2, 3, 4])
+@pytest.mark.parametrize("R", [1, 2, 5, 9])
 def test_interbody_fp32_kernel_variants(pair, R, engine):
-    """Scalar (2) and packed-pair f32x2 (3) FP32 CUDA-core kernels, each forced, over
-    ragged source tiles (odd node counts) and ragged right-hand-side chunks (R = 5, 9)."""
+    """Scalar (2), packed-pair f32x2 (3) and pair-symmetric packed (4) FP32 CUDA-core
+    kernels, each forced, over ragged source tiles (odd node counts) and ragged
+    right-hand-side chunks (R = 5, 9)."""
     s, P = pair
     sig = rand_c((P.N, R), 151 + R)
     ref = P.interbody(sig)
@@ -141,7 +142,7 @@ def test_spheroids_258560_sampled_rows():
     assert np.abs(y64[rows] - ref).max() < 1e-11 * np.abs(ref).max()
     # FP32: the phase k r carries the relative error of r (~2 ulp after the hardware
     # reciprocal square root) times k r <= 4 x 14 here, ~1e-5 per term at most.
-    for engine in (2, 3):
+    for engine in (2, 3, 4):
         s.set_interbody_engine(engine)
         y32 = s.interbody(sig, precision=1)
         assert rel_l2(y32[rows], ref) < 3e-5, engine
@@ -154,12 +155,18 @@ def test_spheroids_258560_sampled_rows():
     assert rel_l2(ytc[rows], ref16) < 3e-5
 
 
+@pytest.mark.parametrize("engine", [0, 1])
 @pytest.mark.parametrize("R", [1, 3, 9])
-def test_interbody_double_float(pair, R):
-    """Double-float (two FP32 numbers) inter-body sum: FP64-class accuracy."""
+def test_interbody_double_float(pair, R, engine):
+    """Double-float (two FP32 numbers) inter-body sum: FP64-class accuracy; the
+    one-directional (0) and the pair-symmetric (1) kernel."""
     s, P = pair
     sig = rand_c((P.N, R), 81 + R)
-    got = s.interbody(sig, precision=2)
+    s.set_fp64_interbody_engine(engine)
+    try:
+        got = s.interbody(sig, precision=2)
+    finally:
+        s.set_fp64_interbody_engine(-1)
     ref = P.interbody(sig)
     assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
 
