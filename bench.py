@@ -302,7 +302,8 @@ def main():
     sigdf = s.get_density()[:, 0]
     mixed_df = {"value": 1e3 * len(dft) / sum(dft), "unit": "RHS solves/s", "ms_per_solve": sum(dft) / len(dft),
                 "density_err_vs_fp64_reference": float(np.linalg.norm(sigdf - sig_ref) / np.linalg.norm(sig_ref)),
-                "residual_kernel": "nbody_df_kernel (double-float, ~48-bit significand)",
+                "residual_kernel": ("nbody_df_sym_kernel" if kernels["fp64_kernel"] == "nbody64_sym_kernel"
+                                    else "nbody_df_kernel") + " (double-float, ~48-bit significand)",
                 "nbody_df_ms_per_launch": dfst[-1].t_nbodydf_ms / max(dfst[-1].n_nbodydf, 1),
                 "nbody32_ms_per_launch": dfst[-1].t_nbody32_ms / max(dfst[-1].n_nbody32, 1),
                 "outer_iterations": dfst[-1].outer_iterations, "inner_iterations": dfst[-1].iterations}

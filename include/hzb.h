@@ -157,14 +157,14 @@ hzb_status hzb_build_scattering_matrices(hzb_ctx *ctx);
  * chunks per target block) for R right-hand sides: times each candidate with CUDA
  * events on the context's stream and keeps the fastest for later calls.
  * which: bit 0 = FP32 kernel, bit 1 = FP64 kernel.  For the FP32 sum with R >= 8 and
- * the engine on automatic (hzb_set_interbody_engine -1) the tensor-core contraction
- * is timed as well and, for this R, the faster engine is kept.  best_ms (may be NULL):
+ * the engine on automatic (hzb_set_interbody_engine -1) the tensor-core contractions
+ * (mma.sync and tcgen05) are timed as well and, for this R, the fastest engine is kept.  best_ms (may be NULL):
  * the fastest time per launch [FP32, FP64].  Not part of the paper: a GB300 tuning aid. */
 hzb_status hzb_autotune(hzb_ctx *ctx, int R, int which, double best_ms[2]);
 
 /* The inter-body kernels the context will launch for R right-hand sides (host only,
  * no GPU work), written to out[6]: [0] FP32 kernel: 0 scalar, 1 packed pairs,
- * 2 pair-symmetric packed, 3 tensor cores; [1] its targets (or packed target pairs)
+ * 2 pair-symmetric packed, 3 tensor cores (mma.sync), 4 tensor cores (tcgen05); [1] its targets (or packed target pairs)
  * per thread, 0 = default; [2] its source chunks, 0 = default; [3] FP64 kernel:
  * 0 one-directional, 1 pair-symmetric; [4], [5] the one-directional FP64 kernel's
  * targets per thread and source chunks (0 = default).  HZB_EINVAL on NULL. */
@@ -195,8 +195,10 @@ hzb_status hzb_set_modal_engine(hzb_ctx *ctx, int engine);
  * 2 = CUDA cores, scalar FP32 kernel; 3 = CUDA cores, packed-pair kernel (two sources
  * per f32x2 instruction); 4 = CUDA cores, pair-symmetric packed kernel (each unordered
  * node pair evaluated once for both directions, results added with FP64 atomics: equal
- * to rounding between runs, not bit for bit); -1 (default) = tensor cores when R >= 16
- * (or as tuned), else as 0.  Returns HZB_EINVAL for other values. */
+ * to rounding between runs, not bit for bit); 5 = tensor cores through tcgen05 (TF32
+ * three-term split, accumulators in tensor memory, 16 or 32 right-hand sides per CTA);
+ * -1 (default) = tcgen05 tensor cores when R >= 16, else as 0, unless hzb_autotune
+ * timed the engines for this R.  Returns HZB_EINVAL for other values. */
 hzb_status hzb_set_interbody_engine(hzb_ctx *ctx, int engine);
 
 /* Engine of the FP64 and double-float inter-body sums (Sec. 3.3): 0 = one-directional
@@ -204,8 +206,9 @@ hzb_status hzb_set_interbody_engine(hzb_ctx *ctx, int engine);
  * bit-reproducible); 1 = pair-symmetric kernels: each unordered pair of nodes on
  * different bodies is evaluated once for both directions (r, 1/r and e^{ikr} are
  * shared), about 1.5x fewer operations; both directions are added into y with FP64
- * atomics, so runs agree to rounding but not bit for bit; -1 (default) = 1.  Returns
- * HZB_EINVAL for other values.  Not part of the paper: a GB300 choice (FP64 runs at
+ * atomics, so runs agree to rounding but not bit for bit; -1 (default) = 1 for R <= 4
+ * right-hand sides, 0 above (the one-directional kernels amortise the pair geometry over
+ * up to 8 right-hand sides per CTA).  Returns HZB_EINVAL for other values.  Not part of the paper: a GB300 choice (FP64 runs at
  * 1/64 of the FP32 rate). */
 hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *ctx, int engine);
 

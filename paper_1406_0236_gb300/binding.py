@@ -206,12 +206,12 @@ class Solver:
 
     def set_interbody_engine(self, engine: int):
         """FP32 inter-body sum engine: 0 CUDA cores, 1 tensor cores, 2 scalar CUDA-core kernel,
-        3 packed-pair CUDA-core kernel, 4 pair-symmetric packed kernel, -1 auto (tensor cores
-        for R >= 16 or as tuned)."""
+        3 packed-pair CUDA-core kernel, 4 pair-symmetric packed kernel, 5 tcgen05 tensor cores,
+        -1 auto (tensor cores for R >= 16 or as tuned)."""
         self._check(lib().hzb_set_interbody_engine(self._h, int(engine)))
 
     def set_fp64_interbody_engine(self, engine: int):
-        """FP64 inter-body sum engine: 0 one-directional, 1 pair-symmetric, -1 auto (1)."""
+        """FP64/double-float inter-body engine: 0 one-directional, 1 pair-symmetric, -1 auto (1 for R <= 4)."""
         self._check(lib().hzb_set_fp64_interbody_engine(self._h, int(engine)))
 
     def set_options(self, **kw):
@@ -262,7 +262,7 @@ class Solver:
         self._check(lib().hzb_autotune(self._h, int(R), int(which), _ptr(best)))
         return best
 
-    FP32_KERNELS = ("nbody32_kernel", "nbody32x2_kernel", "nbody32_sym_kernel", "nbody_tc_kernel")
+    FP32_KERNELS = ("nbody32_kernel", "nbody32x2_kernel", "nbody32_sym_kernel", "nbody_tc_kernel", "nbody_tc5_kernel")
 
     def tuned_config(self, R: int = 1) -> dict:
         """The inter-body kernels this solver launches for R right-hand sides."""

@@ -122,7 +122,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     c->yhat32.release(); c->that32.release(); c->s_b.release(); c->s_r.release(); c->s_d.release();
     c->io_in.release(); c->io_out.release(); c->io_small.release(); c->tiny.release(); c->sol.release();
     c->red.release(); c->krylov.release(); c->small.release();
-    c->sctab.release(); c->nb_part64.release(); c->nb_part32.release(); c->sig32.release(); c->blockpairs.release();
+    c->sctab.release(); c->nb_part64.release(); c->nb_part32.release(); c->sig32.release(); c->blockpairs.release(); c->kerr.release();
     c->dfa.release(); c->dfb.release(); c->dfc.release(); c->dftab.release();
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
     release_graphs(c);
@@ -452,14 +452,16 @@ hzb_status hzb_tuned_config(const hzb_ctx *c, int R, int out[6])
 {
     if (!c || !out) return HZB_EINVAL;
     // the FP32 engine interbody32 takes for R right-hand sides
-    bool tc = c->nbody_engine == 1;
-    if (c->nbody_engine < 0) tc = (c->tune32_tc >= 0 && c->tune32_tc_R == R) ? c->tune32_tc == 1 : R >= 16;
-    int v = c->tune32_x2 >= 0 ? c->tune32_x2 : 1;
-    if (c->nbody_engine >= 2) v = c->nbody_engine - 2;
-    out[0] = tc ? 3 : v;
+    int e = -1;
+    if (c->nbody_engine == 1) e = 1;
+    else if (c->nbody_engine == 5) e = 2;
+    else if (c->nbody_engine < 0) e = (c->tune32_tc >= 0 && c->tune32_tc_R == R) ? c->tune32_tc : (R >= 16 ? 2 : 0);
+    int v = (c->tune32_x2 >= 0 && c->tune32_R == R) ? c->tune32_x2 : (R <= 2 ? 2 : 1);
+    if (c->nbody_engine >= 2 && c->nbody_engine <= 4) v = c->nbody_engine - 2;
+    out[0] = e == 2 ? 4 : (e == 1 ? 3 : v);
     out[1] = c->tune32_tpt;
     out[2] = c->tune32_split;
-    out[3] = c->nbody64_engine == 0 ? 0 : 1;
+    out[3] = (c->nbody64_engine == 1 || (c->nbody64_engine < 0 && R <= 4)) ? 1 : 0;
     out[4] = c->tune64_tpt;
     out[5] = c->tune64_split;
     return HZB_OK;
@@ -494,7 +496,7 @@ hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *c, int engine)
 hzb_status hzb_set_interbody_engine(hzb_ctx *c, int engine)
 {
     if (!c) return HZB_EINVAL;
-    if (engine < -1 || engine > 4) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1, 2, 3, 4}");
+    if (engine < -1 || engine > 5) return fail(c, HZB_EINVAL, "engine in {-1, 0, ..., 5}");
     c->nbody_engine = engine;
     return HZB_OK;
 }

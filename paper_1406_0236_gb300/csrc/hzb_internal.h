@@ -146,10 +146,14 @@ struct hzb_ctx {
     hzb::DevBuf<float2> nb_part32;
     hzb::DevBuf<int2> blockpairs;              // unordered TargetBlock pairs on different bodies (nbody_sym.cu)
     long long n_blockpairs = 0;                // 0: not built, -1: none (one body)
-    int nbody64_engine = -1;                   // FP64 inter-body sum: -1 auto (pair-symmetric), 0 one-directional, 1 symmetric
+    int nbody64_engine = -1;                   // FP64/double-float sums: -1 auto (pair-symmetric for R <= 4),
+                                               // 0 one-directional, 1 pair-symmetric
+    hzb::DevBuf<int> kerr;                     // device error flag of kernels with bounded waits
+    bool kerr_ready = false;
     hzb::DevBuf<float2> sig32;                 // w_j sigma_j / (4 pi) in FP32, N x R (FP32 inter-body kernels)
     int tune64_tpt = 0, tune64_split = 0;      // 0: default
     int tune32_tpt = 0, tune32_split = 0;
+    int tune32_R = 0;                          // R the FP32 variant was tuned for
     int tune32_x2 = -1;                        // FP32 CUDA-core kernel: -1 default (packed), 0 scalar, 1 packed,
                                                // 2 pair-symmetric packed
     int tune_limit_blocks = 0;                 // autotuner: time only the first blocks (0 = all)
@@ -163,7 +167,8 @@ struct hzb_ctx {
     int modal_engine = -1;                     // FP32 modal GEMM: -1 auto, 0 CUDA cores, 1 tensor cores
     int nbody_engine = -1;                     // FP32 inter-body sum: -1 auto, 0 CUDA cores, 1 tensor cores,
                                                // 2 CUDA cores scalar kernel, 3 CUDA cores packed-pair kernel,
-                                               // 4 CUDA cores pair-symmetric packed kernel
+                                               // 4 CUDA cores pair-symmetric packed kernel,
+                                               // 5 tensor cores with tcgen05 (TMEM accumulators)
     int tunetc_split = 0;                      // tensor-core inter-body source split (0: default)
     int tune32_tc = -1, tune32_tc_R = 0;       // autotuner's engine choice for R = tune32_tc_R (-1: none)
     std::vector<cudaGraphExec_t> gexec;        // captured Arnoldi step j
@@ -195,6 +200,7 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   // nbody_df.cu
 hzb_status interbody_tc(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);
+hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);   // nbody_tc5.cu
 const float2 *weighted_sigma32(hzb_ctx *c, int R, const double2 *sigma);      // nbody.cu; nullptr on failure
 hzb_status ensure_sctab(hzb_ctx *c);                                          // nbody.cu: FP64 cos/sin table
 hzb_status interbody64_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y);  // nbody_sym.cu

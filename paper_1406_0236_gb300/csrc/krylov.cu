@@ -395,7 +395,7 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
         graph_key.tpt64 = c->tune64_tpt; graph_key.split64 = c->tune64_split;
         graph_key.modal_engine = c->modal_engine; graph_key.nbody_engine = c->nbody_engine;
         graph_key.splittc = c->tunetc_split; graph_key.tc32 = c->tune32_tc * 1000000 + c->tune32_tc_R;
-        graph_key.x2 = c->tune32_x2; graph_key.engine64 = c->nbody64_engine;
+        graph_key.x2 = c->tune32_x2 * 10000 + c->tune32_R; graph_key.engine64 = c->nbody64_engine;
     };
     if (x_is_zero && (st = vec_zero(c, x, NR))) return st;
     // ||b|| once

@@ -503,9 +503,19 @@ static int default_nsplit_tc(hzb_ctx *c, int R)
     return (int)std::min<long long>(64, std::max<long long>(1, (4LL * sms + ctas - 1) / ctas));
 }
 
+// Source split of the tcgen05 kernel: about two resident CTAs per SM in all.
+static int default_nsplit_tc5(hzb_ctx *c, int R)
+{
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
+    const int rc = (R <= 16) ? 16 : 32;
+    const long long ctas = (long long)c->n_tblocks * 4 * ((R + rc - 1) / rc);
+    return (int)std::min<long long>(64, std::max<long long>(1, (2LL * sms + ctas - 1) / ctas));
+}
+
 hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 {
-    if (c->nbody64_engine != 0) return interbody64_sym(c, R, sigma, y);
+    if (c->nbody64_engine == 1 || (c->nbody64_engine < 0 && R <= 4)) return interbody64_sym(c, R, sigma, y);
     int tpt = c->tune64_tpt > 0 ? c->tune64_tpt : 2;
     int ns = c->tune64_split > 0 ? c->tune64_split : default_nsplit(c, R, tpt);
     return interbody64_cfg(c, R, sigma, y, tpt, ns);
@@ -513,16 +523,20 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 {
-    // many right-hand sides: contraction on the tensor cores (nbody_tc.cu)
-    bool tc = c->nbody_engine == 1;
-    if (c->nbody_engine < 0) tc = (c->tune32_tc >= 0 && c->tune32_tc_R == R) ? c->tune32_tc == 1 : R >= 16;
-    if (tc) {
+    // many right-hand sides: contraction on the tensor cores, tcgen05 (nbody_tc5.cu) or
+    // mma.sync (nbody_tc.cu); engine choice 0 CUDA cores, 1 mma.sync, 2 tcgen05
+    int e = -1;
+    if (c->nbody_engine == 1) e = 1;
+    else if (c->nbody_engine == 5) e = 2;
+    else if (c->nbody_engine < 0) e = (c->tune32_tc >= 0 && c->tune32_tc_R == R) ? c->tune32_tc : (R >= 16 ? 2 : 0);
+    if (e == 2) return interbody_tc5(c, R, sigma, y, default_nsplit_tc5(c, R));
+    if (e == 1) {
         int ns = c->tunetc_split > 0 ? c->tunetc_split : default_nsplit_tc(c, R);
         return interbody_tc(c, R, sigma, y, ns);
     }
     // CUDA cores: variant 0 scalar, 1 packed pairs, 2 pair-symmetric packed
-    int v = c->tune32_x2 >= 0 ? c->tune32_x2 : 1;
-    if (c->nbody_engine >= 2) v = c->nbody_engine - 2;
+    int v = (c->tune32_x2 >= 0 && c->tune32_R == R) ? c->tune32_x2 : (R <= 2 ? 2 : 1);
+    if (c->nbody_engine >= 2 && c->nbody_engine <= 4) v = c->nbody_engine - 2;
     if (v == 2) return interbody32_sym(c, R, sigma, y, (c->tune32_x2 == 2 && c->tune32_tpt == 1) ? 1 : 2);
     const bool x2 = v == 1;
     int tpt = c->tune32_tpt > 0 ? c->tune32_tpt : 4;
@@ -720,7 +734,7 @@ hzb_status autotune(hzb_ctx *c, int R, int which, double *best_ms)
         // FP32 kernel variants: 0 scalar, 1 packed pairs, 2 pair-symmetric packed
         // (one of them when the engine fixes it)
         int xmin = 0, xmax = prec ? 2 : 0;
-        if (prec && c->nbody_engine >= 2) xmin = xmax = c->nbody_engine - 2;
+        if (prec && c->nbody_engine >= 2 && c->nbody_engine <= 4) xmin = xmax = c->nbody_engine - 2;
         for (int xv = xmin; xv <= xmax; ++xv) {
             if (xv == 2) {                  // no source split; TP = 1 or 2 packed target pairs
                 for (int tp = 1; tp <= 2; ++tp) {
@@ -745,7 +759,7 @@ hzb_status autotune(hzb_ctx *c, int R, int which, double *best_ms)
             }
         }
         if (prec && R >= 8 && c->nbody_engine < 0) {
-            // the tensor-core contraction competes for the FP32 inter-body sum
+            // the tensor-core contractions (mma.sync, tcgen05) compete for the FP32 sum
             const int d = default_nsplit_tc(c, R);
             const int cand[4] = {1, 2, d, 2 * d};
             int tbs = 0;
@@ -756,12 +770,25 @@ hzb_status autotune(hzb_ctx *c, int R, int which, double *best_ms)
                 if (ms < 0) return fail(c, HZB_ECUDA, "autotune launch failed");
                 if (ms < tbm) { tbm = ms; tbs = cand[b]; }
             }
+            float t5 = 1e30f;
+            {
+                if (interbody_tc5(c, R, c->io_in.ptr, c->io_out.ptr, default_nsplit_tc5(c, R)))
+                    return fail(c, HZB_ECUDA, "autotune launch failed");
+                cudaEventRecord(c->ev0, c->stream);
+                for (int q = 0; q < 3; ++q)
+                    if (interbody_tc5(c, R, c->io_in.ptr, c->io_out.ptr, default_nsplit_tc5(c, R)))
+                        return fail(c, HZB_ECUDA, "autotune launch failed");
+                cudaEventRecord(c->ev1, c->stream);
+                if (cudaEventSynchronize(c->ev1) != cudaSuccess) return fail(c, HZB_ECUDA, "autotune launch failed");
+                cudaEventElapsedTime(&t5, c->ev0, c->ev1);
+                t5 /= 3;
+            }
             c->tunetc_split = tbs;
-            c->tune32_tc = (tbm < bm) ? 1 : 0;
+            c->tune32_tc = (t5 < tbm && t5 < bm) ? 2 : (tbm < bm ? 1 : 0);
             c->tune32_tc_R = R;
-            bm = std::min(bm, tbm);
+            bm = std::min(bm, std::min(tbm, t5));
         }
-        if (prec) { c->tune32_tpt = bt; c->tune32_split = bs; c->tune32_x2 = bx; }
+        if (prec) { c->tune32_tpt = bt; c->tune32_split = bs; c->tune32_x2 = bx; c->tune32_R = R; }
         else { c->tune64_tpt = bt; c->tune64_split = bs; }
         if (best_ms) best_ms[prec ? 0 : 1] = bm;
     }

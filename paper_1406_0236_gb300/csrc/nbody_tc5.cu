@@ -1,0 +1,378 @@
+// Inter-body sum y = B sigma (Sec. 3.3, Eq. (nystromnaive)) for many right-hand sides
+// with the contraction over sources on the 5th-generation tensor cores (tcgen05,
+// accumulators in tensor memory).
+//
+// A CTA of 256 threads owns 128 targets of one TargetBlock (4 CTAs per block) and RC = 16
+// or 32 right-hand sides.  For every tile of 32 sources:
+//   * two threads per target form the pair kernels G(t, s) = e^{ikr}[n_s.d/r^3 - i(k n_s.d/r^2 + eta/r)]
+//     in FP32 for the 32 sources and stores Re G, Im G, each split into TF32 hi + lo, as
+//     row t of four 128 x 32 K-major operand tiles in shared memory (128-byte swizzle);
+//   * the weighted densities sigma'_{s,r} = w_s sigma_{s,r}/(4 pi) of the RC RHS form
+//     two 2RC x 32 operand tiles B1 = [Re s' ; Im s'] and B2 = [-Im s' ; Re s'] (rows =
+//     output columns, hi + lo each), so that Y = Re G B1 + Im G B2 gives
+//     [Re y | Im y] in the 128 x 2RC accumulator;
+//   * one thread issues 24 MMAs (4 k-steps of 8 sources x {Ahi Bhi, Ahi Blo, Alo Bhi}
+//     for both products) with tcgen05.mma.kind::tf32 into tensor memory and commits
+//     them to an mbarrier; the tile's accumulator starts from zero;
+//   * after the commit, each warp reads 32 lanes x RC columns of the accumulator
+//     (tcgen05.ld) and adds them to running FP32 sums in registers: the tensor cores' internal accumulation is
+//     not rounded to nearest, so chaining ~10^4 tiles in tensor memory would drift.
+// The next tile's positions and densities are loaded into registers while the current
+// tile's pair kernels and MMAs run.  Every mbarrier wait is bounded; on a timeout the CTA sets an error flag, writes NaN
+// outputs, frees its tensor memory and returns.
+#include <algorithm>
+
+#include "hzb_internal.h"
+#include "kernel_math.cuh"
+
+namespace hzb {
+
+static const int T5_M = 128;              // targets per CTA = MMA M = TMEM lanes
+static const int T5_K = 32;               // sources per tile: one 128-byte row of TF32
+// right-hand sides per CTA: RC = 16 or 32 (template), MMA N = 2 RC (real and imaginary columns)
+static const int T5_TMEM_COLS = 128;      // allocated tensor-memory columns (>= 2 RC, power of 2)
+static const int T5_THREADS = 256;        // two threads per target row
+static const int T5_A_BYTES = T5_M * T5_K * 4;          // one A operand tile (16 KB)
+static const int T5_B_BYTES = 64 * T5_K * 4;            // one B operand tile (8 KB at RC = 32)
+static const int T5_SMEM = 4 * T5_A_BYTES + 4 * T5_B_BYTES + 1024 + 1024;   // + source tile, alignment
+
+__device__ __forceinline__ uint32_t t5_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Byte offset of the 16-byte chunk c (4 TF32 values along K) of row `row` in a K-major
+// tile with 128-byte rows and the 128-byte swizzle: 8-row atoms of 1024 bytes, chunk
+// index XOR (row mod 8).
+__device__ __forceinline__ uint32_t t5_chunk_off(int row, int c)
+{
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ void t5_st4(uint32_t saddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(saddr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 1024-byte stride between
+// 8-row groups, descriptor version 1.
+__device__ __forceinline__ uint64_t t5_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, N, M = 128.
+__host__ __device__ constexpr uint32_t t5_idesc(int n)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(T5_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void t5_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ bool t5_wait(uint32_t mbar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void t5_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] += __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void t5_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] += __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void t5_pair(float tx, float ty, float tz, float4 a, float2 b, float k, float eta, float kt,
+                                        float &gre, float &gim)
+{
+    const float dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ir = rsqrtf(r2);
+    const float nd = fmaf(a.w, dx, fmaf(b.x, dy, b.y * dz));
+    const float ndir2 = nd * (ir * ir);
+    const float A = ndir2 * ir;
+    const float B = fmaf(k, ndir2, eta * ir);
+    float turns = (r2 * ir) * kt;
+    turns -= rintf(turns);
+    float s, c;
+    __sincosf(turns * 6.283185307179586f, &s, &c);
+    gre = fmaf(c, A, s * B);
+    gim = fmaf(s, A, -c * B);
+}
+
+template <int RC>
+__global__ void __launch_bounds__(T5_THREADS, 1)
+nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pos,
+                 const float4 *__restrict__ nrm, const float2 *__restrict__ sw, float k, float eta, float kt,
+                 float2 *__restrict__ ypart, double2 *__restrict__ y, size_t split_stride, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char t5_smem_raw[];
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ float4 s_a[T5_K];
+    __shared__ float2 s_b[T5_K];
+    // operand tiles on a 1024-byte boundary (the swizzle atom)
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(t5_smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t sA = base;                          // rh, rl, ih, il: 4 x 16 KB
+    const uint32_t sB = base + 4 * T5_A_BYTES;         // b1h, b1l, b2h, b2l: 4 x 8 KB
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+
+    const TargetBlock tb = blocks[blockIdx.x >> 2];
+    const int sub = blockIdx.x & 3;
+    if (sub * T5_M >= tb.count) return;                // whole CTA past the block's end
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int NC = 2 * RC;                         // accumulator columns
+    const int r0 = blockIdx.y * RC;
+    // pair-kernel duty: row (target) `row`, sources 16 `half` .. 16 `half` + 15 of a tile
+    const int row = tid & (T5_M - 1), half = tid >> 7;
+    float tx = 1e18f, ty = 1e18f, tz = 1e18f;
+    if (sub * T5_M + row < tb.count) {
+        const float4 p = pos[tb.start + sub * T5_M + row];
+        tx = p.x; ty = p.y; tz = p.z;
+    }
+    // B-operand duty: right-hand side bn, sources 4 bc .. 4 bc + 3 (threads with bc < 8)
+    const int bn = tid % RC, bc = tid / RC;
+    const bool bduty = bc < T5_K / 4;
+    const int rb = r0 + bn;
+    // accumulator duty: TMEM lanes 32 (warp mod 4) .., columns RC (warp / 4) ..: real parts
+    // in warps 0-3, imaginary parts in warps 4-7
+    const int orow = 32 * (warp & 3) + lane, ocol = RC * (warp >> 2);
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
+                     "r"(T5_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_taddr;
+    const uint32_t tmem_warp = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)ocol;
+
+    float acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = 0.f;
+    uint32_t phase = 0;
+    bool failed = false;
+    const int c0 = blockIdx.z * chunk, c1 = min(N, c0 + chunk);
+    // the tile sequence: range 0 = [c0, min(c1, excl_lo)), range 1 = [max(c0, excl_hi), c1)
+    const int lo0 = c0, hi0 = min(c1, tb.excl_lo), lo1 = max(c0, tb.excl_hi), hi1 = c1;
+    const int n0 = hi0 > lo0 ? (hi0 - lo0 + T5_K - 1) / T5_K : 0;
+    const int n1 = hi1 > lo1 ? (hi1 - lo1 + T5_K - 1) / T5_K : 0;
+    // registers prefetched for the next tile
+    float4 pa = make_float4(-1e18f, -1e18f, -1e18f, 0.f), pn = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 bv[4];
+    auto tile_of = [&](int i, int &j0, int &cnt) {
+        if (i < n0) { j0 = lo0 + i * T5_K; cnt = min(T5_K, hi0 - j0); }
+        else { j0 = lo1 + (i - n0) * T5_K; cnt = min(T5_K, hi1 - j0); }
+    };
+    auto prefetch = [&](int i) {
+        int j0, cnt;
+        tile_of(i, j0, cnt);
+        pa = make_float4(-1e18f, -1e18f, -1e18f, 0.f);
+        pn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tid < T5_K && tid < cnt) { pa = pos[j0 + tid]; pn = nrm[j0 + tid]; }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int s = 4 * bc + q;
+            bv[q] = (bduty && s < cnt && rb < R) ? sw[(size_t)(j0 + s) * R + rb] : make_float2(0.f, 0.f);
+        }
+    };
+    const int ntile = n0 + n1;
+    if (ntile > 0) prefetch(0);
+    for (int it = 0; it < ntile; ++it) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();                               // previous tile's operands and accumulator consumed
+        if (tid < T5_K) {
+            s_a[tid] = make_float4(pa.x, pa.y, pa.z, pn.x);
+            s_b[tid] = make_float2(pn.y, pn.z);
+        }
+        if (bduty) {   // B operands: rows bn (B1 = Re s', B2 = -Im s') and bn + RC (B1 = Im s', B2 = Re s')
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { h[q] = t5_tf32(bv[q].x); l[q] = t5_tf32(bv[q].x - __uint_as_float(h[q])); }
+            t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn, bc), h[0], h[1], h[2], h[3]);
+            t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
+            t5_st4(sB + 2 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
+            t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { h[q] = t5_tf32(bv[q].y); l[q] = t5_tf32(bv[q].y - __uint_as_float(h[q])); }
+            t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
+            t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { h[q] ^= 0x80000000u; l[q] ^= 0x80000000u; }
+            t5_st4(sB + 2 * T5_B_BYTES + t5_chunk_off(bn, bc), h[0], h[1], h[2], h[3]);
+            t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
+        }
+        __syncthreads();                               // source tile staged
+        if (it + 1 < ntile) prefetch(it + 1);          // overlaps the pair kernels and the MMAs
+        // A operands: row `row`, chunks 4 half .. 4 half + 3
+#pragma unroll 1
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = 4 * half + cc;
+            uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float gr, gi;
+                t5_pair(tx, ty, tz, s_a[4 * c + q], s_b[4 * c + q], k, eta, kt, gr, gi);
+                rh[q] = t5_tf32(gr); rl[q] = t5_tf32(gr - __uint_as_float(rh[q]));
+                ih[q] = t5_tf32(gi); il[q] = t5_tf32(gi - __uint_as_float(ih[q]));
+            }
+            const uint32_t off = t5_chunk_off(row, c);
+            t5_st4(sA + 0 * T5_A_BYTES + off, rh[0], rh[1], rh[2], rh[3]);
+            t5_st4(sA + 1 * T5_A_BYTES + off, rl[0], rl[1], rl[2], rl[3]);
+            t5_st4(sA + 2 * T5_A_BYTES + off, ih[0], ih[1], ih[2], ih[3]);
+            t5_st4(sA + 3 * T5_A_BYTES + off, il[0], il[1], il[2], il[3]);
+        }
+        // make the generic-proxy stores visible to the tensor cores, then issue
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // products: (A tile, B tile) = Re G x B1 and Im G x B2, each hi.hi, hi.lo, lo.hi
+            const int am[6] = {0, 0, 1, 2, 2, 3}, bm[6] = {0, 1, 0, 2, 3, 2};
+#pragma unroll
+            for (int ks = 0; ks < T5_K / 8; ++ks)
+#pragma unroll
+                for (int p = 0; p < 6; ++p)
+                    t5_mma(tmem, t5_desc(sA + am[p] * T5_A_BYTES + 32 * ks), t5_desc(sB + bm[p] * T5_B_BYTES + 32 * ks),
+                           t5_idesc(NC), (ks | p) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                         : "memory");
+        }
+        const bool ok = t5_wait(mbar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (RC == 32) t5_ld32(tmem_warp, acc);
+        else t5_ld16(tmem_warp, acc);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T5_TMEM_COLS) : "memory");
+    if (failed && tid == 0) atomicExch(err, 1);
+    const int t = sub * T5_M + orow;
+    if (t >= tb.count) return;
+    // columns ocol .. ocol + RC - 1: real parts (ocol = 0) or imaginary parts (ocol = RC)
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+        if (r0 + r >= R) break;
+        const size_t e = (size_t)(tb.start + t) * R + r0 + r;
+        const float v = failed ? __int_as_float(0x7fc00000) : acc[r];
+        if (ypart) reinterpret_cast<float *>(ypart + blockIdx.z * split_stride + e)[ocol ? 1 : 0] = v;
+        else reinterpret_cast<double *>(y + e)[ocol ? 1 : 0] = (double)v;
+    }
+}
+
+hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit)
+{
+    if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
+    const int N = (int)c->N;
+    int chunk = (N + nsplit - 1) / nsplit;
+    chunk = ((chunk + T5_K - 1) / T5_K) * T5_K;
+    nsplit = (N + chunk - 1) / chunk;
+    const size_t n = (size_t)N * R;
+    float2 *part = nullptr;
+    if (nsplit > 1) {
+        if (check_cuda(c, c->nb_part32.ensure(n * nsplit), "alloc partial sums")) return HZB_ENOMEM;
+        part = c->nb_part32.ptr;
+    }
+    if (check_cuda(c, c->kerr.ensure(1), "alloc error flag")) return HZB_ENOMEM;
+    if (!c->kerr_ready) {
+        if (check_cuda(c, cudaMemsetAsync(c->kerr.ptr, 0, sizeof(int), c->stream), "clear error flag"))
+            return HZB_ECUDA;
+        c->kerr_ready = true;
+    }
+    static bool attr_done[64] = {false};
+    const int dev = c->opt.device;
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        if (check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               T5_SMEM), "tcgen05 kernel shared memory") ||
+            check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               T5_SMEM), "tcgen05 kernel shared memory"))
+            return HZB_ECUDA;
+        attr_done[dev] = true;
+    }
+    c->interbody_calls++;
+    c->launches += (nsplit > 1) ? 3 : 2;
+    const int slot = prof_begin(c, 1);
+    const float2 *sw = weighted_sigma32(c, R, sigma);
+    if (!sw) return HZB_ENOMEM;
+    const int rc = (R <= 16) ? 16 : 32;
+    dim3 grid(c->n_tblocks * 4, (R + rc - 1) / rc, nsplit);
+    const float k = (float)c->k, eta = (float)c->eta, kt = (float)(c->k / (2.0 * M_PI));
+    if (rc == 16)
+        nbody_tc5_kernel<16><<<grid, T5_THREADS, T5_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
+                                                                      c->nrm32.ptr, sw, k, eta, kt, part, y, n,
+                                                                      c->kerr.ptr);
+    else
+        nbody_tc5_kernel<32><<<grid, T5_THREADS, T5_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
+                                                                      c->nrm32.ptr, sw, k, eta, kt, part, y, n,
+                                                                      c->kerr.ptr);
+    if (nsplit > 1) split_reduce_f2(c, n, nsplit, part, y);
+    cudaError_t e = cudaGetLastError();
+    prof_end(c, slot);
+    if (check_cuda(c, e, "nbody_tc5_kernel")) return HZB_ECUDA;
+    if (!c->capturing) {               // a bounded wait that ran out: outputs are NaN
+        int flag = 0;
+        if (check_cuda(c, cudaMemcpyAsync(&flag, c->kerr.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                       "read error flag") ||
+            check_cuda(c, cudaStreamSynchronize(c->stream), "nbody_tc5_kernel"))
+            return HZB_ECUDA;
+        if (flag) return fail(c, HZB_ETIMEOUT, "tensor-core wait timed out in nbody_tc5_kernel");
+    }
+    return HZB_OK;
+}
+
+}  // namespace hzb

@@ -149,10 +149,11 @@ def test_spheroids_258560_sampled_rows():
     # tensor-core contraction, 16 right-hand sides: 258,560 sources per target
     sig16 = rand_c((P.N, 16), 73)
     ref16 = P.interbody(sig16, targets=rows)
-    s.set_interbody_engine(1)
-    ytc = s.interbody(sig16, precision=1)
+    for engine in (1, 5):                # mma.sync, tcgen05
+        s.set_interbody_engine(engine)
+        ytc = s.interbody(sig16, precision=1)
+        assert rel_l2(ytc[rows], ref16) < 3e-5, engine
     s.set_interbody_engine(-1)
-    assert rel_l2(ytc[rows], ref16) < 3e-5
 
 
 @pytest.mark.parametrize("engine", [0, 1])
@@ -191,6 +192,21 @@ def test_interbody_tensor_cores(pair, R):
     sig = rand_c((P.N, R), 141 + R)
     ref = P.interbody(sig)
     s.set_interbody_engine(1)
+    try:
+        got = s.interbody(sig, precision=1)
+    finally:
+        s.set_interbody_engine(-1)
+    assert rel_l2(got, ref) < 5e-6
+
+
+@pytest.mark.parametrize("R", [1, 5, 16, 40])
+def test_interbody_tcgen05(pair, R):
+    """FP32 inter-body sum with the contraction on tcgen05 tensor cores (TF32 three-term
+    split, accumulators in tensor memory drained into FP32 sums every 32 sources)."""
+    s, P = pair
+    sig = rand_c((P.N, R), 171 + R)
+    ref = P.interbody(sig)
+    s.set_interbody_engine(5)
     try:
         got = s.interbody(sig, precision=1)
     finally:
