@@ -4,9 +4,10 @@
 //
 // A CTA of 256 threads owns 128 targets of one TargetBlock (4 CTAs per block) and RC = 16
 // or 32 right-hand sides.  For every tile of 32 sources:
-//   * two threads per target form the pair kernels G(t, s) = e^{ikr}[n_s.d/r^3 - i(k n_s.d/r^2 + eta/r)]
-//     in FP32 for the 32 sources and stores Re G, Im G, each split into TF32 hi + lo, as
-//     row t of four 128 x 32 K-major operand tiles in shared memory (128-byte swizzle);
+//   * two threads per target form the pair kernels
+//     G(t, s) = e^{ikr}[n_s.d/r^3 - i(k n_s.d/r^2 + eta/r)] in FP32 for the 32 sources, two
+//     sources per f32x2 instruction, and store Re G, Im G, each split into TF32 hi + lo,
+//     as row t of four 128 x 32 K-major operand tiles in shared memory (128-byte swizzle);
 //   * the weighted densities sigma'_{s,r} = w_s sigma_{s,r}/(4 pi) of the RC RHS form
 //     two 2RC x 32 operand tiles B1 = [Re s' ; Im s'] and B2 = [-Im s' ; Re s'] (rows =
 //     output columns, hi + lo each), so that Y = Re G B1 + Im G B2 gives
@@ -15,13 +16,15 @@
 //     for both products) with tcgen05.mma.kind::tf32 into tensor memory and commits
 //     them to an mbarrier; the tile's accumulator starts from zero;
 //   * after the commit, each warp reads 32 lanes x RC columns of the accumulator
-//     (tcgen05.ld) and adds them to running FP32 sums in registers: the tensor cores' internal accumulation is
-//     not rounded to nearest, so chaining ~10^4 tiles in tensor memory would drift.
+//     (tcgen05.ld) and adds them to running FP32 sums in registers: the tensor cores'
+//     internal accumulation is not rounded to nearest, so chaining ~10^4 tiles in tensor
+//     memory would drift.
 // The next tile's positions and densities are loaded into registers while the current
 // tile's pair kernels and MMAs run.  Every mbarrier wait is bounded; on a timeout the CTA sets an error flag, writes NaN
 // outputs, frees its tensor memory and returns.
 #include <algorithm>
 
+#include "f32x2.cuh"
 #include "hzb_internal.h"
 #include "kernel_math.cuh"
 
@@ -123,22 +126,41 @@ __device__ __forceinline__ void t5_ld16(uint32_t taddr, float *v)
     for (int q = 0; q < 16; ++q) v[q] += __uint_as_float(r[q]);
 }
 
-__device__ __forceinline__ void t5_pair(float tx, float ty, float tz, float4 a, float2 b, float k, float eta, float kt,
-                                        float &gre, float &gim)
+// Pair kernels of one target and two sources (packed f32x2), phase reduced to a fraction
+// of a turn (1.5 * 2^23 rounding constant, valid while k r / (2 pi) < 2^22).
+__device__ __forceinline__ void t5_pair2(f2x tx, f2x ty, f2x tz, f2x sx, f2x sy, f2x sz, f2x nx, f2x ny, f2x nz,
+                                         f2x k2, f2x eta2, f2x kt2, f2x &gre, f2x &gim)
 {
-    const float dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ir = rsqrtf(r2);
-    const float nd = fmaf(a.w, dx, fmaf(b.x, dy, b.y * dz));
-    const float ndir2 = nd * (ir * ir);
-    const float A = ndir2 * ir;
-    const float B = fmaf(k, ndir2, eta * ir);
-    float turns = (r2 * ir) * kt;
-    turns -= rintf(turns);
-    float s, c;
-    __sincosf(turns * 6.283185307179586f, &s, &c);
-    gre = fmaf(c, A, s * B);
-    gim = fmaf(s, A, -c * B);
+    const f2x rnd2 = f2_splat(12582912.0f), twopi2 = f2_splat(6.283185307179586f);
+    const f2x dx = f2_sub(tx, sx), dy = f2_sub(ty, sy), dz = f2_sub(tz, sz);
+    const f2x r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    const f2x ir = f2_pack(rsqrtf(ra), rsqrtf(rb));
+    const f2x X = f2_mul(f2_fma(nx, dx, f2_fma(ny, dy, f2_mul(nz, dz))), f2_mul(ir, ir));
+    const f2x A = f2_mul(X, ir), B = f2_fma(k2, X, f2_mul(eta2, ir));
+    const f2x t = f2_mul(f2_mul(r2, ir), kt2);
+    const f2x th = f2_mul(f2_sub(t, f2_sub(f2_add(t, rnd2), rnd2)), twopi2);
+    float ta, tb, sa, ca, sb, cb;
+    f2_unpack(th, ta, tb);
+    __sincosf(ta, &sa, &ca);
+    __sincosf(tb, &sb, &cb);
+    const f2x s2 = f2_pack(sa, sb), c2 = f2_pack(ca, cb);
+    gre = f2_fma(c2, A, f2_mul(s2, B));
+    gim = f2_sub(f2_mul(s2, A), f2_mul(c2, B));
+}
+
+// TF32 hi + lo split of a packed pair: hi rounded to TF32, lo = x - hi rounded to TF32.
+__device__ __forceinline__ void t5_split2(f2x x, uint32_t &h0, uint32_t &h1, uint32_t &l0, uint32_t &l1)
+{
+    float a, b;
+    f2_unpack(x, a, b);
+    h0 = t5_tf32(a);
+    h1 = t5_tf32(b);
+    const f2x lo = f2_sub(x, f2_pack(__uint_as_float(h0), __uint_as_float(h1)));
+    f2_unpack(lo, a, b);
+    l0 = t5_tf32(a);
+    l1 = t5_tf32(b);
 }
 
 template <int RC>
@@ -150,8 +172,7 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
     extern __shared__ __align__(1024) unsigned char t5_smem_raw[];
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) unsigned long long s_mbar;
-    __shared__ float4 s_a[T5_K];
-    __shared__ float2 s_b[T5_K];
+    __shared__ __align__(16) float s_src[6][T5_K];     // x, y, z, nx, ny, nz of the tile's sources
     // operand tiles on a 1024-byte boundary (the swizzle atom)
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(t5_smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -167,11 +188,12 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
     const int r0 = blockIdx.y * RC;
     // pair-kernel duty: row (target) `row`, sources 16 `half` .. 16 `half` + 15 of a tile
     const int row = tid & (T5_M - 1), half = tid >> 7;
-    float tx = 1e18f, ty = 1e18f, tz = 1e18f;
+    f2x tx = f2_splat(1e18f), ty = tx, tz = tx;
     if (sub * T5_M + row < tb.count) {
         const float4 p = pos[tb.start + sub * T5_M + row];
-        tx = p.x; ty = p.y; tz = p.z;
+        tx = f2_splat(p.x); ty = f2_splat(p.y); tz = f2_splat(p.z);
     }
+    const f2x k2 = f2_splat(k), eta2 = f2_splat(eta), kt2 = f2_splat(kt);
     // B-operand duty: right-hand side bn, sources 4 bc .. 4 bc + 3 (threads with bc < 8)
     const int bn = tid % RC, bc = tid / RC;
     const bool bduty = bc < T5_K / 4;
@@ -231,8 +253,8 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();                               // previous tile's operands and accumulator consumed
         if (tid < T5_K) {
-            s_a[tid] = make_float4(pa.x, pa.y, pa.z, pn.x);
-            s_b[tid] = make_float2(pn.y, pn.z);
+            s_src[0][tid] = pa.x; s_src[1][tid] = pa.y; s_src[2][tid] = pa.z;
+            s_src[3][tid] = pn.x; s_src[4][tid] = pn.y; s_src[5][tid] = pn.z;
         }
         if (bduty) {   // B operands: rows bn (B1 = Re s', B2 = -Im s') and bn + RC (B1 = Im s', B2 = Re s')
             uint32_t h[4], l[4];
@@ -259,11 +281,15 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
             const int c = 4 * half + cc;
             uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float gr, gi;
-                t5_pair(tx, ty, tz, s_a[4 * c + q], s_b[4 * c + q], k, eta, kt, gr, gi);
-                rh[q] = t5_tf32(gr); rl[q] = t5_tf32(gr - __uint_as_float(rh[q]));
-                ih[q] = t5_tf32(gi); il[q] = t5_tf32(gi - __uint_as_float(ih[q]));
+            for (int p = 0; p < 2; ++p) {              // sources 4c + 2p, 4c + 2p + 1
+                const int q = 4 * c + 2 * p;
+                f2x gr, gi;
+                t5_pair2(tx, ty, tz, *reinterpret_cast<const f2x *>(&s_src[0][q]),
+                         *reinterpret_cast<const f2x *>(&s_src[1][q]), *reinterpret_cast<const f2x *>(&s_src[2][q]),
+                         *reinterpret_cast<const f2x *>(&s_src[3][q]), *reinterpret_cast<const f2x *>(&s_src[4][q]),
+                         *reinterpret_cast<const f2x *>(&s_src[5][q]), k2, eta2, kt2, gr, gi);
+                t5_split2(gr, rh[2 * p], rh[2 * p + 1], rl[2 * p], rl[2 * p + 1]);
+                t5_split2(gi, ih[2 * p], ih[2 * p + 1], il[2 * p], il[2 * p + 1]);
             }
             const uint32_t off = t5_chunk_off(row, c);
             t5_st4(sA + 0 * T5_A_BYTES + off, rh[0], rh[1], rh[2], rh[3]);
