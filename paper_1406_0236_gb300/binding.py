@@ -132,6 +132,8 @@ def lib():
         "hzb_set_interbody_engine": (i, [p, i]),
         "hzb_set_fp64_interbody_engine": (i, [p, i]),
         "hzb_tuned_config": (i, [p, i, p]),
+        "hzb_save_scattering": (i, [p, ctypes.c_char_p]),
+        "hzb_load_scattering": (i, [p, ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -271,6 +273,14 @@ class Solver:
         return {"fp32_kernel": self.FP32_KERNELS[out[0]], "fp32_tpt": int(out[1]), "fp32_split": int(out[2]),
                 "fp64_kernel": "nbody64_sym_kernel" if out[3] else "nbody64_kernel",
                 "fp64_tpt": int(out[4]), "fp64_split": int(out[5])}
+
+    def save_scattering(self, path: str):
+        """Write the per-shape modal matrices (A~_p, S_p) to `path`."""
+        self._check(lib().hzb_save_scattering(self._h, os.fsencode(path)))
+
+    def load_scattering(self, path: str):
+        """Read matrices written by save_scattering instead of building them."""
+        self._check(lib().hzb_load_scattering(self._h, os.fsencode(path)))
 
     def build_scattering_matrices(self):
         self._check(lib().hzb_build_scattering_matrices(self._h))

@@ -1,0 +1,152 @@
+// Saving and loading the per-shape modal matrices A~_p and S_p = A~_p^{-1} (Sec. 3.2:
+// computed once per distinct body shape and reusable for any arrangement of bodies of
+// that shape at the same wavenumber), so that a later context skips the setup.
+//
+// File layout (little-endian, as the host writes it):
+//   char magic[8] = "HZBSCAT1"; int32 version = 1; int32 n_shapes;
+//   double k, eta;
+//   per shape: hzb_shape spec (the struct as laid out by this library), int32 NG, int32 M,
+//              then (M+1) NG NG complex doubles of A~_p, then the same of S_p,
+//              p = 0..M, each matrix row-major (row = target ring).
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hzb_internal.h"
+
+namespace hzb {
+
+static const char HZB_SCAT_MAGIC[8] = {'H', 'Z', 'B', 'S', 'C', 'A', 'T', '1'};
+
+__global__ void to_fp32_copy_kernel(size_t n, const double2 *a, float2 *b)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+// field by field: the struct's padding bytes are not part of the shape
+static bool same_shape(const hzb_shape &a, const hzb_shape &b)
+{
+    if (a.kind != b.kind || a.n_panels != b.n_panels || a.gl_order != b.gl_order || a.n_modes != b.n_modes) return false;
+    for (int q = 0; q < 4; ++q)
+        if (a.p[q] != b.p[q]) return false;
+    return true;
+}
+
+}  // namespace hzb
+
+using namespace hzb;
+
+extern "C" hzb_status hzb_save_scattering(hzb_ctx *c, const char *path)
+{
+    if (!c || !path) return HZB_EINVAL;
+    if (cudaSetDevice(c->opt.device) != cudaSuccess) return fail(c, HZB_ECUDA, "cudaSetDevice");
+    cudaGetLastError();
+    if (c->state != 3) return fail(c, HZB_ESTATE, "scattering matrices not built");
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(c, HZB_EINVAL, std::string("cannot open for writing: ") + path);
+    bool ok = true;
+    const int version = 1, ns = (int)c->shapes.size();
+    ok &= std::fwrite(HZB_SCAT_MAGIC, 1, 8, f) == 8;
+    ok &= std::fwrite(&version, sizeof(int), 1, f) == 1;
+    ok &= std::fwrite(&ns, sizeof(int), 1, f) == 1;
+    ok &= std::fwrite(&c->k, sizeof(double), 1, f) == 1;
+    ok &= std::fwrite(&c->eta, sizeof(double), 1, f) == 1;
+    std::vector<double2> host;
+    for (int s = 0; s < ns && ok; ++s) {
+        const ShapeDev &sd = *c->shapes[s];
+        const int NG = sd.geom.NG, M = sd.geom.M;
+        hzb_shape spec;
+        std::memset(&spec, 0, sizeof(spec));
+        spec.kind = sd.geom.spec.kind;
+        for (int q = 0; q < 4; ++q) spec.p[q] = sd.geom.spec.p[q];
+        spec.n_panels = sd.geom.spec.n_panels;
+        spec.gl_order = sd.geom.spec.gl_order;
+        spec.n_modes = sd.geom.spec.n_modes;
+        ok &= std::fwrite(&spec, sizeof(hzb_shape), 1, f) == 1;
+        ok &= std::fwrite(&NG, sizeof(int), 1, f) == 1;
+        ok &= std::fwrite(&M, sizeof(int), 1, f) == 1;
+        const size_t nmat = (size_t)(M + 1) * NG * NG;
+        host.resize(nmat);
+        for (const DevBuf<double2> *b : {&sd.A64, &sd.S64}) {
+            if (check_cuda(c, cudaMemcpyAsync(host.data(), b->ptr, nmat * sizeof(double2), cudaMemcpyDeviceToHost,
+                                              c->stream), "copy matrices") ||
+                check_cuda(c, cudaStreamSynchronize(c->stream), "copy matrices")) {
+                std::fclose(f);
+                return HZB_ECUDA;
+            }
+            ok &= std::fwrite(host.data(), sizeof(double2), nmat, f) == nmat;
+        }
+    }
+    ok &= std::fclose(f) == 0;
+    if (!ok) return fail(c, HZB_EINVAL, std::string("write failed: ") + path);
+    return HZB_OK;
+}
+
+extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
+{
+    if (!c || !path) return HZB_EINVAL;
+    if (cudaSetDevice(c->opt.device) != cudaSuccess) return fail(c, HZB_ECUDA, "cudaSetDevice");
+    cudaGetLastError();
+    if (c->state != 2) return fail(c, HZB_ESTATE, "hzb_load_scattering needs bodies and no earlier build");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(c, HZB_EINVAL, std::string("cannot open: ") + path);
+    char magic[8];
+    int version = 0, ns = 0;
+    double k = 0.0, eta = 0.0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, HZB_SCAT_MAGIC, 8) == 0;
+    ok = ok && std::fread(&version, sizeof(int), 1, f) == 1 && version == 1;
+    ok = ok && std::fread(&ns, sizeof(int), 1, f) == 1 && std::fread(&k, sizeof(double), 1, f) == 1 &&
+         std::fread(&eta, sizeof(double), 1, f) == 1;
+    if (!ok) {
+        std::fclose(f);
+        return fail(c, HZB_EINVAL, "not a scattering-matrix file of this version");
+    }
+    if (k != c->k || eta != c->eta || ns != (int)c->shapes.size()) {
+        std::fclose(f);
+        return fail(c, HZB_EINVAL, "file was written for another wavenumber, coupling or set of shapes");
+    }
+    std::vector<double2> host;
+    for (int s = 0; s < ns; ++s) {
+        ShapeDev &sd = *c->shapes[s];
+        hzb_shape spec;
+        int NG = 0, M = 0;
+        ok = std::fread(&spec, sizeof(hzb_shape), 1, f) == 1 && std::fread(&NG, sizeof(int), 1, f) == 1 &&
+             std::fread(&M, sizeof(int), 1, f) == 1;
+        if (!ok || !same_shape(spec, sd.geom.spec) || NG != sd.geom.NG || M != sd.geom.M) {
+            std::fclose(f);
+            return fail(c, HZB_EINVAL, "shape " + std::to_string(s) + " differs from the file's");
+        }
+        const size_t nmat = (size_t)(M + 1) * NG * NG;
+        if (check_cuda(c, sd.A64.ensure(nmat), "alloc A") || check_cuda(c, sd.S64.ensure(nmat), "alloc S") ||
+            check_cuda(c, sd.S32.ensure(nmat), "alloc S32")) {
+            std::fclose(f);
+            return HZB_ENOMEM;
+        }
+        host.resize(nmat);
+        for (DevBuf<double2> *b : {&sd.A64, &sd.S64}) {
+            if (std::fread(host.data(), sizeof(double2), nmat, f) != nmat) {
+                std::fclose(f);
+                return fail(c, HZB_EINVAL, "file ends early");
+            }
+            if (check_cuda(c, cudaMemcpyAsync(b->ptr, host.data(), nmat * sizeof(double2), cudaMemcpyHostToDevice,
+                                              c->stream), "upload matrices") ||
+                check_cuda(c, cudaStreamSynchronize(c->stream), "upload matrices")) {
+                std::fclose(f);
+                return HZB_ECUDA;
+            }
+        }
+        to_fp32_copy_kernel<<<(unsigned)((nmat + 255) / 256), 256, 0, c->stream>>>(nmat, sd.S64.ptr, sd.S32.ptr);
+        if (check_cuda(c, cudaGetLastError(), "to_fp32_copy_kernel")) {
+            std::fclose(f);
+            return HZB_ECUDA;
+        }
+    }
+    std::fclose(f);
+    hzb_status st = make_nodes(c);
+    if (st) return st;
+    if (check_cuda(c, cudaStreamSynchronize(c->stream), "load")) return HZB_ECUDA;
+    c->t_setup_ms = 0.0;
+    c->state = 3;
+    return HZB_OK;
+}

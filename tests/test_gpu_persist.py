@@ -1,0 +1,73 @@
+"""Saving and loading the per-shape modal matrices (Sec. 3.2: the precomputation
+depends only on the shape and the wavenumber): a context that loads them solves like
+one that built them, also with the bodies moved; mismatched files are refused."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._common import gpu_solver, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _moved(wl, shift):
+    bodies = [W.Body(b.shape, b.center + np.asarray(shift) * (q + 1), b.rot) for q, b in enumerate(wl.bodies)]
+    return W.Workload(wl.name + "_moved", bodies, wl.k, wl.eta, wl.directions)
+
+
+def test_load_equals_build(tmp_path):
+    require_gpu()
+    from paper_1406_0236_gb300 import Options, Solver
+    wl = W.tiny_two_spheres()
+    built = gpu_solver(wl)
+    path = str(tmp_path / "scat.bin")
+    built.save_scattering(path)
+    loaded = Solver.from_workload(wl, Options(precision=0, gmres_tol=1e-12))
+    loaded.load_scattering(path)
+    for body, b in enumerate(wl.bodies):
+        ng = b.shape.n_panels * b.shape.gl_order
+        for p in (0, 3):
+            for which in (0, 1):
+                assert np.array_equal(built.get_modal_block(body, p, which, ng),
+                                      loaded.get_modal_block(body, p, which, ng)), (body, p, which)
+    built.solve_plane_waves(wl.directions)
+    loaded.solve_plane_waves(wl.directions)
+    assert rel_l2(loaded.get_density(), built.get_density()) < 1e-13
+
+
+def test_load_with_moved_bodies(tmp_path):
+    """The matrices of a shape serve any placement: load them into moved bodies and
+    compare with a build for the moved geometry."""
+    require_gpu()
+    from paper_1406_0236_gb300 import Options, Solver
+    wl = W.tiny_two_spheres()
+    path = str(tmp_path / "scat.bin")
+    gpu_solver(wl).save_scattering(path)
+    mv = _moved(wl, [0.3, -0.2, 0.5])
+    fresh = gpu_solver(mv)
+    loaded = Solver.from_workload(mv, Options(precision=0, gmres_tol=1e-12))
+    loaded.load_scattering(path)
+    fresh.solve_plane_waves(mv.directions)
+    loaded.solve_plane_waves(mv.directions)
+    assert rel_l2(loaded.get_density(), fresh.get_density()) < 1e-12
+
+
+def test_load_refuses_mismatch(tmp_path):
+    require_gpu()
+    from paper_1406_0236_gb300 import HzbError, Options, Solver
+    wl = W.tiny_two_spheres()
+    path = str(tmp_path / "scat.bin")
+    s = gpu_solver(wl)
+    s.save_scattering(path)
+    with pytest.raises(HzbError):                         # already built
+        s.load_scattering(path)
+    other_k = W.Workload("k", wl.bodies, wl.k * 1.5, wl.eta, wl.directions)
+    t = Solver.from_workload(other_k, Options(precision=0))
+    with pytest.raises(HzbError):                         # other wavenumber
+        t.load_scattering(path)
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"not a file of this library")
+    u = Solver.from_workload(wl, Options(precision=0))
+    with pytest.raises(HzbError):
+        u.load_scattering(str(bad))
+    u.load_scattering(path)                               # a refused load left the context usable
