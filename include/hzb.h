@@ -212,6 +212,8 @@ hzb_status hzb_set_modal_engine(hzb_ctx *ctx, int engine);
  * node pair evaluated once for both directions, results added with FP64 atomics: equal
  * to rounding between runs, not bit for bit); 5 = tensor cores through tcgen05 (TF32
  * three-term split, accumulators in tensor memory, 16 or 32 right-hand sides per CTA);
+ * 6 = the same contraction as a warp-specialised pipeline (producer, MMA and epilogue
+ * warps synchronised by mbarriers, two operand stages, two accumulators);
  * -1 (default) = tcgen05 tensor cores when R >= 16, else as 0, unless hzb_autotune
  * timed the engines for this R.  Returns HZB_EINVAL for other values. */
 hzb_status hzb_set_interbody_engine(hzb_ctx *ctx, int engine);

@@ -454,7 +454,7 @@ hzb_status hzb_tuned_config(const hzb_ctx *c, int R, int out[6])
     // the FP32 engine interbody32 takes for R right-hand sides
     int e = -1;
     if (c->nbody_engine == 1) e = 1;
-    else if (c->nbody_engine == 5) e = 2;
+    else if (c->nbody_engine == 5 || c->nbody_engine == 6) e = 2;
     else if (c->nbody_engine < 0) e = (c->tune32_tc >= 0 && c->tune32_tc_R == R) ? c->tune32_tc : (R >= 16 ? 2 : 0);
     int v = (c->tune32_x2 >= 0 && c->tune32_R == R) ? c->tune32_x2 : (R <= 2 ? 2 : 1);
     if (c->nbody_engine >= 2 && c->nbody_engine <= 4) v = c->nbody_engine - 2;
@@ -496,7 +496,7 @@ hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *c, int engine)
 hzb_status hzb_set_interbody_engine(hzb_ctx *c, int engine)
 {
     if (!c) return HZB_EINVAL;
-    if (engine < -1 || engine > 5) return fail(c, HZB_EINVAL, "engine in {-1, 0, ..., 5}");
+    if (engine < -1 || engine > 6) return fail(c, HZB_EINVAL, "engine in {-1, 0, ..., 6}");
     c->nbody_engine = engine;
     return HZB_OK;
 }

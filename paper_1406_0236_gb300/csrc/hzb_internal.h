@@ -168,7 +168,8 @@ struct hzb_ctx {
     int nbody_engine = -1;                     // FP32 inter-body sum: -1 auto, 0 CUDA cores, 1 tensor cores,
                                                // 2 CUDA cores scalar kernel, 3 CUDA cores packed-pair kernel,
                                                // 4 CUDA cores pair-symmetric packed kernel,
-                                               // 5 tensor cores with tcgen05 (TMEM accumulators)
+                                               // 5 tensor cores with tcgen05 (TMEM accumulators),
+                                               // 6 tcgen05, warp-specialised pipeline
     int tunetc_split = 0;                      // tensor-core inter-body source split (0: default)
     int tune32_tc = -1, tune32_tc_R = 0;       // autotuner's engine choice for R = tune32_tc_R (-1: none)
     std::vector<cudaGraphExec_t> gexec;        // captured Arnoldi step j
@@ -200,7 +201,8 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   // nbody_df.cu
 hzb_status interbody_tc(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);
-hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);   // nbody_tc5.cu
+hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit,
+                         bool ws);   // nbody_tc5.cu; ws: warp-specialised form
 const float2 *weighted_sigma32(hzb_ctx *c, int R, const double2 *sigma);      // nbody.cu; nullptr on failure
 hzb_status ensure_sctab(hzb_ctx *c);                                          // nbody.cu: FP64 cos/sin table
 hzb_status interbody64_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y);  // nbody_sym.cu

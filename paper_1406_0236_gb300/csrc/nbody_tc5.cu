@@ -38,6 +38,7 @@ static const int T5_THREADS = 256;        // two threads per target row
 static const int T5_A_BYTES = T5_M * T5_K * 4;          // one A operand tile (16 KB)
 static const int T5_B_BYTES = 64 * T5_K * 4;            // one B operand tile (8 KB at RC = 32)
 static const int T5_SMEM = 4 * T5_A_BYTES + 4 * T5_B_BYTES + 1024 + 1024;   // + source tile, alignment
+static const int T5_STAGE = 4 * T5_A_BYTES + 4 * T5_B_BYTES;              // one operand stage (96 KB)
 
 __device__ __forceinline__ uint32_t t5_tf32(float x)
 {
@@ -341,7 +342,262 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
     }
 }
 
-hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit)
+// ---------------------------------------------------------------- warp-specialised form
+//
+// The same contraction with the tile phases on separate warps, synchronised by
+// mbarriers only (no block barrier inside the tile loop):
+//   warps 0-15  producers (four per target row): stage the tile's sources (producer-only
+//               named barrier), write the density (B) and pair-kernel (A) operands of
+//               stage s = i mod 2 once the MMAs of tile i - 2 released it (`empty[s]`),
+//               then arrive on `full[s]` (512 arrivals);
+//   warp 20     one thread issues the 24 MMAs of tile i into accumulator b = i mod 2 once
+//               `full[s]` completed and the epilogue released b (`accempty[b]`), then
+//               commits to `empty[s]` and `accfull[b]`;
+//   warps 16-19 epilogue: wait `accfull[b]`, read the 128 lanes x 2RC columns
+//               (tcgen05.ld), add them to FP32 sums, arrive on `accempty[b]` (128).
+// A wait that runs out sets a shared abort flag that every other wait polls; producer
+// decisions to stop are made together (bar.red.or on the producers' barrier), so no
+// named barrier is left waiting.
+static const int WS_PROD_WARPS = 16;
+static const int WS_PROD = WS_PROD_WARPS * 32;      // producer threads
+static const int WS_THREADS = (WS_PROD_WARPS + 5) * 32;
+static const int WS_SMEM = 2 * T5_STAGE + 1024;
+
+__device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, volatile int *abort_flag)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void ws_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// producers' named barrier (id 1, all producer threads) that also ORs a flag across them
+__device__ __forceinline__ bool ws_prod_sync_or(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(WS_PROD)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void ws_prod_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(WS_PROD) : "memory");
+}
+
+template <int RC>
+__global__ void __launch_bounds__(WS_THREADS, 1)
+nbody_tc5ws_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pos,
+                   const float4 *__restrict__ nrm, const float2 *__restrict__ sw, float k, float eta, float kt,
+                   float2 *__restrict__ ypart, double2 *__restrict__ y, size_t split_stride, int *__restrict__ err)
+{
+    constexpr int NC = 2 * RC;                         // accumulator columns: [Re y | Im y]
+    extern __shared__ __align__(1024) unsigned char ws_smem_raw[];
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) unsigned long long s_bar[8];   // full[2], empty[2], accfull[2], accempty[2]
+    __shared__ int s_abort;
+    __shared__ __align__(16) float s_src[6][T5_K];
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(ws_smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&s_bar[0]);
+    const uint32_t full0 = bar0, empty0 = bar0 + 16, accfull0 = bar0 + 32, accempty0 = bar0 + 48;
+    volatile int *abort_flag = &s_abort;
+
+    const TargetBlock tb = blocks[blockIdx.x >> 2];
+    const int sub = blockIdx.x & 3;
+    if (sub * T5_M >= tb.count) return;                // whole CTA past the block's end
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.y * RC;
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
+                     "r"(T5_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * q), "r"(WS_PROD)
+                         : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty0 + 8 * q), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(accfull0 + 8 * q), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(accempty0 + 8 * q), "r"(128) : "memory");
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_taddr;
+
+    const int c0 = blockIdx.z * chunk, c1 = min(N, c0 + chunk);
+    const int lo0 = c0, hi0 = min(c1, tb.excl_lo), lo1 = max(c0, tb.excl_hi), hi1 = c1;
+    const int n0 = hi0 > lo0 ? (hi0 - lo0 + T5_K - 1) / T5_K : 0;
+    const int n1 = hi1 > lo1 ? (hi1 - lo1 + T5_K - 1) / T5_K : 0;
+    const int ntile = n0 + n1;
+
+    if (warp < WS_PROD_WARPS) {
+        // ------------------------------------------------ producers
+        const int row = tid & (T5_M - 1), quarter = tid >> 7;   // sources 8 quarter .. 8 quarter + 7
+        f2x tx = f2_splat(1e18f), ty = tx, tz = tx;
+        if (sub * T5_M + row < tb.count) {
+            const float4 p = pos[tb.start + sub * T5_M + row];
+            tx = f2_splat(p.x); ty = f2_splat(p.y); tz = f2_splat(p.z);
+        }
+        const f2x k2 = f2_splat(k), eta2 = f2_splat(eta), kt2 = f2_splat(kt);
+        const int bn = tid % RC, bc = tid / RC;
+        const bool bduty = bc < T5_K / 4;
+        const int rb = r0 + bn;
+        float4 pa = make_float4(-1e18f, -1e18f, -1e18f, 0.f), pn = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 bv[4];
+        auto prefetch = [&](int i) {
+            int j0, cnt;
+            if (i < n0) { j0 = lo0 + i * T5_K; cnt = min(T5_K, hi0 - j0); }
+            else { j0 = lo1 + (i - n0) * T5_K; cnt = min(T5_K, hi1 - j0); }
+            pa = make_float4(-1e18f, -1e18f, -1e18f, 0.f);
+            pn = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (tid < T5_K && tid < cnt) { pa = pos[j0 + tid]; pn = nrm[j0 + tid]; }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sidx = 4 * bc + q;
+                bv[q] = (bduty && sidx < cnt && rb < R) ? sw[(size_t)(j0 + sidx) * R + rb] : make_float2(0.f, 0.f);
+            }
+        };
+        if (ntile > 0) prefetch(0);
+        for (int it = 0; it < ntile; ++it) {
+            const int st = it & 1, u = it >> 1;
+            const bool ok = (u == 0) || ws_wait(empty0 + 8 * st, (uint32_t)((u - 1) & 1), abort_flag);
+            // all producers agree to go on; also: every producer finished reading s_src
+            if (ws_prod_sync_or(!ok || *abort_flag)) break;
+            const uint32_t sA = base + (uint32_t)st * T5_STAGE;
+            const uint32_t sB = sA + 4 * T5_A_BYTES;
+            if (tid < T5_K) {
+                s_src[0][tid] = pa.x; s_src[1][tid] = pa.y; s_src[2][tid] = pa.z;
+                s_src[3][tid] = pn.x; s_src[4][tid] = pn.y; s_src[5][tid] = pn.z;
+            }
+            if (bduty) {
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { h[q] = t5_tf32(bv[q].x); l[q] = t5_tf32(bv[q].x - __uint_as_float(h[q])); }
+                t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn, bc), h[0], h[1], h[2], h[3]);
+                t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
+                t5_st4(sB + 2 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
+                t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { h[q] = t5_tf32(bv[q].y); l[q] = t5_tf32(bv[q].y - __uint_as_float(h[q])); }
+                t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
+                t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { h[q] ^= 0x80000000u; l[q] ^= 0x80000000u; }
+                t5_st4(sB + 2 * T5_B_BYTES + t5_chunk_off(bn, bc), h[0], h[1], h[2], h[3]);
+                t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
+            }
+            ws_prod_sync();                            // source tile staged
+            if (it + 1 < ntile) prefetch(it + 1);
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c = 2 * quarter + cc;
+                uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const int q = 4 * c + 2 * p;
+                    f2x gr, gi;
+                    t5_pair2(tx, ty, tz, *reinterpret_cast<const f2x *>(&s_src[0][q]),
+                             *reinterpret_cast<const f2x *>(&s_src[1][q]),
+                             *reinterpret_cast<const f2x *>(&s_src[2][q]),
+                             *reinterpret_cast<const f2x *>(&s_src[3][q]),
+                             *reinterpret_cast<const f2x *>(&s_src[4][q]),
+                             *reinterpret_cast<const f2x *>(&s_src[5][q]), k2, eta2, kt2, gr, gi);
+                    t5_split2(gr, rh[2 * p], rh[2 * p + 1], rl[2 * p], rl[2 * p + 1]);
+                    t5_split2(gi, ih[2 * p], ih[2 * p + 1], il[2 * p], il[2 * p + 1]);
+                }
+                const uint32_t off = t5_chunk_off(row, c);
+                t5_st4(sA + 0 * T5_A_BYTES + off, rh[0], rh[1], rh[2], rh[3]);
+                t5_st4(sA + 1 * T5_A_BYTES + off, rl[0], rl[1], rl[2], rl[3]);
+                t5_st4(sA + 2 * T5_A_BYTES + off, ih[0], ih[1], ih[2], ih[3]);
+                t5_st4(sA + 3 * T5_A_BYTES + off, il[0], il[1], il[2], il[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            ws_arrive(full0 + 8 * st);
+        }
+    } else if (warp < WS_PROD_WARPS + 4) {
+        // ------------------------------------------------ epilogue
+        const int q4 = warp - WS_PROD_WARPS;           // TMEM lane quarter (warp mod 4)
+        const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16);
+        float acc[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) acc[q] = 0.f;
+        for (int it = 0; it < ntile; ++it) {
+            const int b = it & 1, v = it >> 1;
+            if (!ws_wait(accfull0 + 8 * b, (uint32_t)(v & 1), abort_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < NC / 16; ++q) t5_ld16(tl + 64 * b + 16 * q, acc + 16 * q);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            ws_arrive(accempty0 + 8 * b);
+        }
+        const bool failed = *abort_flag != 0;
+        const int t = sub * T5_M + 32 * q4 + lane;
+        if (t < tb.count) {
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                if (r0 + r >= R) break;
+                const size_t e = (size_t)(tb.start + t) * R + r0 + r;
+                float2 v = make_float2(acc[r], acc[RC + r]);
+                if (failed) v = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+                if (ypart) ypart[blockIdx.z * split_stride + e] = v;
+                else y[e] = make_double2((double)v.x, (double)v.y);
+            }
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------ MMA issue
+        const int am[6] = {0, 0, 1, 2, 2, 3}, bm[6] = {0, 1, 0, 2, 3, 2};
+        for (int it = 0; it < ntile; ++it) {
+            const int st = it & 1, u = it >> 1;
+            if (!ws_wait(full0 + 8 * st, (uint32_t)(u & 1), abort_flag)) break;
+            if (u >= 1 && !ws_wait(accempty0 + 8 * st, (uint32_t)((u - 1) & 1), abort_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sA = base + (uint32_t)st * T5_STAGE;
+            const uint32_t sB = sA + 4 * T5_A_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < T5_K / 8; ++ks)
+#pragma unroll
+                for (int p = 0; p < 6; ++p)
+                    t5_mma(tmem + 64 * st, t5_desc(sA + am[p] * T5_A_BYTES + 32 * ks),
+                           t5_desc(sB + bm[p] * T5_B_BYTES + 32 * ks), t5_idesc(NC), (ks | p) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             empty0 + 8 * st)
+                         : "memory");
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             accfull0 + 8 * st)
+                         : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T5_TMEM_COLS) : "memory");
+    if (tid == 0 && s_abort) atomicExch(err, 1);
+}
+
+hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit, bool ws)
 {
     if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
     const int N = (int)c->N;
@@ -366,7 +622,11 @@ hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
         if (check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                T5_SMEM), "tcgen05 kernel shared memory") ||
             check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               T5_SMEM), "tcgen05 kernel shared memory"))
+                                               T5_SMEM), "tcgen05 kernel shared memory") ||
+            check_cuda(c, cudaFuncSetAttribute(nbody_tc5ws_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               WS_SMEM), "tcgen05 kernel shared memory") ||
+            check_cuda(c, cudaFuncSetAttribute(nbody_tc5ws_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               WS_SMEM), "tcgen05 kernel shared memory"))
             return HZB_ECUDA;
         attr_done[dev] = true;
     }
@@ -378,7 +638,15 @@ hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
     const int rc = (R <= 16) ? 16 : 32;
     dim3 grid(c->n_tblocks * 4, (R + rc - 1) / rc, nsplit);
     const float k = (float)c->k, eta = (float)c->eta, kt = (float)(c->k / (2.0 * M_PI));
-    if (rc == 16)
+    if (ws && rc == 16)
+        nbody_tc5ws_kernel<16><<<grid, WS_THREADS, WS_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
+                                                                        c->nrm32.ptr, sw, k, eta, kt, part, y, n,
+                                                                        c->kerr.ptr);
+    else if (ws)
+        nbody_tc5ws_kernel<32><<<grid, WS_THREADS, WS_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
+                                                                        c->nrm32.ptr, sw, k, eta, kt, part, y, n,
+                                                                        c->kerr.ptr);
+    else if (rc == 16)
         nbody_tc5_kernel<16><<<grid, T5_THREADS, T5_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
                                                                       c->nrm32.ptr, sw, k, eta, kt, part, y, n,
                                                                       c->kerr.ptr);

@@ -149,7 +149,7 @@ def test_spheroids_258560_sampled_rows():
     # tensor-core contraction, 16 right-hand sides: 258,560 sources per target
     sig16 = rand_c((P.N, 16), 73)
     ref16 = P.interbody(sig16, targets=rows)
-    for engine in (1, 5):                # mma.sync, tcgen05
+    for engine in (1, 5, 6):             # mma.sync, tcgen05, tcgen05 warp-specialised
         s.set_interbody_engine(engine)
         ytc = s.interbody(sig16, precision=1)
         assert rel_l2(ytc[rows], ref16) < 3e-5, engine
@@ -199,14 +199,16 @@ def test_interbody_tensor_cores(pair, R):
     assert rel_l2(got, ref) < 5e-6
 
 
+@pytest.mark.parametrize("engine", [5, 6])
 @pytest.mark.parametrize("R", [1, 5, 16, 40])
-def test_interbody_tcgen05(pair, R):
+def test_interbody_tcgen05(pair, R, engine):
     """FP32 inter-body sum with the contraction on tcgen05 tensor cores (TF32 three-term
-    split, accumulators in tensor memory drained into FP32 sums every 32 sources)."""
+    split, accumulators in tensor memory drained into FP32 sums every 32 sources): the
+    per-CTA form (5) and the warp-specialised pipeline (6)."""
     s, P = pair
     sig = rand_c((P.N, R), 171 + R)
     ref = P.interbody(sig)
-    s.set_interbody_engine(5)
+    s.set_interbody_engine(engine)
     try:
         got = s.interbody(sig, precision=1)
     finally:

@@ -47,7 +47,7 @@ def test_fp64_and_double_float_engines_on_tiny_bodies(tiny, R, engine):
     assert np.abs(ydf - ref).max() < 1e-12 * scale
 
 
-@pytest.mark.parametrize("engine", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("engine", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("R", [1, 5, 17])
 def test_fp32_engines_on_tiny_bodies(tiny, R, engine):
     s, P = tiny
@@ -78,7 +78,7 @@ def test_empty_requests_and_bad_selectors_are_refused(tiny):
     for call in (lambda: s.interbody(np.zeros((P.N, 0), complex)),
                  lambda: s.apply(np.zeros((P.N, 0), complex)),
                  lambda: s.solve_plane_waves(np.zeros((0, 3))),
-                 lambda: s.set_interbody_engine(6),
+                 lambda: s.set_interbody_engine(7),
                  lambda: s.set_interbody_engine(-2),
                  lambda: s.set_fp64_interbody_engine(2),
                  lambda: s.set_modal_engine(7)):
