@@ -63,7 +63,12 @@ typedef enum {
                                  valid for hzb_interbody/hzb_apply and as the refinement residual */
 } hzb_precision;
 
-typedef enum { HZB_SPHERE = 0, HZB_SPHEROID = 1, HZB_OPEN_SHELL = 2 } hzb_shape_kind;
+typedef enum {
+    HZB_SPHERE = 0,
+    HZB_SPHEROID = 1,
+    HZB_OPEN_SHELL = 2,
+    HZB_CURVE_SPLINE = 3   /* generating curve given by points: added with hzb_add_body_curve */
+} hzb_shape_kind;
 
 typedef struct {
     int device;            /* CUDA device ordinal */
@@ -86,7 +91,7 @@ typedef struct {
 } hzb_options;
 
 typedef struct {
-    int kind;              /* hzb_shape_kind */
+    int kind;              /* hzb_shape_kind (HZB_CURVE_SPLINE bodies: hzb_add_body_curve) */
     double p[4];           /* SPHERE: (a); SPHEROID: (a, c) semi-axes (a,a,c);
                               OPEN_SHELL: (R_out, R_in, opening half-angle [rad],
                               rim radius = (R_out - R_in)/2), opening centred on body -z */
@@ -139,6 +144,19 @@ hzb_status hzb_set_wave(hzb_ctx *ctx, double k, double eta);
  * share one set of scattering matrices (the remark on repeated shapes in Sec. 6). */
 hzb_status hzb_add_body(hzb_ctx *ctx, const hzb_shape *shape, const double c[3],
                         const double rot[9], int *body_id);
+
+/* Add a body whose generating curve (Sec. 3.2) is the cubic spline through n_points
+ * points rz[2k] = r_k >= 0, rz[2k+1] = z_k in the body frame, listed from the top pole
+ * (r_0 = 0) down to the bottom pole (r_{n-1} = 0, z_{n-1} < z_0), with r_k > 0 between:
+ * parameter = cumulative chord length t; r(t) with r'' = 0 and z(t) with z' = 0 at both
+ * poles (so the surface closes smoothly on the axis); one Gauss-Legendre panel of
+ * gl_order nodes per spline segment (n_points - 1 panels); n_modes as for hzb_add_body;
+ * c, rot and body_id as for hzb_add_body.  Bodies with the same points, gl_order and
+ * n_modes share their scattering matrices.  Errors: HZB_EINVAL (fewer than 3 or more
+ * than 4097 points, ends off the axis, coincident points, r <= 0 inside, wrong
+ * direction, bad rotation), HZB_ESTATE as hzb_add_body. */
+hzb_status hzb_add_body_curve(hzb_ctx *ctx, const double *rz, int n_points, int gl_order, int n_modes,
+                              const double c[3], const double rot[9], int *body_id);
 
 /* Total node count N (valid after the last hzb_add_body). */
 hzb_status hzb_num_nodes(const hzb_ctx *ctx, long long *n);

@@ -15,7 +15,7 @@ from typing import List, Tuple
 
 import numpy as np
 
-from workloads import OPEN_SHELL, SPHERE, SPHEROID, Body, ShapeSpec
+from workloads import CURVE_SPLINE, OPEN_SHELL, SPHERE, SPHEROID, Body, ShapeSpec
 
 # Near-panel radius in units of the panel's arclength: a panel b is "near" a target
 # on the same curve when some node of b lies closer than NEAR_RHO * L_b.
@@ -106,6 +106,53 @@ class _Rim(Piece):
         return rho * (dc * u[0] + dsn * e[0]), rho * (dc * u[1] + dsn * e[1])
 
 
+class _CubicSegment(Piece):
+    """One segment t in [t_k, t_{k+1}] of a spline generating curve: r and z are cubic
+    polynomials in u = t - t_k with coefficients (c3, c2, c1, c0) (highest power first)."""
+
+    def __init__(self, tk: float, cr, cz):
+        self.tk = tk
+        self.cr = np.asarray(cr, dtype=np.float64)
+        self.cz = np.asarray(cz, dtype=np.float64)
+
+    @staticmethod
+    def _val(c, u):
+        return ((c[0] * u + c[1]) * u + c[2]) * u + c[3]
+
+    @staticmethod
+    def _der(c, u):
+        return (3.0 * c[0] * u + 2.0 * c[1]) * u + c[2]
+
+    @staticmethod
+    def _diff(c, u, h):
+        # p(u + h) - p(u) = h (c1 + c2 (2u + h) + c3 (3u^2 + 3uh + h^2)), no cancellation
+        return h * (c[2] + c[1] * (2.0 * u + h) + c[0] * (3.0 * u * u + 3.0 * u * h + h * h))
+
+    def eval(self, t):
+        u = t - self.tk
+        return self._val(self.cr, u), self._val(self.cz, u), self._der(self.cr, u), self._der(self.cz, u)
+
+    def delta(self, t, h):
+        u = t - self.tk
+        return self._diff(self.cr, u, h), self._diff(self.cz, u, h)
+
+
+def spline_pieces(rz: np.ndarray) -> List[Tuple[Piece, float, float]]:
+    """Spline generating curve through the points rz (n x 2, top pole first): parameter
+    = cumulative chord length; r(t) natural (r'' = 0) and z(t) clamped (z' = 0) at both
+    poles, so the surface of revolution closes smoothly on the axis.  The interpolating
+    cubic splines come from scipy (library routine); one piece per segment."""
+    from scipy.interpolate import CubicSpline
+    rz = np.asarray(rz, dtype=np.float64).reshape(-1, 2)
+    if rz.shape[0] < 3 or rz[0, 0] != 0.0 or rz[-1, 0] != 0.0 or not rz[0, 1] > rz[-1, 1]:
+        raise ValueError("spline curve: >= 3 points from the top pole down to the bottom pole")
+    t = np.concatenate([[0.0], np.cumsum(np.hypot(np.diff(rz[:, 0]), np.diff(rz[:, 1])))])
+    sr = CubicSpline(t, rz[:, 0], bc_type=((2, 0.0), (2, 0.0)))
+    sz = CubicSpline(t, rz[:, 1], bc_type=((1, 0.0), (1, 0.0)))
+    return [(_CubicSegment(t[k], sr.c[:, k], sz.c[:, k]), float(t[k]), float(t[k + 1]))
+            for k in range(t.size - 1)]
+
+
 @dataclass
 class Curve:
     pieces: List[Tuple[Piece, float, float]]      # (piece, t0, t1)
@@ -145,6 +192,11 @@ def shape_curve(shape: ShapeSpec) -> Curve:
                   (_Rim(0.5 * (r_out + r_in), rho, th), 0.0, np.pi),
                   (_Arc(r_in, th, -1.0), 0.0, th)]
         counts = list(shell_panel_split(n, r_out * th, np.pi * rho, r_in * th))
+    elif shape.kind == CURVE_SPLINE:
+        pieces = spline_pieces(shape.curve_points())
+        if len(pieces) != n:
+            raise ValueError("a spline curve has one panel per segment")
+        counts = [1] * n
     else:
         raise ValueError("unknown shape kind %r" % shape.kind)
     panels = []

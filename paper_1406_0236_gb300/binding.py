@@ -133,6 +133,7 @@ def lib():
         "hzb_set_fp64_interbody_engine": (i, [p, i]),
         "hzb_tuned_config": (i, [p, i, p]),
         "hzb_save_scattering": (i, [p, ctypes.c_char_p]),
+        "hzb_add_body_curve": (i, [p, _D, i, i, i, _D, _D, ctypes.POINTER(i)]),
         "hzb_load_scattering": (i, [p, ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
@@ -223,6 +224,11 @@ class Solver:
 
     # ------------------------------------------------------------ geometry
     def add_body(self, kind: int, params, n_panels: int, gl_order: int, n_modes: int, center, rot) -> int:
+        if int(kind) == 3:                  # spline generating curve: params = (r0, z0, r1, z1, ...)
+            rz = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1))
+            if rz.size // 2 - 1 != int(n_panels):
+                raise ValueError("a spline curve has one panel per segment: n_panels = points - 1")
+            return self.add_body_curve(rz.reshape(-1, 2), gl_order, n_modes, center, rot)
         s = _Shape()
         s.kind = int(kind)
         pp = list(params) + [0.0] * (4 - len(params))
@@ -244,6 +250,19 @@ class Solver:
             sh = b.shape
             s.add_body(sh.kind, sh.params, sh.n_panels, sh.gl_order, sh.n_modes, b.center, b.rot)
         return s
+
+    def add_body_curve(self, rz, gl_order: int, n_modes: int, center, rot) -> int:
+        """Body whose generating curve is the cubic spline through the (r, z) points rz
+        (top pole first, both ends on the axis); one panel per spline segment."""
+        pts = np.ascontiguousarray(np.asarray(rz, dtype=np.float64).reshape(-1, 2))
+        c = np.ascontiguousarray(center, dtype=np.float64)
+        r = np.ascontiguousarray(np.asarray(rot, dtype=np.float64).reshape(9))
+        bid = ctypes.c_int()
+        self._check(lib().hzb_add_body_curve(self._h, pts.ctypes.data_as(_D), int(pts.shape[0]), int(gl_order),
+                                             int(n_modes), c.ctypes.data_as(_D), r.ctypes.data_as(_D),
+                                             ctypes.byref(bid)))
+        self.bodies += 1
+        return bid.value
 
     @property
     def N(self) -> int:

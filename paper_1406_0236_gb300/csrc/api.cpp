@@ -172,9 +172,33 @@ static bool same_shape(const hzb_shape &a, const hzb_shape &b)
     return true;
 }
 
+static hzb_status add_body_impl(hzb_ctx *c, const hzb_shape *shape, const std::vector<double> &curve,
+                                const double cen[3], const double rot[9], int *body_id);
+
 hzb_status hzb_add_body(hzb_ctx *c, const hzb_shape *shape, const double cen[3], const double rot[9], int *body_id)
 {
     if (!c) return HZB_EINVAL;
+    if (shape && shape->kind == HZB_CURVE_SPLINE) return fail(c, HZB_EINVAL, "spline curves go through hzb_add_body_curve");
+    return add_body_impl(c, shape, std::vector<double>(), cen, rot, body_id);
+}
+
+hzb_status hzb_add_body_curve(hzb_ctx *c, const double *rz, int n_points, int gl_order, int n_modes,
+                              const double cen[3], const double rot[9], int *body_id)
+{
+    if (!c) return HZB_EINVAL;
+    if (!rz || n_points < 3 || n_points > 4097) return fail(c, HZB_EINVAL, "curve needs 3..4097 points");
+    hzb_shape sh;
+    std::memset(&sh, 0, sizeof(sh));
+    sh.kind = HZB_CURVE_SPLINE;
+    sh.n_panels = n_points - 1;
+    sh.gl_order = gl_order;
+    sh.n_modes = n_modes;
+    return add_body_impl(c, &sh, std::vector<double>(rz, rz + 2 * (size_t)n_points), cen, rot, body_id);
+}
+
+static hzb_status add_body_impl(hzb_ctx *c, const hzb_shape *shape, const std::vector<double> &curve,
+                                const double cen[3], const double rot[9], int *body_id)
+{
     if (c->state < 1 || c->state > 2) return fail(c, HZB_ESTATE, "hzb_add_body needs hzb_set_wave and no build yet");
     if (!shape || !cen || !rot) return fail(c, HZB_EINVAL, "null argument");
     for (int q = 0; q < 3; ++q)
@@ -192,12 +216,12 @@ hzb_status hzb_add_body(hzb_ctx *c, const hzb_shape *shape, const double cen[3],
     if (det < 0) return fail(c, HZB_EINVAL, "rotation has determinant -1");
     int sidx = -1;
     for (size_t s = 0; s < c->shapes.size(); ++s)
-        if (same_shape(c->shapes[s]->geom.spec, *shape)) sidx = (int)s;
+        if (same_shape(c->shapes[s]->geom.spec, *shape) && c->shapes[s]->geom.curve_rz == curve) sidx = (int)s;
     if (sidx < 0) {
         ShapeDev *sd = new (std::nothrow) ShapeDev();
         if (!sd) return HZB_ENOMEM;
         std::string err;
-        if (!build_shape_geometry(*shape, sd->geom, err)) {
+        if (!build_shape_geometry(*shape, curve, sd->geom, err)) {
             delete sd;
             return fail(c, HZB_EINVAL, err);
         }

@@ -51,7 +51,7 @@ void piece_eval(const Piece &pc, double t, double &r, double &z, double &dr, dou
 {
     CurvePiece cp;
     cp.type = pc.type;
-    for (int q = 0; q < 6; ++q) cp.p[q] = pc.p[q];
+    for (int q = 0; q < 10; ++q) cp.p[q] = pc.p[q];
     curve_eval(cp, t, r, z, dr, dz);
 }
 
@@ -90,9 +90,51 @@ static double nearest_parameter(const Piece &pc, double ta, double tb, double r0
 // curve, or when some node of b lies closer to i than NEAR_RHO * L_b.
 static const double NEAR_RHO = 1.0;
 
-bool build_shape_geometry(const hzb_shape &spec, ShapeGeom &g, std::string &err)
+// Cubic spline through (t_k, y_k), k = 0..n-1, as power-form segments
+// y = a + b u + c u^2 + d u^3, u = t - t_k: second derivatives M_k from the tridiagonal
+// continuity equations (Thomas algorithm); end conditions either y'' = 0 (natural) or
+// y' = 0 (clamped) at both ends.
+static void cubic_spline(const std::vector<double> &t, const std::vector<double> &y, bool clamped,
+                         std::vector<double> &a, std::vector<double> &b, std::vector<double> &c,
+                         std::vector<double> &d)
+{
+    const int n = (int)t.size();
+    std::vector<double> h(n - 1), lo(n, 0.0), di(n, 0.0), up(n, 0.0), rhs(n, 0.0), M(n, 0.0);
+    for (int k = 0; k + 1 < n; ++k) h[k] = t[k + 1] - t[k];
+    for (int k = 1; k + 1 < n; ++k) {
+        lo[k] = h[k - 1];
+        di[k] = 2.0 * (h[k - 1] + h[k]);
+        up[k] = h[k];
+        rhs[k] = 6.0 * ((y[k + 1] - y[k]) / h[k] - (y[k] - y[k - 1]) / h[k - 1]);
+    }
+    if (clamped) {              // y'(t_0) = y'(t_{n-1}) = 0
+        di[0] = 2.0 * h[0]; up[0] = h[0]; rhs[0] = 6.0 * (y[1] - y[0]) / h[0];
+        lo[n - 1] = h[n - 2]; di[n - 1] = 2.0 * h[n - 2]; rhs[n - 1] = -6.0 * (y[n - 1] - y[n - 2]) / h[n - 2];
+    } else {                    // y''(t_0) = y''(t_{n-1}) = 0
+        di[0] = 1.0; up[0] = 0.0; rhs[0] = 0.0;
+        lo[n - 1] = 0.0; di[n - 1] = 1.0; rhs[n - 1] = 0.0;
+    }
+    for (int k = 1; k < n; ++k) {       // forward elimination
+        const double m = lo[k] / di[k - 1];
+        di[k] -= m * up[k - 1];
+        rhs[k] -= m * rhs[k - 1];
+    }
+    M[n - 1] = rhs[n - 1] / di[n - 1];
+    for (int k = n - 2; k >= 0; --k) M[k] = (rhs[k] - up[k] * M[k + 1]) / di[k];
+    a.resize(n - 1); b.resize(n - 1); c.resize(n - 1); d.resize(n - 1);
+    for (int k = 0; k + 1 < n; ++k) {
+        a[k] = y[k];
+        b[k] = (y[k + 1] - y[k]) / h[k] - h[k] * (2.0 * M[k] + M[k + 1]) / 6.0;
+        c[k] = 0.5 * M[k];
+        d[k] = (M[k + 1] - M[k]) / (6.0 * h[k]);
+    }
+}
+
+bool build_shape_geometry(const hzb_shape &spec, const std::vector<double> &curve_rz, ShapeGeom &g,
+                          std::string &err)
 {
     g.spec = spec;
+    g.curve_rz = curve_rz;
     if (spec.n_modes < 3 || spec.n_modes > 1023 || spec.n_modes % 2 == 0) {
         err = "n_modes must be odd in [3, 1023]";
         return false;
@@ -129,6 +171,40 @@ bool build_shape_geometry(const hzb_shape &spec, ShapeGeom &g, std::string &err)
         int rest = n - nr;
         int no = (int)std::lround(rest * Lo / (Lo + Li));
         counts = {no, nr, rest - no};
+    } else if (spec.kind == HZB_CURVE_SPLINE) {
+        // points from the top pole to the bottom pole (both on the axis); chord-length
+        // parameter; r natural, z clamped (z' = 0) at the poles; one panel per segment
+        const int n = (int)curve_rz.size() / 2;
+        if (n < 3 || (int)curve_rz.size() != 2 * n || n - 1 != spec.n_panels) {
+            err = "curve needs >= 3 points (r, z) and n_panels = points - 1";
+            return false;
+        }
+        if (curve_rz[0] != 0.0 || curve_rz[2 * (n - 1)] != 0.0) {
+            err = "the curve must start and end on the axis (r = 0)";
+            return false;
+        }
+        std::vector<double> t(n, 0.0), r(n), z(n);
+        for (int k = 0; k < n; ++k) {
+            r[k] = curve_rz[2 * k];
+            z[k] = curve_rz[2 * k + 1];
+            if (!std::isfinite(r[k]) || !std::isfinite(z[k]) || (k > 0 && k < n - 1 && !(r[k] > 0.0))) {
+                err = "curve points must be finite with r > 0 between the poles";
+                return false;
+            }
+            if (k > 0) {
+                const double h = std::hypot(r[k] - r[k - 1], z[k] - z[k - 1]);
+                if (!(h > 0.0)) { err = "consecutive curve points coincide"; return false; }
+                t[k] = t[k - 1] + h;
+            }
+        }
+        if (!(z[0] > z[n - 1])) { err = "the curve must run from the top pole down (outward normal)"; return false; }
+        std::vector<double> ar, br, cr, dr, az, bz, cz, dz;
+        cubic_spline(t, r, false, ar, br, cr, dr);
+        cubic_spline(t, z, true, az, bz, cz, dz);
+        for (int k = 0; k + 1 < n; ++k) {
+            g.pieces.push_back(Piece{3, {ar[k], br[k], cr[k], dr[k], az[k], bz[k], cz[k], dz[k], t[k], 0.0}, t[k], t[k + 1]});
+            counts.push_back(1);
+        }
     } else {
         err = "unknown shape kind";
         return false;

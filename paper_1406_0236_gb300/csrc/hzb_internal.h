@@ -17,7 +17,7 @@ namespace hzb {
 // type 1: arc of radius R at polar angle th0 + sg * t; type 2: rim semicircle.
 struct Piece {
     int type;
-    double p[6];
+    double p[10];
     double t0, t1;
 };
 
@@ -29,6 +29,7 @@ struct Panel {
 // Discretised generating curve of one distinct shape.
 struct ShapeGeom {
     hzb_shape spec;
+    std::vector<double> curve_rz;         // HZB_CURVE_SPLINE: the n_panels + 1 points (r, z)
     int NG = 0, NF = 0, M = 0;
     std::vector<Piece> pieces;
     std::vector<Panel> panels;
@@ -41,7 +42,8 @@ struct ShapeGeom {
     std::vector<double> near_tstar;       // closest parameter on that panel
 };
 
-bool build_shape_geometry(const hzb_shape &spec, ShapeGeom &g, std::string &err);
+bool build_shape_geometry(const hzb_shape &spec, const std::vector<double> &curve_rz, ShapeGeom &g,
+                          std::string &err);
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
 // evaluate gamma and gamma' of a piece at t
 void piece_eval(const Piece &pc, double t, double &r, double &z, double &dr, double &dz);

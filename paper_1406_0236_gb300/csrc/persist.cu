@@ -3,11 +3,13 @@
 // that shape at the same wavenumber), so that a later context skips the setup.
 //
 // File layout (little-endian, as the host writes it):
-//   char magic[8] = "HZBSCAT1"; int32 version = 1; int32 n_shapes;
+//   char magic[8] = "HZBSCAT1"; int32 version = 2; int32 n_shapes;
 //   double k, eta;
-//   per shape: hzb_shape spec (the struct as laid out by this library), int32 NG, int32 M,
-//              then (M+1) NG NG complex doubles of A~_p, then the same of S_p,
-//              p = 0..M, each matrix row-major (row = target ring).
+//   per shape: hzb_shape spec (the struct as laid out by this library, padding zeroed),
+//              int32 NG, int32 M, int32 n_curve, n_curve doubles (the spline curve's
+//              (r, z) points, none for the analytic shapes), then (M+1) NG NG complex
+//              doubles of A~_p, then the same of S_p, p = 0..M, each matrix row-major
+//              (row = target ring).
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -46,7 +48,7 @@ extern "C" hzb_status hzb_save_scattering(hzb_ctx *c, const char *path)
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(c, HZB_EINVAL, std::string("cannot open for writing: ") + path);
     bool ok = true;
-    const int version = 1, ns = (int)c->shapes.size();
+    const int version = 2, ns = (int)c->shapes.size();
     ok &= std::fwrite(HZB_SCAT_MAGIC, 1, 8, f) == 8;
     ok &= std::fwrite(&version, sizeof(int), 1, f) == 1;
     ok &= std::fwrite(&ns, sizeof(int), 1, f) == 1;
@@ -66,6 +68,9 @@ extern "C" hzb_status hzb_save_scattering(hzb_ctx *c, const char *path)
         ok &= std::fwrite(&spec, sizeof(hzb_shape), 1, f) == 1;
         ok &= std::fwrite(&NG, sizeof(int), 1, f) == 1;
         ok &= std::fwrite(&M, sizeof(int), 1, f) == 1;
+        const int ncv = (int)sd.geom.curve_rz.size();
+        ok &= std::fwrite(&ncv, sizeof(int), 1, f) == 1;
+        if (ncv > 0) ok &= std::fwrite(sd.geom.curve_rz.data(), sizeof(double), ncv, f) == (size_t)ncv;
         const size_t nmat = (size_t)(M + 1) * NG * NG;
         host.resize(nmat);
         for (const DevBuf<double2> *b : {&sd.A64, &sd.S64}) {
@@ -95,7 +100,7 @@ extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
     int version = 0, ns = 0;
     double k = 0.0, eta = 0.0;
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, HZB_SCAT_MAGIC, 8) == 0;
-    ok = ok && std::fread(&version, sizeof(int), 1, f) == 1 && version == 1;
+    ok = ok && std::fread(&version, sizeof(int), 1, f) == 1 && version == 2;
     ok = ok && std::fread(&ns, sizeof(int), 1, f) == 1 && std::fread(&k, sizeof(double), 1, f) == 1 &&
          std::fread(&eta, sizeof(double), 1, f) == 1;
     if (!ok) {
@@ -111,9 +116,13 @@ extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
         ShapeDev &sd = *c->shapes[s];
         hzb_shape spec;
         int NG = 0, M = 0;
+        int ncv = 0;
         ok = std::fread(&spec, sizeof(hzb_shape), 1, f) == 1 && std::fread(&NG, sizeof(int), 1, f) == 1 &&
-             std::fread(&M, sizeof(int), 1, f) == 1;
-        if (!ok || !same_shape(spec, sd.geom.spec) || NG != sd.geom.NG || M != sd.geom.M) {
+             std::fread(&M, sizeof(int), 1, f) == 1 && std::fread(&ncv, sizeof(int), 1, f) == 1 && ncv >= 0 &&
+             ncv <= 2 * 4097;
+        std::vector<double> curve(ok ? ncv : 0);
+        if (ok && ncv > 0) ok = std::fread(curve.data(), sizeof(double), ncv, f) == (size_t)ncv;
+        if (!ok || !same_shape(spec, sd.geom.spec) || NG != sd.geom.NG || M != sd.geom.M || curve != sd.geom.curve_rz) {
             std::fclose(f);
             return fail(c, HZB_EINVAL, "shape " + std::to_string(s) + " differs from the file's");
         }

@@ -530,7 +530,7 @@ hzb_status build_shape_matrices(hzb_ctx *c, ShapeDev &sd)
     for (const Piece &p : g.pieces) {
         CurvePiece cp;
         cp.type = p.type;
-        for (int q = 0; q < 6; ++q) cp.p[q] = p.p[q];
+        for (int q = 0; q < 10; ++q) cp.p[q] = p.p[q];
         pieces.push_back(cp);
     }
     std::vector<int> panel_piece;

@@ -12,6 +12,7 @@ SHAPES = {
     "sphere": W.ShapeSpec(W.SPHERE, (1.0,), 6, 8, 13),
     "spheroid": W.ShapeSpec(W.SPHEROID, (1.0, 2.0), 7, 8, 15),
     "shell": W.ShapeSpec(W.OPEN_SHELL, (1.0, 0.8, np.pi / 3, 0.1), 9, 8, 13),
+    "spline": W.ShapeSpec(W.CURVE_SPLINE, W.pear_curve(11), 10, 8, 13),
 }
 
 

@@ -71,6 +71,29 @@ def test_green_identity_on_device():
     assert np.abs(u - ue).max() / np.abs(ue).max() < 1e-10
 
 
+def test_green_identity_spline_bodies_on_device():
+    """Green's identity (the paper's accuracy test) on two pear-shaped spline bodies and a
+    sphere: interior point sources' data are reproduced outside."""
+    require_gpu()
+    from oracle import fields
+    pear = W.ShapeSpec(W.CURVE_SPLINE, W.pear_curve(21), 20, 10, 31)
+    ball = W.ShapeSpec(W.SPHERE, (0.7,), 8, 10, 31)
+    bodies = [W.Body(pear, np.array([-1.6, 0.0, 0.0]), W.rotation_taking_z_to([0.3, 0.2, 1.0])),
+              W.Body(pear, np.array([1.7, 0.2, 0.1]), W.rotation_taking_z_to([-0.5, 1.0, 0.2])),
+              W.Body(ball, np.array([0.0, 2.2, -0.3]), np.eye(3))]
+    wl = W.Workload("pears", bodies, 2.0, 2.0, np.array([[0, 0, 1.0]]))
+    s = gpu_solver(wl, tol=1e-12)
+    x, _, _ = s.get_nodes()
+    src = np.array([[-1.6, 0.05, 0.1], [1.7, 0.15, 0.05], [0.1, 2.2, -0.3]])
+    tg = W.exterior_targets(wl, 10, 6)
+    v = -fields.point_source_field(x, src, wl.k)
+    st = s.solve_data(v)
+    assert st.converged
+    u = s.eval_field(tg)[:, 0]
+    ue = fields.point_source_field(tg, src, wl.k)
+    assert np.abs(u - ue).max() / np.abs(ue).max() < 1e-8
+
+
 def test_mie_single_sphere_on_device():
     require_gpu()
     from oracle import fields

@@ -97,3 +97,65 @@ def test_rotation_takes_ez_to_axis():
         assert np.allclose(R.T @ R, np.eye(3), atol=1e-14)
         assert abs(np.linalg.det(R) - 1) < 1e-14
         assert np.allclose(R[:, 2], a / np.linalg.norm(a), atol=1e-14)
+
+
+def _sphere_points(n):
+    th = np.linspace(0.0, np.pi, n)
+    rz = np.stack([np.sin(th), np.cos(th)], axis=1)
+    rz[0, 0] = rz[-1, 0] = 0.0
+    return rz
+
+
+def test_spline_curve_interpolates_with_pole_conditions():
+    """The spline pieces pass through the points, r'' = 0 and z' = 0 at both poles, and
+    value, first and second derivative are continuous at the joints."""
+    from oracle.geometry import spline_pieces
+    rz = np.asarray(W.pear_curve(11)).reshape(-1, 2)
+    pcs = spline_pieces(rz)
+    for k, (pc, t0, t1) in enumerate(pcs):
+        r0, z0, _, _ = pc.eval(np.array(t0))
+        r1, z1, _, _ = pc.eval(np.array(t1))
+        assert abs(r0 - rz[k, 0]) < 1e-14 and abs(z0 - rz[k, 1]) < 1e-14
+        assert abs(r1 - rz[k + 1, 0]) < 1e-13 and abs(z1 - rz[k + 1, 1]) < 1e-13
+    first, last = pcs[0][0], pcs[-1][0]
+    assert abs(first.cr[1]) < 1e-14 and abs(first.cz[2]) < 1e-14          # r''(0) = 0, z'(0) = 0
+    u = pcs[-1][2] - pcs[-1][1]
+    assert abs(6 * last.cr[0] * u + 2 * last.cr[1]) < 1e-12              # r''(end) = 0
+    assert abs(3 * last.cz[0] * u * u + 2 * last.cz[1] * u + last.cz[2]) < 1e-12   # z'(end) = 0
+    for (a, _, ta1), (b, tb0, _) in zip(pcs[:-1], pcs[1:]):
+        ea, eb = a.eval(np.array(ta1)), b.eval(np.array(tb0))
+        assert np.allclose(ea, eb, atol=1e-12)
+        # second derivatives r'' and z'' agree at the joint
+        ua = ta1 - a.tk
+        assert abs((6 * a.cr[0] * ua + 2 * a.cr[1]) - 2 * b.cr[1]) < 1e-10
+        assert abs((6 * a.cz[0] * ua + 2 * a.cz[1]) - 2 * b.cz[1]) < 1e-10
+
+
+def test_spline_surface_rule_integrates_its_own_area():
+    """The tensor rule on the spline body integrates the area of that surface of
+    revolution, 2 pi int r |gamma'| dt, computed independently by adaptive quadrature
+    of scipy's spline objects."""
+    from scipy.integrate import quad
+    from scipy.interpolate import CubicSpline
+    rz = np.asarray(W.pear_curve(13)).reshape(-1, 2)
+    t = np.concatenate([[0.0], np.cumsum(np.hypot(np.diff(rz[:, 0]), np.diff(rz[:, 1])))])
+    sr = CubicSpline(t, rz[:, 0], bc_type=((2, 0.0), (2, 0.0)))
+    sz = CubicSpline(t, rz[:, 1], bc_type=((1, 0.0), (1, 0.0)))
+    f = lambda x: 2 * np.pi * sr(x) * np.hypot(sr(x, 1), sz(x, 1))
+    exact = sum(quad(f, t[k], t[k + 1], epsabs=0.0, epsrel=1e-13, limit=200)[0] for k in range(t.size - 1))
+    shape = W.ShapeSpec(W.CURVE_SPLINE, tuple(rz.reshape(-1)), 12, 10, 9)
+    area, nsum, _ = _integrals(shape)
+    assert abs(area - exact) < 1e-12 * exact
+    assert np.abs(nsum).max() < 1e-12
+
+
+def test_spline_through_sphere_points_converges_to_the_sphere():
+    """Spline curves through points of the unit circle give surfaces whose area tends to
+    4 pi at the interpolation order (error / 16 when the point spacing halves)."""
+    errs = []
+    for n in (17, 33, 65):
+        shape = W.ShapeSpec(W.CURVE_SPLINE, tuple(_sphere_points(n).reshape(-1)), n - 1, 8, 9)
+        area, _, vol = _integrals(shape)
+        errs.append(abs(area - 4 * np.pi))
+        assert abs(vol - 4 * np.pi / 3) < 1e-3
+    assert errs[1] < errs[0] / 8 and errs[2] < errs[1] / 8

@@ -24,6 +24,7 @@ from scipy.spatial import cKDTree
 SPHERE = 0
 SPHEROID = 1
 OPEN_SHELL = 2
+CURVE_SPLINE = 3
 
 DEFAULT_SEED = 20140601
 
@@ -37,6 +38,9 @@ class ShapeSpec:
     kind OPEN_SHELL: params = (R_out, R_in, half_angle_rad, rim_radius)
                      a thick spherical shell whose opening (centred on body -z)
                      has the given half-angle; the rim is a semicircle.
+    kind CURVE_SPLINE: params = (r_0, z_0, r_1, z_1, ...), the points of a cubic-spline
+                     generating curve from the top pole (r_0 = 0) to the bottom pole;
+                     n_panels must equal the number of points - 1 (one panel per segment).
     n_panels Gauss-Legendre panels of gl_order nodes each on the generating
     curve, n_modes (odd) equispaced azimuthal nodes.
     """
@@ -59,7 +63,14 @@ class ShapeSpec:
             return float(self.params[0])
         if self.kind == SPHEROID:
             return float(max(self.params[0], self.params[1]))
+        if self.kind == CURVE_SPLINE:
+            rz = np.asarray(self.params, dtype=float).reshape(-1, 2)
+            return float(np.max(np.hypot(rz[:, 0], rz[:, 1])) * 1.05)
         return float(self.params[0])
+
+    def curve_points(self) -> np.ndarray:
+        """(n, 2) array of (r, z) points of a CURVE_SPLINE shape."""
+        return np.asarray(self.params, dtype=float).reshape(-1, 2)
 
 
 @dataclass
@@ -165,6 +176,19 @@ def min_gap(bodies: List[Body]) -> float:
 
 
 # --------------------------------------------------------------------------- workloads
+
+def pear_curve(n_points: int = 13, a: float = 1.0, e: float = 0.25) -> tuple:
+    """Points (r, z) of an egg/pear-shaped generating curve, rho(th) = a (1 + e cos th)
+    sampled at equal polar angles th from 0 (top pole) to pi (bottom pole); a
+    CURVE_SPLINE shape interpolates them with one panel per segment."""
+    th = np.linspace(0.0, np.pi, n_points)
+    rho = a * (1.0 + e * np.cos(th))
+    r = rho * np.sin(th)
+    r[0] = 0.0
+    r[-1] = 0.0
+    z = rho * np.cos(th)
+    return tuple(np.stack([r, z], axis=1).reshape(-1).tolist())
+
 
 def two_spheres(n_panels=10, gl_order=10, n_modes=41, k=2.0, eta=None, sep=1.5,
                 directions=None, name="two_spheres_8200") -> Workload:
