@@ -24,33 +24,39 @@ void launch_modal_gemm_tc(hzb_ctx *c, int n, int nc, int modes, const float2 *A,
 
 
 // One block per (body of the shape, ring).  y is N x R (FP64); out is the shape's
-// panel array (M+1) x NG x ncols in precision T.
+// panel array (M+1) x NG x ncols in precision T, which is also the arithmetic precision
+// (twiddles rounded from FP64 values; the FP32 path's DFT then runs on the FP32 pipe).
 template <typename T>
 __global__ void dft_forward_kernel(int NG, int NF, int R, int ncols, const long long *__restrict__ body_off,
                                    const double2 *__restrict__ y, typename C2<T>::t *__restrict__ yh)
 {
     typedef typename C2<T>::t ct;
     extern __shared__ double smem_d[];
-    double2 *tw = (double2 *)smem_d;                 // NF: e^{-2 pi i m / NF}
-    double2 *ring = tw + NF;                         // NF x R
+    ct *tw = (ct *)smem_d;                           // NF: e^{-2 pi i m / NF}
+    ct *ring = tw + NF;                              // NF x R
     const int bs = blockIdx.y, i = blockIdx.x;
     const int M = (NF - 1) / 2;
     const long long base = body_off[bs] + (long long)i * NF;
     for (int m = threadIdx.x; m < NF; m += blockDim.x) {
         double s, c;
         sincospi(-2.0 * m / NF, &s, &c);
-        tw[m] = make_double2(c, s);
+        tw[m].x = (T)c;
+        tw[m].y = (T)s;
     }
-    for (int e = threadIdx.x; e < NF * R; e += blockDim.x) ring[e] = y[base * R + e];
+    for (int e = threadIdx.x; e < NF * R; e += blockDim.x) {
+        const double2 v = y[base * R + e];
+        ring[e].x = (T)v.x;
+        ring[e].y = (T)v.y;
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < NF * R; e += blockDim.x) {
         const int pidx = e / R, r = e % R;
         const int p = pidx - M;
         const int pm = ((p % NF) + NF) % NF;
-        double sx = 0.0, sy = 0.0;
+        T sx = (T)0, sy = (T)0;
         int idx = 0;
         for (int l = 0; l < NF; ++l) {
-            const double2 v = ring[l * R + r], w = tw[idx];
+            const ct v = ring[l * R + r], w = tw[idx];
             sx = fma(v.x, w.x, fma(-v.y, w.y, sx));
             sy = fma(v.x, w.y, fma(v.y, w.x, sy));
             idx += pm;
@@ -77,38 +83,39 @@ __global__ void dft_inverse_kernel(int NG, int NF, int R, int ncols, const long 
                                    const typename C2<T>::t *__restrict__ th, const double2 *__restrict__ sigma,
                                    double alpha, double beta, double2 *__restrict__ out)
 {
+    typedef typename C2<T>::t ct;
     extern __shared__ double smem_d[];
-    double2 *tw = (double2 *)smem_d;                 // NF: e^{+2 pi i m / NF}
-    double2 *co = tw + NF;                           // NF x R coefficients, p = -M..M
+    ct *tw = (ct *)smem_d;                           // NF: e^{+2 pi i m / NF}
+    ct *co = tw + NF;                                // NF x R coefficients, p = -M..M
     const int bs = blockIdx.y, i = blockIdx.x;
     const int M = (NF - 1) / 2;
     const long long base = body_off[bs] + (long long)i * NF;
     for (int m = threadIdx.x; m < NF; m += blockDim.x) {
         double s, c;
         sincospi(2.0 * m / NF, &s, &c);
-        tw[m] = make_double2(c, s);
+        tw[m].x = (T)c;
+        tw[m].y = (T)s;
     }
     for (int e = threadIdx.x; e < NF * R; e += blockDim.x) {
         const int pidx = e / R, r = e % R, p = pidx - M;
         const int ap = p < 0 ? -p : p, sg = p < 0 ? 1 : 0;
-        const auto v = th[((size_t)ap * NG + i) * ncols + (2 * bs + sg) * R + r];
-        co[e] = make_double2((double)v.x, (double)v.y);
+        co[e] = th[((size_t)ap * NG + i) * ncols + (2 * bs + sg) * R + r];
     }
     __syncthreads();
     const double sc = beta / NF;
     for (int e = threadIdx.x; e < NF * R; e += blockDim.x) {
         const int l = e / R, r = e % R;
-        double sx = 0.0, sy = 0.0;
+        T sx = (T)0, sy = (T)0;
         // p = -M .. M  ->  twiddle index (p l) mod NF, starting at (-M l) mod NF
         int idx = (int)(((long long)(NF - M) * l) % NF);
         for (int pidx = 0; pidx < NF; ++pidx) {
-            const double2 v = co[pidx * R + r], w = tw[idx];
+            const ct v = co[pidx * R + r], w = tw[idx];
             sx = fma(v.x, w.x, fma(-v.y, w.y, sx));
             sy = fma(v.x, w.y, fma(v.y, w.x, sy));
             idx += l;
             if (idx >= NF) idx -= NF;
         }
-        double2 o = make_double2(sx * sc, sy * sc);
+        double2 o = make_double2((double)sx * sc, (double)sy * sc);
         if (alpha != 0.0) {
             const double2 s = sigma[base * R + e];
             o.x = fma(alpha, s.x, o.x);
@@ -218,7 +225,7 @@ static hzb_status local_inverse_t(hzb_ctx *c, int R, const double2 *y, const dou
             S = (const ct *)sd.S32.ptr;
         }
         const long long *doff = sd.body_offs.ptr;        // first node of each body of the shape
-        size_t smem = (size_t)NF * (R + 1) * sizeof(double2);
+        size_t smem = (size_t)NF * (R + 1) * sizeof(ct);
         if (smem > 200 * 1024) return fail(c, HZB_EINVAL, "n_modes * R too large for the modal apply");
         dft_smem_limit<T>(smem);
         dft_forward_kernel<T><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, y, yh);
