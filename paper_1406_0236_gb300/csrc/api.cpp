@@ -504,7 +504,7 @@ hzb_status hzb_set_execution(hzb_ctx *c, int check_every, int use_graphs)
 hzb_status hzb_set_modal_engine(hzb_ctx *c, int engine)
 {
     if (!c) return HZB_EINVAL;
-    if (engine < -1 || engine > 1) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1}");
+    if (engine < -1 || engine > 2) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1, 2}");
     c->modal_engine = engine;
     return HZB_OK;
 }

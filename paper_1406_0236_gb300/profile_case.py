@@ -1,13 +1,13 @@
 """Run one operator of the library on a named workload, for profilers and timing.
 
     python -m paper_1406_0236_gb300.profile_case --workload spheroids8_258560 \
-        --op interbody32 --repeat 2 [--rhs 1] [--autotune] [--engine -1]
+        --op interbody32 --repeat 2 [--rhs 1] [--autotune] [--engine -1] [--modal-engine -1]
 
 ops: interbody32, interbody64, interbody_df (B sigma), local_inverse64, local_inverse32 (D^{-1} y),
 apply64, apply32, solve_mixed, solve_fp64.  Prints the mean time per call measured
 with CUDA events.  Inputs are seeded random densities (ops) or the workload's plane
-waves (solves).  --engine picks the FP32 inter-body engine (0 CUDA cores, 1 tensor
-cores, -1 automatic).
+waves (solves).  --engine picks the FP32 inter-body engine and --modal-engine the FP32
+modal GEMM engine (see Solver.set_interbody_engine / set_modal_engine; -1 automatic).
 """
 from __future__ import annotations
 
@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--rhs", type=int, default=1)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--engine", type=int, default=-1)
+    ap.add_argument("--modal-engine", type=int, default=-1)
     args = ap.parse_args()
 
     import numpy as np
@@ -42,6 +43,7 @@ def main():
     s = Solver.from_workload(wl, Options(precision=min(prec, 1), gmres_tol=1e-8, verify_final=0),
                              stream=torch.cuda.current_stream().cuda_stream)
     s.set_interbody_engine(args.engine)
+    s.set_modal_engine(args.modal_engine)
     needs_build = not args.op.startswith("interbody")
     if needs_build:
         s.build_scattering_matrices()

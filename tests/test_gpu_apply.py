@@ -83,13 +83,15 @@ def test_interbody_fp32_kernel_variants(pair, R, engine):
     assert rel_l2(got, ref) < 2e-6
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("R", [1, 3, 24])
-def test_local_inverse_tensor_cores(pair, R):
-    """FP32 modal GEMM on the tensor cores (TF32 with a three-term split)."""
+def test_local_inverse_tensor_cores(pair, R, engine):
+    """FP32 modal GEMM on the tensor cores (TF32 with a three-term split): mma.sync (1)
+    and tcgen05 (2)."""
     s, P = pair
     y = rand_c((P.N, R), 131 + R)
     ref = P.local_inverse(y)
-    s.set_modal_engine(1)
+    s.set_modal_engine(engine)
     try:
         got = s.local_inverse(y, precision=1)
     finally:

@@ -81,7 +81,7 @@ def test_empty_requests_and_bad_selectors_are_refused(tiny):
                  lambda: s.set_interbody_engine(7),
                  lambda: s.set_interbody_engine(-2),
                  lambda: s.set_fp64_interbody_engine(2),
-                 lambda: s.set_modal_engine(7)):
+                 lambda: s.set_modal_engine(3)):
         with pytest.raises(HzbError) as e:
             call()
         assert e.value.status == -1
