@@ -215,11 +215,13 @@ hzb_status hzb_tuned_config(const hzb_ctx *ctx, int R, int out[6]);
 hzb_status hzb_set_execution(hzb_ctx *ctx, int check_every, int use_graphs);
 
 /* Engine of the FP32 per-mode scattering GEMM (Eq. (singleinverse) step (2)):
- * 0 = CUDA cores; 1 = tensor cores (mma.sync), TF32 with a three-term hi/lo split and
- * FP32 accumulation (about FP32 accuracy); 2 = the same on tcgen05 (accumulators in
- * tensor memory, drained into FP32 registers every 64 of the K = 2 N_G terms); -1
- * (default) = tensor cores when a shape's panel has at least 32 columns (2 x bodies of
- * the shape x right-hand sides).  Returns HZB_EINVAL for other values. */
+ * 0 = CUDA cores; 1 = tensor cores through mma.sync, TF32 with a three-term hi/lo split
+ * and FP32 accumulation (about FP32 accuracy); 2 = the same contraction on tcgen05 with
+ * the operands streamed by TMA (embedded, split S_p images built once per shape: about
+ * 32 N_G^2 (M+1) bytes; accumulators in tensor memory drained into FP32 registers every
+ * 64 of the K = 2 N_G terms); -1 (default) = 2 when a shape's panel has at least 32
+ * columns (2 x bodies of the shape x right-hand sides), else 0.  Returns HZB_EINVAL for
+ * other values. */
 hzb_status hzb_set_modal_engine(hzb_ctx *ctx, int engine);
 
 /* Engine of the FP32 inter-body sum (Sec. 3.3): 0 = CUDA cores (one pair kernel per

@@ -204,7 +204,7 @@ class Solver:
         self._check(lib().hzb_set_execution(self._h, int(check_every), int(use_graphs)))
 
     def set_modal_engine(self, engine: int):
-        """FP32 modal GEMM engine: 0 CUDA cores, 1 tensor cores (mma.sync TF32 x 3), 2 tcgen05, -1 auto."""
+        """FP32 modal GEMM engine: 0 CUDA cores, 1 mma.sync TF32 x 3, 2 tcgen05 fed by TMA, -1 auto."""
         self._check(lib().hzb_set_modal_engine(self._h, int(engine)))
 
     def set_interbody_engine(self, engine: int):

@@ -114,6 +114,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     cudaDeviceSynchronize();
     for (ShapeDev *s : c->shapes) {
         s->ring.release(); s->body_offs.release(); s->A64.release(); s->S64.release(); s->S32.release();
+        s->Aimg.release();
         delete s;
     }
     c->pos64.release(); c->nrm64.release(); c->pos32.release(); c->nrm32.release(); c->body_of.release();
@@ -122,7 +123,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     c->yhat32.release(); c->that32.release(); c->s_b.release(); c->s_r.release(); c->s_d.release();
     c->io_in.release(); c->io_out.release(); c->io_small.release(); c->tiny.release(); c->sol.release();
     c->red.release(); c->krylov.release(); c->small.release();
-    c->sctab.release(); c->nb_part64.release(); c->nb_part32.release(); c->sig32.release(); c->blockpairs.release(); c->kerr.release();
+    c->sctab.release(); c->nb_part64.release(); c->nb_part32.release(); c->sig32.release(); c->blockpairs.release(); c->kerr.release(); c->Ximg.release();
     c->dfa.release(); c->dfb.release(); c->dfc.release(); c->dftab.release();
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
     release_graphs(c);

@@ -78,6 +78,9 @@ struct ShapeDev {
     DevBuf<double2> A64;                  // (M+1) x NG x NG: A~_p
     DevBuf<double2> S64;                  // (M+1) x NG x NG: S_p = A~_p^{-1}
     DevBuf<float2> S32;                   // FP32 copy of S64
+    DevBuf<float> Aimg;                   // embedded, TF32-split S_p for the TMA modal GEMM (modal_tma.cu)
+    alignas(64) unsigned char tmA[128];   // its TMA tensor map (CUtensorMap)
+    bool tmA_ready = false;
 };
 
 struct BodyRec {
@@ -151,6 +154,7 @@ struct hzb_ctx {
     int nbody64_engine = -1;                   // FP64/double-float sums: -1 auto (pair-symmetric for R <= 4),
                                                // 0 one-directional, 1 pair-symmetric
     hzb::DevBuf<int> kerr;                     // device error flag of kernels with bounded waits
+    hzb::DevBuf<float> Ximg;                   // embedded, TF32-split modal panel (TMA modal GEMM)
     bool kerr_ready = false;
     hzb::DevBuf<float2> sig32;                 // w_j sigma_j / (4 pi) in FP32, N x R (FP32 inter-body kernels)
     int tune64_tpt = 0, tune64_split = 0;      // 0: default
@@ -203,6 +207,7 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   // nbody_df.cu
 hzb_status interbody_tc(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);
+hzb_status modal_gemm_tma(hzb_ctx *c, ShapeDev &sd, int ncols, const float2 *X, float2 *Cout);  // modal_tma.cu
 hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit,
                          bool ws);   // nbody_tc5.cu; ws: warp-specialised form
 const float2 *weighted_sigma32(hzb_ctx *c, int R, const double2 *sigma);      // nbody.cu; nullptr on failure

@@ -267,7 +267,7 @@ static hzb_status ensure_pinned(hzb_ctx *c, size_t n)
 
 // Pointers and sizes a captured Arnoldi step depends on: a change invalidates the graphs.
 struct GraphKey {
-    static const int NP = 21;
+    static const int NP = 22;
     const void *p[NP];
     long long N;
     int R, m, precision, tpt32, split32, tpt64, split64, modal_engine, nbody_engine, splittc, tc32, x2, engine64;
@@ -388,7 +388,7 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
                                         c->yhat32.ptr, c->that32.ptr, c->nb_part32.ptr, c->nb_part64.ptr,
                                         c->sctab.ptr, (const void *)c->stream, c->tblocks.ptr, c->sig32.ptr,
                                         c->w_a.ptr, c->w_b.ptr, c->f_a.ptr, c->f_b.ptr, c->dfa.ptr,
-                                        c->blockpairs.ptr};
+                                        c->blockpairs.ptr, c->Ximg.ptr};
         std::memcpy(graph_key.p, ps, sizeof(ps));
         graph_key.N = N; graph_key.R = R; graph_key.m = m; graph_key.precision = precision;
         graph_key.tpt32 = c->tune32_tpt; graph_key.split32 = c->tune32_split;

@@ -10,7 +10,6 @@
 #include <algorithm>
 
 #include "hzb_internal.h"
-#include "tcgen05.cuh"
 #include "kernel_math.cuh"
 
 namespace hzb {
@@ -22,8 +21,6 @@ template <> struct C2<float> { typedef float2 t; };
 static const int DFT_THREADS = 128;
 
 void launch_modal_gemm_tc(hzb_ctx *c, int n, int nc, int modes, const float2 *A, const float2 *B, float2 *C);
-hzb_status launch_modal_gemm_tc5(hzb_ctx *c, int n, int nc, int modes, const float2 *A, const float2 *B,
-                                 float2 *C);
 
 
 // One block per (body of the shape, ring).  y is N x R (FP64); out is the shape's
@@ -233,11 +230,13 @@ static hzb_status local_inverse_t(hzb_ctx *c, int R, const double2 *y, const dou
         dft_smem_limit<T>(smem);
         dft_forward_kernel<T><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, y, yh);
         // FP32 path: tensor cores (TF32 x 3) once the panels are wide enough to fill them
-        const bool tc = (sizeof(T) == 4) && (c->modal_engine == 1 || (c->modal_engine < 0 && ncols >= 32));
-        if (sizeof(T) == 4 && c->modal_engine == 2) {
-            hzb_status st = launch_modal_gemm_tc5(c, NG, ncols, M + 1, (const float2 *)S, (const float2 *)yh, (float2 *)th);
+        // FP32 path: tcgen05 fed by TMA (modal_tma.cu) once the panels are wide enough to
+        // fill the tensor cores, or as chosen; mma.sync TF32 x 3 on request
+        const bool f32 = sizeof(T) == 4;
+        if (f32 && (c->modal_engine == 2 || (c->modal_engine < 0 && ncols >= 32))) {
+            hzb_status st = modal_gemm_tma(c, sd, ncols, (const float2 *)yh, (float2 *)th);
             if (st) return st;
-        } else if (tc)
+        } else if (f32 && c->modal_engine == 1)
             launch_modal_gemm_tc(c, NG, ncols, M + 1, (const float2 *)S, (const float2 *)yh, (float2 *)th);
         else
             modal_gemm_kernel<T><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(NG, ncols, S, yh, th);
@@ -412,166 +411,6 @@ modal_gemm_tc_kernel(int n, int nc, const float2 *__restrict__ A, const float2 *
                 if (col < nc) base[2 * col] = acc[mt][nt][2 * h];
                 if (col + 1 < nc) base[2 * (col + 1)] = acc[mt][nt][2 * h + 1];
             }
-}
-
-// ---------------------------------------------------------------- tcgen05 modal GEMM
-//
-// C[p] = A[p] B[p] (A = S_p: n x n complex; B, C: n x nc complex, row-major) on the
-// 5th-generation tensor cores through the real embedding
-//     [Cr; Ci] = [[Ar, -Ai], [Ai, Ar]] [Br; Bi]      (M = K = 2n, N = nc),
-// each real product in TF32 with a three-term hi/lo split.  A CTA of 256 threads owns a
-// 128 x 64 tile of the embedded C for one mode; per 32-wide K chunk the threads write the
-// A tile (128 rows x 32, K-major) and the B tile (64 columns x 32, K-major) with the
-// 128-byte swizzle, one thread issues 12 tcgen05 MMAs into tensor memory and commits them
-// to an mbarrier (bounded wait); every two chunks the eight warps add the accumulator
-// (32 lanes x 32 columns each) into FP32 registers and the next chunk starts from zero.
-static const int MG_M = 128, MG_N = 64, MG_K = 32, MG_THREADS = 256, MG_FLUSH = 2;
-static const int MG_A = MG_M * MG_K * 4, MG_B = MG_N * MG_K * 4;
-static const int MG_SMEM = 2 * MG_A + 2 * MG_B + 1024;
-
-__global__ void __launch_bounds__(MG_THREADS)
-modal_gemm_tc5_kernel(int n, int nc, const float2 *__restrict__ A, const float2 *__restrict__ B,
-                      float2 *__restrict__ C, int *__restrict__ err)
-{
-    extern __shared__ __align__(1024) unsigned char mg_smem_raw[];
-    __shared__ uint32_t s_taddr;
-    __shared__ __align__(8) unsigned long long s_mbar;
-    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(mg_smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t sAh = base, sAl = base + MG_A, sBh = base + 2 * MG_A, sBl = sBh + MG_B;
-    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
-    const int p = blockIdx.z, m0 = blockIdx.y * MG_M, c0 = blockIdx.x * MG_N;
-    const int n2 = 2 * n;
-    const float2 *Ap = A + (size_t)p * n * n;
-    const float2 *Bp = B + (size_t)p * n * nc;
-    float2 *Cp = C + (size_t)p * n * nc;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) {
-        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(MG_N)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = s_taddr;
-    const uint32_t tmem_warp = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
-    float acc[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = 0.f;
-    // A duty: row `arow`, chunks 4 ahalf .. +3; B duty: column `bcol`, chunks 2 bq, 2 bq + 1
-    const int arow = tid & (MG_M - 1), ahalf = tid >> 7;
-    const int bcol = tid & (MG_N - 1), bq = tid >> 6;
-    const int m = m0 + arow, mr = m < n ? m : m - n;
-    const int cg = c0 + bcol;
-    const int nk = (n2 + MG_K - 1) / MG_K;
-    uint32_t phase = 0;
-    bool failed = false;
-    for (int kc = 0; kc < nk; ++kc) {
-        const int k0 = kc * MG_K;
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();                               // previous chunk's operands consumed
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            const int c = 4 * ahalf + cc;
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int k = k0 + 4 * c + q;
-                float a = 0.f;
-                if (m < n2 && k < n2) {
-                    const float2 v = Ap[(size_t)mr * n + (k < n ? k : k - n)];
-                    a = (m < n) ? (k < n ? v.x : -v.y) : (k < n ? v.y : v.x);
-                }
-                h[q] = t5_tf32(a);
-                l[q] = t5_tf32(a - __uint_as_float(h[q]));
-            }
-            t5_st4(sAh + t5_chunk_off(arow, c), h[0], h[1], h[2], h[3]);
-            t5_st4(sAl + t5_chunk_off(arow, c), l[0], l[1], l[2], l[3]);
-        }
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int c = 2 * bq + cc;
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int k = k0 + 4 * c + q;
-                float b = 0.f;
-                if (k < n2 && cg < nc) {
-                    const float2 v = Bp[(size_t)(k < n ? k : k - n) * nc + cg];
-                    b = (k < n) ? v.x : v.y;
-                }
-                h[q] = t5_tf32(b);
-                l[q] = t5_tf32(b - __uint_as_float(h[q]));
-            }
-            t5_st4(sBh + t5_chunk_off(bcol, c), h[0], h[1], h[2], h[3]);
-            t5_st4(sBl + t5_chunk_off(bcol, c), l[0], l[1], l[2], l[3]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t as[3] = {sAh, sAh, sAl}, bs[3] = {sBh, sBl, sBh};
-            const bool first = (kc % MG_FLUSH) == 0;
-#pragma unroll
-            for (int ks = 0; ks < MG_K / 8; ++ks)
-#pragma unroll
-                for (int t = 0; t < 3; ++t)
-                    t5_mma(tmem, t5_desc(as[t] + 32 * ks), t5_desc(bs[t] + 32 * ks), t5_idesc(MG_N),
-                           (first && ks == 0 && t == 0) ? 0u : 1u);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                         : "memory");
-        }
-        const bool ok = t5_wait(mbar, phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if ((kc % MG_FLUSH) == MG_FLUSH - 1 || kc == nk - 1) t5_ld32(tmem_warp, acc);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MG_N) : "memory");
-    if (failed && tid == 0) atomicExch(err, 1);
-    const int r = m0 + 32 * (warp & 3) + lane;
-    if (r >= n2) return;
-    const int rr = r < n ? r : r - n, comp = r < n ? 0 : 1;
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        const int col = c0 + 32 * (warp >> 2) + q;
-        if (col < nc)
-            reinterpret_cast<float *>(&Cp[(size_t)rr * nc + col])[comp] =
-                failed ? __int_as_float(0x7fc00000) : acc[q];
-    }
-}
-
-hzb_status launch_modal_gemm_tc5(hzb_ctx *c, int n, int nc, int modes, const float2 *A, const float2 *B, float2 *C)
-{
-    if (check_cuda(c, c->kerr.ensure(1), "alloc error flag")) return HZB_ENOMEM;
-    if (!c->kerr_ready) {
-        if (check_cuda(c, cudaMemsetAsync(c->kerr.ptr, 0, sizeof(int), c->stream), "clear error flag"))
-            return HZB_ECUDA;
-        c->kerr_ready = true;
-    }
-    static bool attr_done[64] = {false};
-    const int dev = c->opt.device;
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        if (check_cuda(c, cudaFuncSetAttribute(modal_gemm_tc5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               MG_SMEM), "tcgen05 modal GEMM shared memory"))
-            return HZB_ECUDA;
-        attr_done[dev] = true;
-    }
-    dim3 grid((nc + MG_N - 1) / MG_N, (2 * n + MG_M - 1) / MG_M, modes);
-    modal_gemm_tc5_kernel<<<grid, MG_THREADS, MG_SMEM, c->stream>>>(n, nc, A, B, C, c->kerr.ptr);
-    return HZB_OK;
 }
 
 void launch_modal_gemm_tc(hzb_ctx *c, int n, int nc, int modes, const float2 *A, const float2 *B, float2 *C)

@@ -87,7 +87,7 @@ def test_interbody_fp32_kernel_variants(pair, R, engine):
 @pytest.mark.parametrize("R", [1, 3, 24])
 def test_local_inverse_tensor_cores(pair, R, engine):
     """FP32 modal GEMM on the tensor cores (TF32 with a three-term split): mma.sync (1)
-    and tcgen05 (2)."""
+    and tcgen05 fed by TMA (2)."""
     s, P = pair
     y = rand_c((P.N, R), 131 + R)
     ref = P.local_inverse(y)
