@@ -206,7 +206,8 @@ hzb_status hzb_tuned_config(const hzb_ctx *ctx, int R, int out[6]);
 /* GMRES execution controls (no effect on results beyond rounding of where a
  * converged right-hand side stops):
  *   check_every: Arnoldi steps issued between host reads of the residual estimates
- *                (0 = auto: 4 when N x R <= 1e6, else 1); a right-hand side that
+ *                (0 = auto: 4 when N x R <= 1e6 and N^2 x R < 4e9, else 1, since a
+ *                chunk's steps after convergence each cost one apply); a right-hand side that
  *                converges inside a chunk is frozen on the device, so later steps of
  *                the chunk change nothing for it;
  *   use_graphs:  capture each Arnoldi step j (operator apply, CGS2, Givens) once as a

@@ -448,7 +448,11 @@ hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is
         // Steps run in chunks of `every` without host synchronisation: a right-hand
         // side that converges inside a chunk is frozen by givens_kernel (its next basis
         // vectors are zero and its jdone stays), so the extra steps change nothing.
-        const int every = c->check_every > 0 ? c->check_every : ((long long)NR <= 1000000 ? 4 : 1);
+        // automatic: chunks of 4 where an apply is cheap next to a host round trip; every
+        // step where an apply costs milliseconds (a converged chunk's extra steps would
+        // each cost a full apply)
+        const double pair_work = (double)c->N * (double)c->N * R;
+        const int every = c->check_every > 0 ? c->check_every : ((long long)NR <= 1000000 && pair_work < 4e9 ? 4 : 1);
         int j = 0;
         while (j < m && total < maxit) {
             const int q = std::min(every, std::min(m - j, maxit - total));
