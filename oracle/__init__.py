@@ -22,6 +22,8 @@ scatterers"):
   solvers.py   GMRES and a dense direct solve (Sec. 4)
   fields.py    plane waves, point sources, fields, far field, Mie series, sphere
                eigenvalues
+  compress.py  the accelerated scheme (Sec. 5): proxy-sphere interpolative
+               decomposition per shape, reduced system Eq. (ip6), density recovery
   liboracle.c  the plain-C double-precision loops behind the above
 
 Every function is pinned by `tests/test_oracle_*.py` against closed forms,

@@ -1,0 +1,112 @@
+"""Pins of the oracle's accelerated scheme (Sec. 5, Eqs. (ip0)-(ip6)) against what
+the mathematics fixes, independently of the proxy construction where it matters:
+
+  * the ID of an exactly low-rank matrix recovers its rank and reproduces it;
+  * with eps = 0 on a full-rank proxy matrix every node is a skeleton node, and the
+    reduced system's solution is the uncompressed one (the scheme reduces to Eq.
+    (precond));
+  * Eq. (ip0): each off-diagonal block of the dense Nystrom matrix (brute force) is
+    reproduced by U_p A_pq(I_p, I_q) V_q^* to about eps;
+  * the compressed solve matches the uncompressed dense solve to about eps, and the
+    identity V_p^* sig_p = sig~_p holds for the recovered density;
+  * Green's identity: interior point sources' boundary data gives back their field
+    outside, through the compressed solve.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Problem, dense_solve, fields
+from oracle.compress import Compressed, interpolative_decomposition
+
+
+@pytest.fixture(scope="module")
+def wl():
+    # 3 spheroids (0.5, 0.5, 1) of 6 x 8 x 21 = 1,008 nodes, spacing 4, k = 2
+    return W.separated_spheroids(spacing=4.0, n_panels=6, gl_order=8, n_modes=21)
+
+
+@pytest.fixture(scope="module")
+def P(wl):
+    return Problem(wl)
+
+
+@pytest.fixture(scope="module")
+def dense(P):
+    return P.dense_matrix()
+
+
+def test_id_of_exactly_low_rank_matrix():
+    rng = np.random.default_rng(11)
+    r = 12
+    A = rng.standard_normal((60, r)) + 1j * rng.standard_normal((60, r))
+    B = rng.standard_normal((r, 80)) + 1j * rng.standard_normal((r, 80))
+    Z = A @ B
+    idd = interpolative_decomposition(Z, 1e-12)
+    assert idd.rank == r
+    assert np.allclose(idd.T[:, idd.J], np.eye(r), atol=0)
+    assert np.linalg.norm(Z - Z[:, idd.J] @ idd.T) < 1e-12 * np.linalg.norm(Z)
+    # full column rank with eps = 0: every column is kept and T is the identity
+    Zf = rng.standard_normal((50, 30)) + 1j * rng.standard_normal((50, 30))
+    f = interpolative_decomposition(Zf, 0.0)
+    assert f.rank == 30 and sorted(f.J) == list(range(30))
+    assert np.array_equal(f.T[:, f.J], np.eye(30)) and np.count_nonzero(f.T) == 30
+
+
+def test_full_skeleton_reduces_to_uncompressed(P, dense):
+    C = Compressed(P, 0.0)
+    for shp, idd in C.ids.items():
+        assert idd.rank == shp.n_nodes
+    v = fields.plane_wave(P.nodes.x, P.wl.directions, P.k)[:, 0]
+    sig, res = C.solve(v, 1e-13)
+    assert res.converged
+    ref = dense_solve(dense, v)
+    assert np.linalg.norm(sig - ref) < 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-10])
+def test_off_diagonal_blocks_factor_to_eps(P, dense, eps):
+    C = Compressed(P, eps)
+    sl = P.body_slices()
+    shp = P.wl.bodies[0].shape
+    assert C.ids[shp].rank < 0.75 * shp.n_nodes
+    T = C.ids[shp].T
+    J = C.ids[shp].J
+    for p in range(len(sl)):
+        for q in range(len(sl)):
+            if p == q:
+                continue
+            A = dense[sl[p], sl[q]]
+            approx = T.T @ A[np.ix_(J, J)] @ T
+            assert np.linalg.norm(A - approx) < eps * np.linalg.norm(A)
+
+
+def test_compressed_solve_matches_uncompressed(P, dense):
+    eps = 1e-10
+    C = Compressed(P, eps)
+    v = fields.plane_wave(P.nodes.x, P.wl.directions, P.k)[:, 0]
+    sig, res = C.solve(v, 1e-13)
+    assert res.converged
+    ref = dense_solve(dense, v)
+    assert np.linalg.norm(sig - ref) < 10 * eps * np.linalg.norm(ref)
+    # V_p^* sig_p = sig~_p for the recovered density
+    for q, b, st, sf in C.body_blocks():
+        t = C.ids[b.shape].T @ sig[sf]
+        assert np.linalg.norm(t - res.x[st]) < 1e-11 * np.linalg.norm(res.x[st])
+    # far field from the recovered density
+    xh = W.uniform_directions(12, 7)
+    uf = fields.far_field(P.nodes, sig, P.k, P.eta, xh)
+    ur = fields.far_field(P.nodes, ref, P.k, P.eta, xh)
+    assert np.abs(uf - ur).max() < 10 * eps * np.abs(ur).max()
+
+
+def test_green_identity_through_compressed_solve(wl, P):
+    C = Compressed(P, 1e-10)
+    src = W.point_sources(wl, 5)
+    tg = W.exterior_targets(wl, 10, 6)
+    v = -fields.point_source_field(P.nodes.x, src, wl.k)
+    sig, res = C.solve(v, 1e-13)
+    assert res.converged
+    u = fields.field(P.nodes, sig, wl.k, wl.eta, tg)
+    ue = fields.point_source_field(tg, src, wl.k)
+    assert np.abs(u - ue).max() < 1e-8 * np.abs(ue).max()

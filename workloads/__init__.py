@@ -209,6 +209,22 @@ def tiny_two_spheres(n_panels=4, gl_order=6, n_modes=9, k=1.0, sep=1.6) -> Workl
     return two_spheres(n_panels, gl_order, n_modes, k=k, sep=sep, name="two_spheres_tiny")
 
 
+def separated_spheroids(n_bodies=3, spacing=3.5, a=0.5, c=1.0, n_panels=4, gl_order=6, n_modes=11,
+                        k=2.0, seed=DEFAULT_SEED, name="separated_spheroids") -> Workload:
+    """n_bodies spheroids (a, a, c) with seeded random symmetry axes, centres on a line
+    along x with the given spacing plus a seeded transverse jitter of 0.3 spacing; for
+    the accelerated scheme (Sec. 5), whose compression needs bodies that are not tightly
+    packed.  Plane wave along +z."""
+    rng = np.random.default_rng(seed)
+    shape = ShapeSpec(SPHEROID, (a, c), n_panels, gl_order, n_modes)
+    bodies = []
+    for q in range(n_bodies):
+        cen = np.array([spacing * q, 0.0, 0.0])
+        cen[1:] += 0.3 * spacing * (rng.random(2) - 0.5)
+        bodies.append(Body(shape, cen, rotation_taking_z_to(rng.standard_normal(3))))
+    return Workload(name, bodies, k, k, np.array([[0.0, 0.0, 1.0]]), gmres_tol=1e-10)
+
+
 def spheroids8(seed=DEFAULT_SEED, n_panels=20, gl_order=16, n_modes=101, k=4.0,
                n_rhs=1) -> Workload:
     """Eight prolate spheroids, semi-axes (1,1,2), symmetry axes uniform on the sphere
