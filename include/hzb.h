@@ -307,6 +307,65 @@ hzb_status hzb_far_field(hzb_ctx *ctx, int n, const double *xhat, double *out);
 hzb_status hzb_eval_field(hzb_ctx *ctx, int n, const double *x, double *out);
 
 /* ------------------------------------------------------------------------------
+ * Accelerated scheme (Sec. 5, Eqs. (ip0)-(ip6)).  For bodies that are not tightly
+ * packed, each shape gets an interpolative decomposition (ID): a skeleton J of k of
+ * its n nodes and T (k x n, T(:, J) = I) with V_p^* = T and U_p = T^T, such that every
+ * off-diagonal block factors as A_pq ~ U_p A_pq(J_p, J_q) V_q^* (Eq. (ip0)).  GMRES
+ * then runs on the reduced system (Eq. (ip6))
+ *       sig~ + S B~ sig~ = -v~,  S_p = T A_pp^{-1} T^T,  v~_p = T A_pp^{-1} v_p,
+ * whose inter-body sum B~ = B(J, J) is the direct sum over skeleton nodes only, and
+ * the density on all nodes follows from Eq. (ip1): sig = D^{-1} (-v - U B~ sig~), so
+ * hzb_get_density, hzb_far_field and hzb_eval_field work unchanged.  While the
+ * acceleration is on, hzb_solve_plane_waves and hzb_solve_data solve this way in the
+ * context's precision (FP64, or mixed: FP32 reduced applies with FP64 refinement);
+ * the result differs from the direct solve by about eps times the conditioning.
+ * ------------------------------------------------------------------------------ */
+
+/* Compute every shape's ID on the GPU and switch the acceleration on.  The ID is of
+ * the proxy matrix [K(z, y_j) w_j ; G(x_i, z) ; dG/dn_z(x_i, z)] (rows: points z of a
+ * sphere of radius rho about the body centre, n_theta Gauss-Legendre rings in
+ * cos(theta) times the body's N_F azimuths; each block scaled to unit Frobenius norm);
+ * its rank k counts the pivots of a column-pivoted QR with |R_jj| > eps |R_11|.
+ *   eps:          tolerance in [0, 1); 0 keeps every column of nonzero pivot
+ *   n_theta:      proxy rings, 0 = max(16, ceil(1.2 N_G)), at most 4096
+ *   proxy_radius: rho for every shape, or 0 = per shape midway between its largest
+ *                 node radius and the nearest other body's bounding sphere
+ * Needs hzb_build_scattering_matrices.  HZB_EINVAL if a proxy sphere cannot enclose
+ * its body while excluding every other body (bodies too close).  Device memory: about
+ * 3 k n complex doubles per shape while it is compressed, then k n + 1.5 k^2. */
+hzb_status hzb_compress(hzb_ctx *ctx, double eps, int n_theta, double proxy_radius);
+
+/* Install a skeleton for the shape of `body` (shared by every body of that shape):
+ * J holds k distinct node indices of the shape (0..n-1, any order), T the k x n
+ * complex matrix row-major with row s belonging to J[s].  Once every shape has one,
+ * the reduced system is built and the acceleration switched on. */
+hzb_status hzb_set_skeleton(hzb_ctx *ctx, int body, int k, const int *J, const double *T);
+
+/* The skeleton of the shape of `body`: *k (0: none); J (k ints, ascending) and T
+ * (k x n complex, row-major, rows in the order of J) are filled when not NULL. */
+hzb_status hzb_get_skeleton(hzb_ctx *ctx, int body, int *k, int *J, double *T);
+
+/* on = 1: solves go through the reduced system (HZB_ESTATE without skeletons);
+ * on = 0: the direct solve of Eq. (precond). */
+hzb_status hzb_set_acceleration(hzb_ctx *ctx, int on);
+
+/* *n = unknowns of the reduced system (sum of k over the bodies), 0 without one. */
+hzb_status hzb_reduced_size(const hzb_ctx *ctx, long long *n);
+
+/* out = sig~ + S B~ sig~, the reduced operator of Eq. (ip6), on host arrays of
+ * (reduced size) x R complex in the reduced numbering (body by body, each body's
+ * skeleton in ascending order); precision: hzb_precision. */
+hzb_status hzb_apply_reduced(hzb_ctx *ctx, int R, const double *sig, double *out, int precision);
+
+/* Interpolative decomposition of a rows x cols complex matrix Z (host, column-major)
+ * on the GPU: column-pivoted QR stopped at |R_jj| <= eps |R_11|, T = [I, R11^{-1} R12]
+ * in the original column order.  Out: *k; J (cols ints; the first k are the skeleton
+ * columns in pivot order); T (room for min(rows, cols) x cols complex; k x cols
+ * row-major, row s for column J[s], T(:, J) = I). */
+hzb_status hzb_interp_decomp(hzb_ctx *ctx, int rows, int cols, const double *Z, double eps, int *k,
+                             int *J, double *T);
+
+/* ------------------------------------------------------------------------------
  * Learned warm start (no counterpart in the paper; it only seeds GMRES through the
  * x0 of hzb_solve_data, and the zero-guess solve remains the fallback).
  * A multilayer perceptron: n_in inputs -> depth hidden layers of `width` units with

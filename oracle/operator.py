@@ -118,16 +118,26 @@ class Problem:
     def dense_matrix(self) -> np.ndarray:
         """The full N x N Nystrom matrix A = D + B (Eq. (blocksystem))."""
         nd = self.nodes
-        d = nd.x[:, None, :] - nd.x[None, :, :]                  # x_i - x_j
-        R = np.sqrt((d * d).sum(-1))
-        np.fill_diagonal(R, 1.0)
-        phi = np.exp(1j * self.k * R) / (4.0 * np.pi * R)
-        n_dot_ymx = -(nd.n[None, :, :] * d).sum(-1)
-        K = phi * (1j * self.k - 1.0 / R) * n_dot_ymx / R - 1j * self.eta * phi
-        A = K * nd.w[None, :]
+        A = interaction_block(nd.x, nd.x, nd.n, nd.w, self.k, self.eta, same=True)
         for q, sl in enumerate(self.body_slices()):
             A[sl, sl] = self.dense_block_diagonal(q)
         return A
+
+
+def interaction_block(xt: np.ndarray, xs: np.ndarray, ns: np.ndarray, ws: np.ndarray, k: float, eta: float,
+                      same: bool = False) -> np.ndarray:
+    """K(x_i, y_j) w_j for targets xt and sources (xs, ns, ws): the entries of B
+    (Sec. 3.3, Eq. (nystromnaive)), K(x, y) = dphi/dn(y) - i eta phi.  same = True
+    when targets and sources are one node set: the diagonal is then evaluated at
+    distance 1 and the caller overwrites it."""
+    d = xt[:, None, :] - xs[None, :, :]                       # x_i - y_j
+    R = np.sqrt((d * d).sum(-1))
+    if same:
+        np.fill_diagonal(R, 1.0)
+    phi = np.exp(1j * k * R) / (4.0 * np.pi * R)
+    n_dot_ymx = -(ns[None, :, :] * d).sum(-1)
+    K = phi * (1j * k - 1.0 / R) * n_dot_ymx / R - 1j * eta * phi
+    return K * ws[None, :]
 
 
 def problem(wl: Workload) -> Problem:

@@ -135,6 +135,13 @@ def lib():
         "hzb_save_scattering": (i, [p, ctypes.c_char_p]),
         "hzb_add_body_curve": (i, [p, _D, i, i, i, _D, _D, ctypes.POINTER(i)]),
         "hzb_load_scattering": (i, [p, ctypes.c_char_p]),
+        "hzb_compress": (i, [p, d, i, d]),
+        "hzb_set_skeleton": (i, [p, i, i, p, p]),
+        "hzb_get_skeleton": (i, [p, i, ctypes.POINTER(i), p, p]),
+        "hzb_set_acceleration": (i, [p, i]),
+        "hzb_reduced_size": (i, [p, ctypes.POINTER(ctypes.c_longlong)]),
+        "hzb_apply_reduced": (i, [p, i, p, p, i]),
+        "hzb_interp_decomp": (i, [p, i, i, p, d, ctypes.POINTER(i), p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -178,6 +185,7 @@ class Solver:
         self._check(L.hzb_set_wave(h, float(k), float(eta)))
         self.k, self.eta = float(k), float(eta)
         self.bodies = 0
+        self._body_n = []                   # node count of each body
 
     # ------------------------------------------------------------ plumbing
     def _check(self, status: int, ctx="self"):
@@ -241,6 +249,7 @@ class Solver:
         self._check(lib().hzb_add_body(self._h, ctypes.byref(s), c.ctypes.data_as(_D), r.ctypes.data_as(_D),
                                        ctypes.byref(bid)))
         self.bodies += 1
+        self._body_n.append(int(n_panels) * int(gl_order) * int(n_modes))
         return bid.value
 
     @classmethod
@@ -262,6 +271,7 @@ class Solver:
                                              int(n_modes), c.ctypes.data_as(_D), r.ctypes.data_as(_D),
                                              ctypes.byref(bid)))
         self.bodies += 1
+        self._body_n.append((int(pts.shape[0]) - 1) * int(gl_order) * int(n_modes))
         return bid.value
 
     @property
@@ -385,6 +395,57 @@ class Solver:
             self._check(rc)
         self._R = R
         return self._stats(st, rc)
+
+    # ------------------------------------------------------------ accelerated scheme
+    def compress(self, eps: float, n_theta: int = 0, proxy_radius: float = 0.0):
+        """Skeletons of every shape by the GPU's interpolative decomposition (Sec. 5);
+        solves then run on the reduced system of Eq. (ip6)."""
+        self._check(lib().hzb_compress(self._h, float(eps), int(n_theta), float(proxy_radius)))
+
+    def set_skeleton(self, body: int, J, T):
+        J = np.ascontiguousarray(J, dtype=np.int32)
+        T = np.ascontiguousarray(T, dtype=np.complex128)
+        self._check(lib().hzb_set_skeleton(self._h, int(body), int(J.size), _ptr(J), _ptr(T)))
+
+    def get_skeleton(self, body: int):
+        """(J ascending, T with rows in J's order) of the body's shape, or None."""
+        k = ctypes.c_int()
+        self._check(lib().hzb_get_skeleton(self._h, int(body), ctypes.byref(k), None, None))
+        if k.value == 0:
+            return None
+        n = self._body_n[body]
+        J = np.zeros(k.value, dtype=np.int32)
+        T = np.zeros((k.value, n), dtype=np.complex128)
+        self._check(lib().hzb_get_skeleton(self._h, int(body), ctypes.byref(k), _ptr(J), _ptr(T)))
+        return J, T
+
+    def set_acceleration(self, on: bool):
+        self._check(lib().hzb_set_acceleration(self._h, int(bool(on))))
+
+    @property
+    def reduced_size(self) -> int:
+        n = ctypes.c_longlong()
+        self._check(lib().hzb_reduced_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def apply_reduced(self, sig, precision: int = HZB_PREC_FP64):
+        a = np.ascontiguousarray(sig, dtype=np.complex128)
+        R = 1 if a.ndim == 1 else int(a.shape[1])
+        out = np.zeros_like(a)
+        self._check(lib().hzb_apply_reduced(self._h, R, _ptr(a), _ptr(out), int(precision)))
+        return out
+
+    def interp_decomp(self, Z, eps: float):
+        """GPU interpolative decomposition of Z (rows x cols): (J in pivot order, T)."""
+        Z = np.asarray(Z, dtype=np.complex128)
+        rows, cols = Z.shape
+        Zc = np.asfortranarray(Z)
+        J = np.zeros(cols, dtype=np.int32)
+        T = np.zeros((min(rows, cols), cols), dtype=np.complex128)
+        k = ctypes.c_int()
+        self._check(lib().hzb_interp_decomp(self._h, rows, cols, Zc.ctypes.data_as(ctypes.c_void_p), float(eps),
+                                            ctypes.byref(k), _ptr(J), _ptr(T)))
+        return J[:k.value].copy(), T[:k.value].copy()
 
     def get_density(self, out=None):
         R = getattr(self, "_R", 1)

@@ -112,6 +112,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     cudaSetDevice(c->opt.device);
     // the caller's stream may already be gone: wait for the whole device instead
     cudaDeviceSynchronize();
+    release_compression(c);
     for (ShapeDev *s : c->shapes) {
         s->ring.release(); s->body_offs.release(); s->A64.release(); s->S64.release(); s->S32.release();
         s->Aimg.release();
@@ -418,6 +419,7 @@ hzb_status hzb_solve_plane_waves(hzb_ctx *c, int R, const double *dirs, hzb_stat
         return HZB_ECUDA;
     hzb_status st = plane_waves(c, R, c->io_small.ptr, c->io_in.ptr);
     if (st) return st;
+    if (c->accel && c->rctx) return solve_reduced(c, R, c->io_in.ptr, nullptr, stats);
     return solve_driver(c, R, c->io_in.ptr, nullptr, stats);
 }
 
@@ -432,6 +434,7 @@ hzb_status hzb_solve_data(hzb_ctx *c, int R, const double *v, const double *x0, 
     hzb_status st;
     if ((st = stage_in(c, c->io_in, v, n, on_device, &dv))) return st;
     if (x0 && (st = stage_in(c, c->io_out, x0, n, on_device, &dx0))) return st;
+    if (c->accel && c->rctx) return solve_reduced(c, R, dv, dx0, stats);
     return solve_driver(c, R, dv, dx0, stats);
 }
 

@@ -81,6 +81,13 @@ struct ShapeDev {
     DevBuf<float> Aimg;                   // embedded, TF32-split S_p for the TMA modal GEMM (modal_tma.cu)
     alignas(64) unsigned char tmA[128];   // its TMA tensor map (CUtensorMap)
     bool tmA_ready = false;
+    // accelerated scheme (compress.cu, Sec. 5): the shape's skeleton and reduced blocks
+    int skel_k = 0;                       // skeleton size k (0: none)
+    std::vector<int> skel_J;              // skeleton nodes, shape-local, ascending
+    DevBuf<double2> T64;                  // k x n row-major: V_p^* = T, U_p = T^T
+    DevBuf<double2> St64;                 // k x k row-major: S_p = T A_pp^{-1} T^T
+    DevBuf<float2> St32;                  // its FP32 copy
+    DevBuf<long long> red_offs;           // first reduced-system node of each body of the shape
 };
 
 struct BodyRec {
@@ -183,6 +190,21 @@ struct hzb_ctx {
     unsigned char gkey[256];
     bool gkey_valid = false;
     bool capturing = false;
+    // accelerated scheme (compress.cu): the reduced system of Eq. (ip6) as a context of its
+    // own over the skeleton nodes; its local operator is the dense S_p of each body
+    hzb_ctx *rctx = nullptr;
+    bool reduced = false;                      // this context is a reduced system
+    bool accel = false;                        // solves go through the reduced system
+    double t_compress_ms = 0.0;
+    struct RShape {
+        int k, ms;
+        const double2 *S64;
+        const float2 *S32;
+        const long long *offs;                 // first reduced node of each body of the shape
+    };
+    std::vector<RShape> rshapes;               // reduced context: one per shape
+    hzb::DevBuf<double2> rb, rx;               // reduced right-hand side and guess (parent)
+    hzb::DevBuf<long long> zero_off;           // {0}: one body at offset 0
     // device timing of the inter-body kernels during a solve: event pairs
     std::vector<cudaEvent_t> evpool;
     std::vector<int> evkind;                   // 0: FP64, 1: FP32, per recorded pair
@@ -235,8 +257,19 @@ hzb_status apply_op(hzb_ctx *c, int R, const double2 *x, double2 *z, int precisi
 hzb_status gmres_solve(hzb_ctx *c, int R, const double2 *b, double2 *x, int x_is_zero,
                        int precision, double tol, int maxit, int restart,
                        int *iters, double *relres, int *converged);
-hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *st);
+// b_given: the preconditioned right-hand side itself (then v is not read)
+hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *st,
+                        const double2 *b_given = nullptr);
 void release_graphs(hzb_ctx *c);
+
+// modal.cu: Y = A_pp^{-1} X for one body of the shape, X and Y n x R (node-major)
+hzb_status shape_inverse64(hzb_ctx *c, ShapeDev &sd, int R, const double2 *X, double2 *Y);
+
+// compress.cu: the reduced system's local operator tau = alpha sigma + beta S y
+hzb_status reduced_local(hzb_ctx *c, int R, const double2 *y, const double2 *sigma, double alpha,
+                         double beta, double2 *tau, bool fp32);
+hzb_status solve_reduced(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *st);
+void release_compression(hzb_ctx *c);
 
 // fields.cu
 hzb_status plane_waves(hzb_ctx *c, int R, const double *dirs_dev, double2 *v);

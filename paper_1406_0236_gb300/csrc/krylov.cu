@@ -532,7 +532,8 @@ static hzb_status true_residual(hzb_ctx *c, int R, const double2 *b, const doubl
     return residual_with(c, R, b, x, r_out, rel, c->opt.residual);
 }
 
-hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *stats)
+hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *stats,
+                        const double2 *b_given)
 {
     const size_t NR = (size_t)c->N * R;
     hzb_status st;
@@ -547,8 +548,13 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
     c->evkind.clear();
     c->prof_on = true;
     cudaEventRecord(c->ev0, c->stream);
-    // b = -D^{-1} v
-    if ((st = local_inverse64(c, R, v, nullptr, 0.0, -1.0, bbuf.ptr))) { cleanup(); return st; }
+    // b = -D^{-1} v, unless given
+    if (b_given) {
+        if ((st = vec_copy(c, bbuf.ptr, b_given, NR))) { cleanup(); return st; }
+    } else if ((st = local_inverse64(c, R, v, nullptr, 0.0, -1.0, bbuf.ptr))) {
+        cleanup();
+        return st;
+    }
     double2 *x = c->sol.ptr;
     int it = 0, conv = 0, outer = 0;
     double rr = 0.0;

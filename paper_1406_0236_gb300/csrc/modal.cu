@@ -203,6 +203,7 @@ static hzb_status local_inverse_t(hzb_ctx *c, int R, const double2 *y, const dou
                                   double beta, double2 *tau)
 {
     typedef typename C2<T>::t ct;
+    if (c->reduced) return reduced_local(c, R, y, sigma, alpha, beta, tau, sizeof(T) == 4);
     for (ShapeDev *sp : c->shapes) {
         ShapeDev &sd = *sp;
         const int NG = sd.geom.NG, NF = sd.geom.NF, M = sd.geom.M;
@@ -289,6 +290,30 @@ hzb_status local_inverse64_scratch(hzb_ctx *c, int R, const double2 *y, const do
         if (check_cuda(c, cudaGetLastError(), "modal apply")) return HZB_ECUDA;
     }
     return HZB_OK;
+}
+
+// Y = A_pp^{-1} X for a single body of the shape placed at offset 0 (X, Y: n x R,
+// node-major), FP64: the same three kernels as local_inverse64.
+hzb_status shape_inverse64(hzb_ctx *c, ShapeDev &sd, int R, const double2 *X, double2 *Y)
+{
+    const int NG = sd.geom.NG, NF = sd.geom.NF, M = sd.geom.M;
+    const int ncols = 2 * R;
+    const size_t panel = (size_t)(M + 1) * NG * ncols;
+    if (check_cuda(c, c->yhat64.ensure(panel), "alloc") || check_cuda(c, c->that64.ensure(panel), "alloc") ||
+        check_cuda(c, c->zero_off.ensure(1), "alloc"))
+        return HZB_ENOMEM;
+    if (check_cuda(c, cudaMemsetAsync(c->zero_off.ptr, 0, sizeof(long long), c->stream), "memset")) return HZB_ECUDA;
+    size_t smem = (size_t)NF * (R + 1) * sizeof(double2);
+    if (smem > 200 * 1024) return fail(c, HZB_EINVAL, "n_modes * R too large for the modal apply");
+    dft_smem_limit<double>(smem);
+    dft_forward_kernel<double><<<dim3(NG, 1), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, c->zero_off.ptr, X,
+                                                                             c->yhat64.ptr);
+    modal_gemm_kernel<double><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(
+        NG, ncols, sd.S64.ptr, c->yhat64.ptr, c->that64.ptr);
+    dft_inverse_kernel<double><<<dim3(NG, 1), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, c->zero_off.ptr,
+                                                                             c->that64.ptr, nullptr, 0.0, 1.0, Y);
+    c->launches += 3;
+    return check_cuda(c, cudaGetLastError(), "shape inverse");
 }
 
 // Largest per-shape panel (M+1) x N_G x (2 m_s R) of the context, in complex values.

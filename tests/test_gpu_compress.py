@@ -1,0 +1,214 @@
+"""Parity of the accelerated scheme (Sec. 5, Eqs. (ip0)-(ip6)) through the C ABI.
+
+  * the GPU interpolative decomposition against the oracle's (column-pivoted QR) on
+    matrices whose pivot order is unique: same skeleton, same T;
+  * the reduced operator sig~ + S B~ sig~ with one given skeleton on both sides,
+    element by element, in FP64, FP32 and double-float;
+  * the GPU's own skeletons: the factorisation Eq. (ip0) of every off-diagonal block of
+    the oracle's dense matrix to about eps, rank close to the oracle's;
+  * compressed solves (FP64 and mixed) against the oracle's dense solve, far field
+    included; eps = 0 keeps every node and reproduces the direct solve;
+  * at the eight-spheroid size (258,560 nodes): the factorisation on sampled rows of
+    real off-diagonal blocks, and Green's identity through the compressed solve.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._common import gpu_solver, rand_c, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _sep_wl():
+    # 3 spheroids (0.5, 0.5, 1) of 6 x 8 x 21 = 1,008 nodes, spacing 4, k = 2
+    return W.separated_spheroids(spacing=4.0, n_panels=6, gl_order=8, n_modes=21)
+
+
+@pytest.fixture(scope="module")
+def sep():
+    require_gpu()
+    from oracle import Problem
+    wl = _sep_wl()
+    P = Problem(wl)
+    return wl, P, P.dense_matrix()
+
+
+def _decaying(rows, cols, seed, decay=0.25):
+    g = np.random.default_rng(seed)
+    U = g.standard_normal((rows, cols)) + 1j * g.standard_normal((rows, cols))
+    V = g.standard_normal((cols, cols)) + 1j * g.standard_normal((cols, cols))
+    s = 10.0 ** (-decay * np.arange(cols))
+    return (U * s) @ V
+
+
+@pytest.mark.parametrize("rows,cols,eps,decay", [(80, 60, 1e-8, 0.25), (300, 200, 1e-10, 0.25),
+                                                 (50, 90, 0.0, 0.02), (700, 40, 1e-6, 0.25)])
+def test_interp_decomp_matches_oracle(sep, rows, cols, eps, decay):
+    from oracle.compress import interpolative_decomposition
+    wl, P, _ = sep
+    s = gpu_solver(wl)
+    Z = _decaying(rows, cols, rows + cols, decay)
+    ref = interpolative_decomposition(Z, eps)
+    J, T = s.interp_decomp(Z, eps)
+    assert J.size == ref.rank
+    assert np.array_equal(J, ref.J)
+    assert np.array_equal(T[:, J], np.eye(J.size))
+    # T = R11^{-1} R12 is fixed to about the unit roundoff times the condition of R11
+    kappa = ref.diag[0] / ref.diag[ref.rank - 1]
+    assert np.abs(T - ref.T).max() < 1e-14 * kappa * max(1.0, np.abs(ref.T).max())
+    assert np.linalg.norm(Z - Z[:, J] @ T) <= 10 * max(eps, 1e-14) * np.linalg.norm(Z) * np.sqrt(cols)
+
+
+def test_interp_decomp_exact_rank(sep):
+    wl, P, _ = sep
+    s = gpu_solver(wl)
+    g = np.random.default_rng(4)
+    Z = (g.standard_normal((90, 9)) + 1j * g.standard_normal((90, 9))) @ \
+        (g.standard_normal((9, 70)) + 1j * g.standard_normal((9, 70)))
+    J, T = s.interp_decomp(Z, 1e-12)
+    assert J.size == 9
+    assert np.linalg.norm(Z - Z[:, J] @ T) < 1e-12 * np.linalg.norm(Z)
+
+
+def _given_skeleton(n, k, seed):
+    g = np.random.default_rng(seed)
+    J = np.sort(g.choice(n, size=k, replace=False))
+    T = 0.3 * (g.standard_normal((k, n)) + 1j * g.standard_normal((k, n)))
+    T[:, J] = np.eye(k)
+    return J, T
+
+
+@pytest.mark.parametrize("R", [1, 3, 9])
+def test_reduced_apply_with_given_skeleton(sep, R):
+    from oracle.compress import Compressed
+    wl, P, _ = sep
+    shp = wl.bodies[0].shape
+    J, T = _given_skeleton(shp.n_nodes, 333, 17)
+    C = Compressed(P, 0.0, skeletons={shp: (J, T)})
+    s = gpu_solver(wl)
+    s.set_skeleton(0, J, T)
+    assert s.reduced_size == C.Nk
+    Jg, Tg = s.get_skeleton(2)
+    assert np.array_equal(Jg, J) and np.array_equal(Tg, T)
+    sig = rand_c((C.Nk, R), 31 + R)
+    ref = C.apply(sig)
+    got64 = s.apply_reduced(sig, precision=0)
+    assert np.abs(got64 - ref).max() < 1e-12 * np.abs(ref).max()
+    gotdf = s.apply_reduced(sig, precision=2)
+    assert np.abs(gotdf - ref).max() < 1e-11 * np.abs(ref).max()
+    got32 = s.apply_reduced(sig, precision=1)
+    assert rel_l2(got32, ref) < 5e-6
+
+
+def test_gpu_skeleton_factorises_blocks(sep):
+    from oracle.compress import Compressed, default_proxy_radius
+    wl, P, D = sep
+    shp = wl.bodies[0].shape
+    eps = 1e-10
+    rho = default_proxy_radius(wl, shp)
+    C = Compressed(P, eps)
+    s = gpu_solver(wl)
+    s.compress(eps, 0, rho)
+    J, T = s.get_skeleton(0)
+    assert abs(J.size - C.ids[shp].rank) <= max(3, 0.02 * J.size)
+    assert np.array_equal(T[:, J], np.eye(J.size))
+    sl = P.body_slices()
+    for p in range(3):
+        for q in range(3):
+            if p != q:
+                A = D[sl[p], sl[q]]
+                assert np.linalg.norm(A - T.T @ A[np.ix_(J, J)] @ T) < eps * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-13, 1e-9), (1, 1e-11, 1e-8)])
+def test_compressed_solve_matches_dense(sep, precision, tol, bound):
+    from oracle import dense_solve, fields
+    wl, P, D = sep
+    s = gpu_solver(wl, precision=precision, tol=tol)
+    s.compress(1e-10)
+    st = s.solve_plane_waves(wl.directions)
+    assert st.converged
+    v = fields.plane_wave(P.nodes.x, wl.directions, P.k)[:, 0]
+    ref = dense_solve(D, v)
+    got = s.get_density()[:, 0]
+    assert rel_l2(got, ref) < bound
+    xh = W.uniform_directions(12, 7)
+    uf = s.far_field(xh)[:, 0]
+    ur = fields.far_field(P.nodes, ref, P.k, P.eta, xh)
+    assert np.abs(uf - ur).max() < bound * np.abs(ur).max()
+    # the direct solve is back once the acceleration is off
+    s.set_acceleration(False)
+    s.solve_plane_waves(wl.directions)
+    assert rel_l2(s.get_density()[:, 0], ref) < 1e-9
+
+
+def test_eps_zero_keeps_every_node(sep):
+    wl, P, D = sep
+    s = gpu_solver(wl, tol=1e-13)
+    s.solve_plane_waves(wl.directions)
+    direct = s.get_density()[:, 0].copy()
+    s.compress(0.0)
+    assert s.reduced_size == P.N
+    st = s.solve_plane_waves(wl.directions)
+    assert st.converged
+    assert rel_l2(s.get_density()[:, 0], direct) < 1e-11
+
+
+def test_compress_refuses_touching_bodies():
+    require_gpu()
+    from paper_1406_0236_gb300 import HzbError
+    s = gpu_solver(W.two_spheres(n_panels=3, gl_order=6, n_modes=9, sep=1.005))
+    with pytest.raises(HzbError) as e:
+        s.compress(1e-8)
+    assert e.value.status == -1
+    with pytest.raises(HzbError) as e:
+        s.set_acceleration(True)
+    assert e.value.status == -7
+
+
+# ---------------------------------------------------------------- eight spheroids, full size
+
+@pytest.fixture(scope="module")
+def big():
+    require_gpu()
+    wl = W.spheroids8()
+    s = gpu_solver(wl, precision=1, tol=1e-10)
+    s.compress(1e-10)
+    return wl, s
+
+
+def test_spheroids8_factorisation_on_sampled_entries(big):
+    """Eq. (ip0) on sampled rows and columns of real off-diagonal blocks: the oracle
+    evaluates A_pq(I, C) and A_pq(J_p, J_q) entry by entry."""
+    from oracle import Problem
+    from oracle.operator import interaction_block
+    wl, s = big
+    P = Problem(wl)
+    nd, sl = P.nodes, P.body_slices()
+    J, T = s.get_skeleton(0)
+    assert J.size < 0.25 * wl.bodies[0].shape.n_nodes
+    g = np.random.default_rng(12)
+    for p, q in ((0, 1), (3, 4), (6, 1)):
+        xp, xq = nd.x[sl[p]], nd.x[sl[q]]
+        nq, wq = nd.n[sl[q]], nd.w[sl[q]]
+        I = np.sort(g.choice(xp.shape[0], 48, replace=False))
+        Cs = np.sort(g.choice(xq.shape[0], 400, replace=False))
+        A = interaction_block(xp[I], xq[Cs], nq[Cs], wq[Cs], wl.k, wl.eta)
+        Ajj = interaction_block(xp[J], xq[J], nq[J], wq[J], wl.k, wl.eta)
+        approx = T[:, I].T @ Ajj @ T[:, Cs]
+        assert np.linalg.norm(A - approx) < 1e-9 * np.linalg.norm(A), (p, q)
+
+
+def test_spheroids8_green_identity_through_compressed_solve(big):
+    from oracle import fields
+    wl, s = big
+    x, _, _ = s.get_nodes()
+    src = W.point_sources(wl, 5)
+    tg = W.exterior_targets(wl, 10, 6)
+    v = -fields.point_source_field(x, src, wl.k)
+    st = s.solve_data(np.ascontiguousarray(v[:, None]))
+    assert st.converged
+    u = s.eval_field(tg)[:, 0]
+    ue = fields.point_source_field(tg, src, wl.k)
+    assert np.abs(u - ue).max() < 1e-7 * np.abs(ue).max()
