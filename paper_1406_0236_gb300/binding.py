@@ -419,6 +419,11 @@ class Solver:
         self._check(lib().hzb_get_skeleton(self._h, int(body), ctypes.byref(k), _ptr(J), _ptr(T)))
         return J, T
 
+    def get_skeleton_size(self, body: int) -> int:
+        k = ctypes.c_int()
+        self._check(lib().hzb_get_skeleton(self._h, int(body), ctypes.byref(k), None, None))
+        return k.value
+
     def set_acceleration(self, on: bool):
         self._check(lib().hzb_set_acceleration(self._h, int(bool(on))))
 

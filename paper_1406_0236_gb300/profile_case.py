@@ -1,13 +1,16 @@
 """Run one operator of the library on a named workload, for profilers and timing.
 
     python -m paper_1406_0236_gb300.profile_case --workload spheroids8_258560 \
-        --op interbody32 --repeat 2 [--rhs 1] [--autotune] [--engine -1] [--modal-engine -1]
+        --op interbody32 --repeat 2 [--rhs 1] [--autotune] [--engine -1] [--modal-engine -1] \
+        [--accel-eps 1e-8]
 
 ops: interbody32, interbody64, interbody_df (B sigma), local_inverse64, local_inverse32 (D^{-1} y),
-apply64, apply32, solve_mixed, solve_fp64.  Prints the mean time per call measured
+apply64, apply32, solve_mixed, solve_fp64, compress.  Prints the mean time per call measured
 with CUDA events.  Inputs are seeded random densities (ops) or the workload's plane
 waves (solves).  --engine picks the FP32 inter-body engine and --modal-engine the FP32
 modal GEMM engine (see Solver.set_interbody_engine / set_modal_engine; -1 automatic).
+--accel-eps > 0 computes the skeletons of the accelerated scheme (Sec. 5) first, so the
+solves run on the reduced system; compress times the skeleton computation itself.
 """
 from __future__ import annotations
 
@@ -30,6 +33,7 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--engine", type=int, default=-1)
     ap.add_argument("--modal-engine", type=int, default=-1)
+    ap.add_argument("--accel-eps", type=float, default=0.0)
     args = ap.parse_args()
 
     import numpy as np
@@ -49,6 +53,8 @@ def main():
         s.build_scattering_matrices()
     if args.autotune:
         s.autotune(args.rhs, 1 if prec == 1 else 2)
+    if args.accel_eps > 0 and args.op != "compress":
+        s.compress(args.accel_eps)
     N = s.N
     g = torch.Generator(device="cuda").manual_seed(7)
     x = torch.randn((N, args.rhs), dtype=torch.complex128, device="cuda", generator=g)
@@ -62,6 +68,8 @@ def main():
             s.local_inverse(x, precision=prec)
         elif args.op.startswith("apply"):
             s.apply(x, precision=prec)
+        elif args.op == "compress":
+            s.compress(args.accel_eps)
         else:
             s.solve_plane_waves(dirs)
 
