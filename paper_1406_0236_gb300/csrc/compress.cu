@@ -15,7 +15,7 @@
 //     block-circulant: M = (1/N_F) F^* diag(M^_p) F with M^_p = M^_{-p};
 //     proxy_modes_kernel forms M^_p for p = 0..M.
 //  2. Column-pivoted QR of every M^_p, stopped once all trailing columns are below
-//     0.1 eps |M|_col / sqrt(N_G): R_p with |M^_p u| ~ |R_p P_p^T u|.  The matrix Z with
+//     0.3 eps |M|_col: R_p with |M^_p u| ~ |R_p P_p^T u|.  The matrix Z with
 //     rows (p, s),  Z[(p,s), (i,l)] = R_p[s, i] e^{-2 pi i p l / N_F} / sqrt(N_F),  has
 //     |Z x| ~ |M x| for all x (Parseval), so a column ID of Z is a column ID of M with
 //     about as many rows as the rank instead of 3 n_theta N_F.
@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "hzb_internal.h"
@@ -170,7 +171,8 @@ __global__ void cpqr_init_kernel(int m, int n, const double2 *__restrict__ A, si
 }
 
 // Per-mode stopping thresholds: |M|_col^2 = max_i (1/N_F) (n_0(i) + 2 sum_{p>=1} n_p(i)),
-// thr2[p] = (0.1 eps |M|_col / sqrt(N_G))^2 for every mode (one block).
+// thr2[p] = (0.3 eps |M|_col)^2 for every mode (one block): the rows dropped from each
+// mode change |Z x| by about the largest trailing column norm, below the ID tolerance.
 __global__ void mode_threshold_kernel(int NG, int modes, int NF, double eps, const double *__restrict__ nrm2,
                                       double *__restrict__ thr2, int *__restrict__ rank)
 {
@@ -188,7 +190,7 @@ __global__ void mode_threshold_kernel(int NG, int modes, int NF, double eps, con
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = fmax(t, red[q]);
-        const double th = 0.1 * eps * sqrt(t) / sqrt((double)NG);
+        const double th = 0.3 * eps * sqrt(t);
         for (int p = 0; p < modes; ++p) {
             thr2[p] = th * th;
             rank[p] = -1;
@@ -728,6 +730,22 @@ __global__ void permute_rows_kernel(int k, int n, const int *__restrict__ src_ro
     }
 }
 
+// Ut = T^T (n x k row-major) from T (k x n row-major)
+__global__ void transpose_kernel(int k, int n, const double2 *__restrict__ T, double2 *__restrict__ Ut)
+{
+    __shared__ double2 tile[32][33];
+    const int s0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        const int s = s0 + q, i = i0 + threadIdx.x;
+        if (s < k && i < n) tile[q][threadIdx.x] = T[(size_t)s * n + i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        const int i = i0 + q, s = s0 + threadIdx.x;
+        if (s < k && i < n) Ut[(size_t)i * k + s] = tile[threadIdx.x][q];
+    }
+}
+
 // Install J (any order, distinct) and T (device, k x n rows in J's order) as the shape's
 // skeleton with J ascending, and form its reduced blocks.
 static hzb_status install_skeleton(hzb_ctx *c, ShapeDev &sd, const std::vector<int> &J, DevBuf<double2> &T)
@@ -746,6 +764,12 @@ static hzb_status install_skeleton(hzb_ctx *c, ShapeDev &sd, const std::vector<i
         return HZB_ECUDA;
     }
     permute_rows_kernel<<<grid_for((size_t)k * n), 256, 0, c->stream>>>(k, n, src.ptr, T.ptr, sd.T64.ptr);
+    c->launches++;
+    if (check_cuda(c, sd.U64.ensure((size_t)k * n), "alloc U")) {
+        src.release();
+        return HZB_ENOMEM;
+    }
+    transpose_kernel<<<dim3((n + 31) / 32, (k + 31) / 32), dim3(32, 8), 0, c->stream>>>(k, n, sd.T64.ptr, sd.U64.ptr);
     c->launches++;
     hzb_status st = check_cuda(c, cudaStreamSynchronize(c->stream), "skeleton");
     src.release();
@@ -900,7 +924,7 @@ void release_compression(hzb_ctx *c)
         c->rctx = nullptr;
     }
     for (ShapeDev *s : c->shapes) {
-        s->T64.release(); s->St64.release(); s->St32.release(); s->red_offs.release();
+        s->T64.release(); s->U64.release(); s->St64.release(); s->St32.release(); s->red_offs.release();
         s->skel_k = 0;
         s->skel_J.clear();
     }
@@ -998,21 +1022,24 @@ static hzb_status build_reduced(hzb_ctx *c)
 }
 
 // out[ooff_b + i][r] = alpha sig[ooff_b + i][r] + beta sum_j A[i][j] y[yoff_b + j][r] for the
-// ms bodies b of a shape and i < rows, A rows x cols row-major (A precision T), columns
-// in groups of 8; one warp per row.
-template <typename T>
+// ms bodies b of a shape and i < rows; A rows x cols row-major.  One block of 256 threads
+// per row i, right-hand-side columns (body, r) in groups of 8, the row's products summed
+// across the block in a fixed order.  F32: A in FP32 and FP32 accumulation (the reduced
+// system's FP32 operator), else FP64.  The restriction T w (A = T), the extension
+// T^T y (A = T^T) and the reduced local operator S y (A = S) all take this form.
+template <bool F32>
 __global__ void __launch_bounds__(256) body_gemv_kernel(int rows, int cols, int ms, int R,
                                                         const long long *__restrict__ yoff,
-                                                        const long long *__restrict__ ooff,
-                                                        const T *__restrict__ A, const double2 *__restrict__ y,
-                                                        const double2 *__restrict__ sig, double alpha, double beta,
-                                                        double2 *__restrict__ out)
+                                                        const long long *__restrict__ ooff, const void *__restrict__ Av,
+                                                        const double2 *__restrict__ y, const double2 *__restrict__ sig,
+                                                        double alpha, double beta, double2 *__restrict__ out)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    typedef typename std::conditional<F32, float, double>::type acc_t;
+    __shared__ acc_t part[8][16];
+    const int i = blockIdx.x;
     if (i >= rows) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int ncol = ms * R;
-    const T *a = A + (size_t)i * cols;
     for (int c0 = 0; c0 < ncol; c0 += 8) {
         const int nc = min(8, ncol - c0);
         long long base[8];
@@ -1023,77 +1050,27 @@ __global__ void __launch_bounds__(256) body_gemv_kernel(int rows, int cols, int 
             base[q] = yoff[cc / R];
             rr[q] = cc % R;
         }
-        double sx[8], sy[8];
+        acc_t sx[8], sy[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) sx[q] = sy[q] = 0.0;
-        for (int j = lane; j < cols; j += 32) {
-            const T av = a[j];
-            const double ax = (double)av.x, ay = (double)av.y;
+        for (int q = 0; q < 8; ++q) sx[q] = sy[q] = (acc_t)0;
+        for (int j = threadIdx.x; j < cols; j += 256) {
+            acc_t ax, ay;
+            if (F32) {
+                const float2 av = ((const float2 *)Av)[(size_t)i * cols + j];
+                ax = av.x;
+                ay = av.y;
+            } else {
+                const double2 av = ((const double2 *)Av)[(size_t)i * cols + j];
+                ax = (acc_t)av.x;
+                ay = (acc_t)av.y;
+            }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 if (q < nc) {
                     const double2 v = y[(base[q] + j) * R + rr[q]];
-                    sx[q] = fma(ax, v.x, fma(-ay, v.y, sx[q]));
-                    sy[q] = fma(ax, v.y, fma(ay, v.x, sy[q]));
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            sx[q] = warp_sum(sx[q]);
-            sy[q] = warp_sum(sy[q]);
-        }
-        if (lane < nc) {
-            double vx = 0.0, vy = 0.0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q == lane) { vx = sx[q]; vy = sy[q]; }
-            const int cc = c0 + lane;
-            const size_t o = (size_t)(ooff[cc / R] + i) * R + cc % R;
-            double2 res = make_double2(beta * vx, beta * vy);
-            if (alpha != 0.0) {
-                res.x += alpha * sig[o].x;
-                res.y += alpha * sig[o].y;
-            }
-            out[o] = res;
-        }
-    }
-}
-
-// FP32 variant of the products' arithmetic: S in FP32 and FP32 accumulation
-__global__ void __launch_bounds__(256) body_gemv32_kernel(int rows, int cols, int ms, int R,
-                                                          const long long *__restrict__ off,
-                                                          const float2 *__restrict__ A, const double2 *__restrict__ y,
-                                                          const double2 *__restrict__ sig, double alpha, double beta,
-                                                          double2 *__restrict__ out)
-{
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (i >= rows) return;
-    const int ncol = ms * R;
-    const float2 *a = A + (size_t)i * cols;
-    for (int c0 = 0; c0 < ncol; c0 += 8) {
-        const int nc = min(8, ncol - c0);
-        long long base[8];
-        int rr[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int cc = min(c0 + q, ncol - 1);
-            base[q] = off[cc / R];
-            rr[q] = cc % R;
-        }
-        float sx[8], sy[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) sx[q] = sy[q] = 0.f;
-        for (int j = lane; j < cols; j += 32) {
-            const float2 av = a[j];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (q < nc) {
-                    const double2 vd = y[(base[q] + j) * R + rr[q]];
-                    const float vx = (float)vd.x, vy = (float)vd.y;
-                    sx[q] = fmaf(av.x, vx, fmaf(-av.y, vy, sx[q]));
-                    sy[q] = fmaf(av.x, vy, fmaf(av.y, vx, sy[q]));
+                    const acc_t vx = (acc_t)v.x, vy = (acc_t)v.y;
+                    sx[q] = fma(ax, vx, fma(-ay, vy, sx[q]));
+                    sy[q] = fma(ax, vy, fma(ay, vx, sy[q]));
                 }
             }
         }
@@ -1103,62 +1080,45 @@ __global__ void __launch_bounds__(256) body_gemv32_kernel(int rows, int cols, in
                 sx[q] += __shfl_xor_sync(0xffffffffu, sx[q], o);
                 sy[q] += __shfl_xor_sync(0xffffffffu, sy[q], o);
             }
-        if (lane < nc) {
-            float vx = 0.f, vy = 0.f;
+        if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q == lane) { vx = sx[q]; vy = sy[q]; }
-            const int cc = c0 + lane;
-            const size_t o = (size_t)(off[cc / R] + i) * R + cc % R;
-            double2 res = make_double2(beta * (double)vx, beta * (double)vy);
+            for (int q = 0; q < 8; ++q) {
+                part[w][2 * q] = sx[q];
+                part[w][2 * q + 1] = sy[q];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nc) {
+            const int q = threadIdx.x;
+            double vx = 0.0, vy = 0.0;
+            for (int ww = 0; ww < 8; ++ww) {
+                vx += (double)part[ww][2 * q];
+                vy += (double)part[ww][2 * q + 1];
+            }
+            const int cc = c0 + q;
+            const size_t o = (size_t)(ooff[cc / R] + i) * R + cc % R;
+            double2 res = make_double2(beta * vx, beta * vy);
             if (alpha != 0.0) {
                 res.x += alpha * sig[o].x;
                 res.y += alpha * sig[o].y;
             }
             out[o] = res;
         }
+        __syncthreads();
     }
 }
 
-// out[poff_b + i][r] = alpha sig[..] + beta sum_s T[s][i] y[roff_b + s][r]  (U_p y = T^T y)
-__global__ void __launch_bounds__(256) extend_kernel(int k, int n, int ms, int R, const long long *__restrict__ poff,
-                                                     const long long *__restrict__ roff,
-                                                     const double2 *__restrict__ T, const double2 *__restrict__ y,
-                                                     const double2 *__restrict__ sig, double alpha, double beta,
-                                                     double2 *__restrict__ out)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cc = blockIdx.y;               // column = body * R + r
-    if (i >= n) return;
-    const int b = cc / R, r = cc % R;
-    const double2 *yb = y + (size_t)roff[b] * R + r;
-    double sx = 0.0, sy = 0.0;
-    for (int s = 0; s < k; ++s) {
-        const double2 t = T[(size_t)s * n + i];
-        const double2 v = yb[(size_t)s * R];
-        sx = fma(t.x, v.x, fma(-t.y, v.y, sx));
-        sy = fma(t.x, v.y, fma(t.y, v.x, sy));
-    }
-    const size_t o = (size_t)(poff[b] + i) * R + r;
-    double2 res = make_double2(beta * sx, beta * sy);
-    if (alpha != 0.0) {
-        res.x += alpha * sig[o].x;
-        res.y += alpha * sig[o].y;
-    }
-    out[o] = res;
-}
 
 hzb_status reduced_local(hzb_ctx *c, int R, const double2 *y, const double2 *sigma, double alpha, double beta,
                          double2 *tau, bool fp32)
 {
     for (const hzb_ctx::RShape &rs : c->rshapes) {
-        const unsigned g = (unsigned)((rs.k + 7) / 8);
         if (fp32)
-            body_gemv32_kernel<<<g, 256, 0, c->stream>>>(rs.k, rs.k, rs.ms, R, rs.offs, rs.S32, y, sigma, alpha, beta,
-                                                         tau);
-        else
-            body_gemv_kernel<double2><<<g, 256, 0, c->stream>>>(rs.k, rs.k, rs.ms, R, rs.offs, rs.offs, rs.S64, y,
+            body_gemv_kernel<true><<<rs.k, 256, 0, c->stream>>>(rs.k, rs.k, rs.ms, R, rs.offs, rs.offs, rs.S32, y,
                                                                 sigma, alpha, beta, tau);
+        else
+            body_gemv_kernel<false><<<rs.k, 256, 0, c->stream>>>(rs.k, rs.k, rs.ms, R, rs.offs, rs.offs, rs.S64, y,
+                                                                 sigma, alpha, beta, tau);
         c->launches++;
     }
     return check_cuda(c, cudaGetLastError(), "reduced local operator");
@@ -1170,9 +1130,9 @@ static hzb_status restrict_all(hzb_ctx *c, int R, const double2 *w, double s, do
     for (ShapeDev *sp : c->shapes) {
         ShapeDev &sd = *sp;
         const int n = sd.geom.NG * sd.geom.NF;
-        body_gemv_kernel<double2><<<(unsigned)((sd.skel_k + 7) / 8), 256, 0, c->stream>>>(
-            sd.skel_k, n, (int)sd.bodies.size(), R, sd.body_offs.ptr, sd.red_offs.ptr, sd.T64.ptr, w, nullptr, 0.0, s,
-            out);
+        body_gemv_kernel<false><<<sd.skel_k, 256, 0, c->stream>>>(sd.skel_k, n, (int)sd.bodies.size(), R,
+                                                                  sd.body_offs.ptr, sd.red_offs.ptr, sd.T64.ptr, w,
+                                                                  nullptr, 0.0, s, out);
         c->launches++;
     }
     return check_cuda(c, cudaGetLastError(), "restrict");
@@ -1210,15 +1170,15 @@ hzb_status solve_reduced(hzb_ctx *c, int R, const double2 *v, const double2 *x0,
     // sig = D^{-1} (-v - U B~ sig~)
     const double2 *sig_t = r->sol.ptr;
     if (check_cuda(c, r->s_r.ensure(RR), "alloc")) return HZB_ENOMEM;
-    const int prec = c->opt.precision == HZB_PREC_FP64 ? HZB_PREC_FP64 : c->opt.residual;
-    st = prec == HZB_PREC_DOUBLE_FLOAT ? interbody_df(r, R, sig_t, r->s_r.ptr) : interbody64(r, R, sig_t, r->s_r.ptr);
+    // FP64 path: FP64; mixed path: double-float (about 1e-13 per term, far below its tolerance)
+    st = c->opt.precision == HZB_PREC_FP64 ? interbody64(r, R, sig_t, r->s_r.ptr) : interbody_df(r, R, sig_t, r->s_r.ptr);
     if (st) return fail(c, st, r->err);
     for (ShapeDev *sp : c->shapes) {
         ShapeDev &sd = *sp;
         const int n = sd.geom.NG * sd.geom.NF;
-        extend_kernel<<<dim3((n + 255) / 256, (unsigned)(sd.bodies.size() * R)), 256, 0, c->stream>>>(
-            sd.skel_k, n, (int)sd.bodies.size(), R, sd.body_offs.ptr, sd.red_offs.ptr, sd.T64.ptr, r->s_r.ptr, v, -1.0,
-            -1.0, c->w_b.ptr);
+        body_gemv_kernel<false><<<n, 256, 0, c->stream>>>(n, sd.skel_k, (int)sd.bodies.size(), R, sd.red_offs.ptr,
+                                                          sd.body_offs.ptr, sd.U64.ptr, r->s_r.ptr, v, -1.0, -1.0,
+                                                          c->w_b.ptr);
         c->launches++;
     }
     if (check_cuda(c, cudaGetLastError(), "extend")) return HZB_ECUDA;

@@ -84,7 +84,8 @@ struct ShapeDev {
     // accelerated scheme (compress.cu, Sec. 5): the shape's skeleton and reduced blocks
     int skel_k = 0;                       // skeleton size k (0: none)
     std::vector<int> skel_J;              // skeleton nodes, shape-local, ascending
-    DevBuf<double2> T64;                  // k x n row-major: V_p^* = T, U_p = T^T
+    DevBuf<double2> T64;                  // k x n row-major: V_p^* = T
+    DevBuf<double2> U64;                  // n x k row-major: U_p = T^T
     DevBuf<double2> St64;                 // k x k row-major: S_p = T A_pp^{-1} T^T
     DevBuf<float2> St32;                  // its FP32 copy
     DevBuf<long long> red_offs;           // first reduced-system node of each body of the shape
