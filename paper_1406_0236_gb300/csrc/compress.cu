@@ -305,30 +305,31 @@ __global__ void __launch_bounds__(1024) cpqr_pivot_kernel(int j, int m, int n, d
     if (threadIdx.x == 0) beta[b] = uu > 0.0 ? 2.0 / uu : 0.0;
 }
 
-// Step j: apply the reflector to every trailing column c > j (one block of 256 threads
-// per column; the column part j..m-1 is held in registers when it fits) and store the
-// exact norm of its rows j+1..m-1 as the column's new trailing norm.  Grid (n-j-1, batch).
-template <int MAXR>
+// Step j: apply the reflector to every trailing column c > j and store the exact norm of
+// its rows j+1..m-1 as the column's new trailing norm.  One warp per column (eight per
+// block, no block-wide synchronisation); the column part j..m-1 is held in registers,
+// W values per lane, when it fits (W = 0: two passes over memory).  Grid
+// (ceil((n-j-1)/8), batch).
+template <int W>
 __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, double2 *__restrict__ A, size_t sA,
                                                           double *__restrict__ nrm2, const int *__restrict__ rank,
                                                           const double2 *__restrict__ u,
                                                           const double *__restrict__ beta)
 {
-    __shared__ double red[32];
     const int b = blockIdx.y;
     if (rank[b] >= 0) return;
-    const int c = j + 1 + blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int c = j + 1 + blockIdx.x * 8 + (threadIdx.x >> 5);
     if (c >= n) return;
     double2 *col = A + b * sA + (size_t)c * m;
     const double2 *ub = u + (size_t)b * m;
     const double bt = beta[b];
-    const int len = m - j;
     double sr = 0.0, si = 0.0;
-    if (MAXR > 0 && len <= MAXR * 256) {
-        double2 v[MAXR > 0 ? MAXR : 1];
+    if (W > 0) {
+        double2 v[W > 0 ? W : 1];
 #pragma unroll
-        for (int q = 0; q < (MAXR > 0 ? MAXR : 1); ++q) {
-            const int r = j + threadIdx.x + q * 256;
+        for (int q = 0; q < (W > 0 ? W : 1); ++q) {
+            const int r = j + lane + 32 * q;
             if (r < m) {
                 v[q] = col[r];
                 const double2 w = ub[r];
@@ -336,13 +337,13 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
                 si += w.x * v[q].y - w.y * v[q].x;
             }
         }
-        sr = block_sum(sr, red);
-        si = block_sum(si, red);
+        sr = warp_sum(sr);
+        si = warp_sum(si);
         const double fr = bt * sr, fi = bt * si;
         double nn = 0.0;
 #pragma unroll
-        for (int q = 0; q < (MAXR > 0 ? MAXR : 1); ++q) {
-            const int r = j + threadIdx.x + q * 256;
+        for (int q = 0; q < (W > 0 ? W : 1); ++q) {
+            const int r = j + lane + 32 * q;
             if (r < m) {
                 const double2 w = ub[r];
                 double2 a = v[q];
@@ -352,19 +353,19 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
                 if (r > j) nn += a.x * a.x + a.y * a.y;
             }
         }
-        nn = block_sum(nn, red);
-        if (threadIdx.x == 0) nrm2[(size_t)b * n + c] = nn;
+        nn = warp_sum(nn);
+        if (lane == 0) nrm2[(size_t)b * n + c] = nn;
     } else {
-        for (int r = j + threadIdx.x; r < m; r += 256) {
+        for (int r = j + lane; r < m; r += 32) {
             const double2 a = col[r], w = ub[r];
             sr += w.x * a.x + w.y * a.y;
             si += w.x * a.y - w.y * a.x;
         }
-        sr = block_sum(sr, red);
-        si = block_sum(si, red);
+        sr = warp_sum(sr);
+        si = warp_sum(si);
         const double fr = bt * sr, fi = bt * si;
         double nn = 0.0;
-        for (int r = j + threadIdx.x; r < m; r += 256) {
+        for (int r = j + lane; r < m; r += 32) {
             const double2 w = ub[r];
             double2 a = col[r];
             a.x -= fr * w.x - fi * w.y;
@@ -372,8 +373,8 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
             col[r] = a;
             if (r > j) nn += a.x * a.x + a.y * a.y;
         }
-        nn = block_sum(nn, red);
-        if (threadIdx.x == 0) nrm2[(size_t)b * n + c] = nn;
+        nn = warp_sum(nn);
+        if (lane == 0) nrm2[(size_t)b * n + c] = nn;
     }
 }
 
@@ -384,21 +385,22 @@ static hzb_status cpqr_run(hzb_ctx *c, int m, int n, int batch, double2 *A, size
                            int *rank, const double *thr2, double2 *u, double *beta, std::vector<int> &ranks)
 {
     const int steps = std::min(m, n);
-    auto update = [&](int j, dim3 g) {
+    auto update = [&](int j, int batch_) {
         const int len = m - j;
-        if (len <= 2 * 256)
-            cpqr_update_kernel<2><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
-        else if (len <= 8 * 256)
-            cpqr_update_kernel<8><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
-        else if (len <= 24 * 256)
-            cpqr_update_kernel<24><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+        const dim3 g((unsigned)((n - j - 1 + 7) / 8), batch_);
+        if (len <= 4 * 32)
+            cpqr_update_kernel<4><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+        else if (len <= 16 * 32)
+            cpqr_update_kernel<16><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+        else if (len <= 32 * 32)
+            cpqr_update_kernel<32><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else
             cpqr_update_kernel<0><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
     };
     ranks.assign(batch, -1);
     for (int j = 0; j < steps; ++j) {
         cpqr_pivot_kernel<<<batch, 1024, 0, c->stream>>>(j, m, n, A, sA, nrm2, perm, rank, thr2, u, beta);
-        if (n - j - 1 > 0) update(j, dim3(n - j - 1, batch));
+        if (n - j - 1 > 0) update(j, batch);
         c->launches += 2;
         if ((j & 31) == 31 || j == steps - 1) {
             if (check_cuda(c, cudaGetLastError(), "cpqr")) return HZB_ECUDA;
@@ -1022,11 +1024,13 @@ static hzb_status build_reduced(hzb_ctx *c)
 }
 
 // out[ooff_b + i][r] = alpha sig[ooff_b + i][r] + beta sum_j A[i][j] y[yoff_b + j][r] for the
-// ms bodies b of a shape and i < rows; A rows x cols row-major.  One block of 256 threads
-// per row i, right-hand-side columns (body, r) in groups of 8, the row's products summed
-// across the block in a fixed order.  F32: A in FP32 and FP32 accumulation (the reduced
-// system's FP32 operator), else FP64.  The restriction T w (A = T), the extension
-// T^T y (A = T^T) and the reduced local operator S y (A = S) all take this form.
+// ms bodies b of a shape and i < rows; A rows x cols row-major.  One warp per row, eight
+// rows per block; the right-hand-side columns (body, r) go in groups of 8, and each
+// 256-wide slice of their y values is staged once in shared memory for the block's
+// eight rows.  F32: A in FP32 and FP32 accumulation (the reduced system's FP32
+// operator), else FP64.  The restriction T w (A = T), the extension T^T y (A = T^T)
+// and the reduced local operator S y (A = S) all take this form.
+static const int GEMV_ROWS = 8;
 template <bool F32>
 __global__ void __launch_bounds__(256) body_gemv_kernel(int rows, int cols, int ms, int R,
                                                         const long long *__restrict__ yoff,
@@ -1035,42 +1039,53 @@ __global__ void __launch_bounds__(256) body_gemv_kernel(int rows, int cols, int 
                                                         double alpha, double beta, double2 *__restrict__ out)
 {
     typedef typename std::conditional<F32, float, double>::type acc_t;
-    __shared__ acc_t part[8][16];
-    const int i = blockIdx.x;
-    if (i >= rows) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ acc_t ys[8][256][2];
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * GEMV_ROWS + (threadIdx.x >> 5);
     const int ncol = ms * R;
     for (int c0 = 0; c0 < ncol; c0 += 8) {
         const int nc = min(8, ncol - c0);
-        long long base[8];
-        int rr[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int cc = min(c0 + q, ncol - 1);
-            base[q] = yoff[cc / R];
-            rr[q] = cc % R;
-        }
         acc_t sx[8], sy[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) sx[q] = sy[q] = (acc_t)0;
-        for (int j = threadIdx.x; j < cols; j += 256) {
-            acc_t ax, ay;
-            if (F32) {
-                const float2 av = ((const float2 *)Av)[(size_t)i * cols + j];
-                ax = av.x;
-                ay = av.y;
-            } else {
-                const double2 av = ((const double2 *)Av)[(size_t)i * cols + j];
-                ax = (acc_t)av.x;
-                ay = (acc_t)av.y;
-            }
+        for (int jc = 0; jc < cols; jc += 256) {
+            __syncthreads();
+            {
+                const int j = jc + threadIdx.x;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (q < nc) {
-                    const double2 v = y[(base[q] + j) * R + rr[q]];
-                    const acc_t vx = (acc_t)v.x, vy = (acc_t)v.y;
-                    sx[q] = fma(ax, vx, fma(-ay, vy, sx[q]));
-                    sy[q] = fma(ax, vy, fma(ay, vx, sy[q]));
+                for (int q = 0; q < 8; ++q) {
+                    if (q < nc) {
+                        const int cc = c0 + q;
+                        double2 v = make_double2(0.0, 0.0);
+                        if (j < cols) v = y[(yoff[cc / R] + j) * R + cc % R];
+                        ys[q][threadIdx.x][0] = (acc_t)v.x;
+                        ys[q][threadIdx.x][1] = (acc_t)v.y;
+                    }
+                }
+            }
+            __syncthreads();
+            if (i < rows) {
+                const int jn = min(256, cols - jc);
+#pragma unroll 4
+                for (int jj = lane; jj < jn; jj += 32) {
+                    acc_t ax, ay;
+                    if (F32) {
+                        const float2 av = ((const float2 *)Av)[(size_t)i * cols + jc + jj];
+                        ax = av.x;
+                        ay = av.y;
+                    } else {
+                        const double2 av = ((const double2 *)Av)[(size_t)i * cols + jc + jj];
+                        ax = (acc_t)av.x;
+                        ay = (acc_t)av.y;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (q < nc) {
+                            const acc_t vx = ys[q][jj][0], vy = ys[q][jj][1];
+                            sx[q] = fma(ax, vx, fma(-ay, vy, sx[q]));
+                            sy[q] = fma(ax, vy, fma(ay, vx, sy[q]));
+                        }
+                    }
                 }
             }
         }
@@ -1080,22 +1095,15 @@ __global__ void __launch_bounds__(256) body_gemv_kernel(int rows, int cols, int 
                 sx[q] += __shfl_xor_sync(0xffffffffu, sx[q], o);
                 sy[q] += __shfl_xor_sync(0xffffffffu, sy[q], o);
             }
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                part[w][2 * q] = sx[q];
-                part[w][2 * q + 1] = sy[q];
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < nc) {
-            const int q = threadIdx.x;
+        if (i < rows && lane < nc) {
             double vx = 0.0, vy = 0.0;
-            for (int ww = 0; ww < 8; ++ww) {
-                vx += (double)part[ww][2 * q];
-                vy += (double)part[ww][2 * q + 1];
-            }
-            const int cc = c0 + q;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q == lane) {
+                    vx = (double)sx[q];
+                    vy = (double)sy[q];
+                }
+            const int cc = c0 + lane;
             const size_t o = (size_t)(ooff[cc / R] + i) * R + cc % R;
             double2 res = make_double2(beta * vx, beta * vy);
             if (alpha != 0.0) {
@@ -1104,20 +1112,20 @@ __global__ void __launch_bounds__(256) body_gemv_kernel(int rows, int cols, int 
             }
             out[o] = res;
         }
-        __syncthreads();
     }
 }
 
+static unsigned gemv_blocks(int rows) { return (unsigned)((rows + GEMV_ROWS - 1) / GEMV_ROWS); }
 
 hzb_status reduced_local(hzb_ctx *c, int R, const double2 *y, const double2 *sigma, double alpha, double beta,
                          double2 *tau, bool fp32)
 {
     for (const hzb_ctx::RShape &rs : c->rshapes) {
         if (fp32)
-            body_gemv_kernel<true><<<rs.k, 256, 0, c->stream>>>(rs.k, rs.k, rs.ms, R, rs.offs, rs.offs, rs.S32, y,
+            body_gemv_kernel<true><<<gemv_blocks(rs.k), 256, 0, c->stream>>>(rs.k, rs.k, rs.ms, R, rs.offs, rs.offs, rs.S32, y,
                                                                 sigma, alpha, beta, tau);
         else
-            body_gemv_kernel<false><<<rs.k, 256, 0, c->stream>>>(rs.k, rs.k, rs.ms, R, rs.offs, rs.offs, rs.S64, y,
+            body_gemv_kernel<false><<<gemv_blocks(rs.k), 256, 0, c->stream>>>(rs.k, rs.k, rs.ms, R, rs.offs, rs.offs, rs.S64, y,
                                                                  sigma, alpha, beta, tau);
         c->launches++;
     }
@@ -1130,7 +1138,7 @@ static hzb_status restrict_all(hzb_ctx *c, int R, const double2 *w, double s, do
     for (ShapeDev *sp : c->shapes) {
         ShapeDev &sd = *sp;
         const int n = sd.geom.NG * sd.geom.NF;
-        body_gemv_kernel<false><<<sd.skel_k, 256, 0, c->stream>>>(sd.skel_k, n, (int)sd.bodies.size(), R,
+        body_gemv_kernel<false><<<gemv_blocks(sd.skel_k), 256, 0, c->stream>>>(sd.skel_k, n, (int)sd.bodies.size(), R,
                                                                   sd.body_offs.ptr, sd.red_offs.ptr, sd.T64.ptr, w,
                                                                   nullptr, 0.0, s, out);
         c->launches++;
@@ -1176,7 +1184,7 @@ hzb_status solve_reduced(hzb_ctx *c, int R, const double2 *v, const double2 *x0,
     for (ShapeDev *sp : c->shapes) {
         ShapeDev &sd = *sp;
         const int n = sd.geom.NG * sd.geom.NF;
-        body_gemv_kernel<false><<<n, 256, 0, c->stream>>>(n, sd.skel_k, (int)sd.bodies.size(), R, sd.red_offs.ptr,
+        body_gemv_kernel<false><<<gemv_blocks(n), 256, 0, c->stream>>>(n, sd.skel_k, (int)sd.bodies.size(), R, sd.red_offs.ptr,
                                                           sd.body_offs.ptr, sd.U64.ptr, r->s_r.ptr, v, -1.0, -1.0,
                                                           c->w_b.ptr);
         c->launches++;
