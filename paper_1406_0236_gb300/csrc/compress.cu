@@ -306,21 +306,24 @@ __global__ void __launch_bounds__(1024) cpqr_pivot_kernel(int j, int m, int n, d
 }
 
 // Step j: apply the reflector to every trailing column c > j and store the exact norm of
-// its rows j+1..m-1 as the column's new trailing norm.  One warp per column (eight per
-// block, no block-wide synchronisation); the column part j..m-1 is held in registers,
-// W values per lane, when it fits (W = 0: two passes over memory).  Grid
-// (ceil((n-j-1)/8), batch).
-template <int W>
+// its rows j+1..m-1 as the column's new trailing norm.  NW warps per column (the column
+// part j..m-1 in registers, W values per lane) with the two sums shared through shared
+// memory when NW > 1; eight columns per block when NW = 1.  W = 0: one warp per column,
+// two passes over memory (columns longer than the register form holds).
+// Grid (columns / columns per block, batch).
+template <int NW, int W>
 __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, double2 *__restrict__ A, size_t sA,
                                                           double *__restrict__ nrm2, const int *__restrict__ rank,
                                                           const double2 *__restrict__ u,
                                                           const double *__restrict__ beta)
 {
+    __shared__ double part[8][3];
     const int b = blockIdx.y;
     if (rank[b] >= 0) return;
-    const int lane = threadIdx.x & 31;
-    const int c = j + 1 + blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (c >= n) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int c = NW == 1 ? j + 1 + blockIdx.x * 8 + wp : j + 1 + blockIdx.x;
+    const int r0 = j + (NW == 1 ? 0 : wp * 32 * W) + lane;      // this lane's first row
+    if (NW == 1 && c >= n) return;
     double2 *col = A + b * sA + (size_t)c * m;
     const double2 *ub = u + (size_t)b * m;
     const double bt = beta[b];
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
         double2 v[W > 0 ? W : 1];
 #pragma unroll
         for (int q = 0; q < (W > 0 ? W : 1); ++q) {
-            const int r = j + lane + 32 * q;
+            const int r = r0 + 32 * q;
             if (r < m) {
                 v[q] = col[r];
                 const double2 w = ub[r];
@@ -339,11 +342,23 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
         }
         sr = warp_sum(sr);
         si = warp_sum(si);
+        if (NW > 1) {
+            if (lane == 0) {
+                part[wp][0] = sr;
+                part[wp][1] = si;
+            }
+            __syncthreads();
+            sr = si = 0.0;
+            for (int q = 0; q < NW; ++q) {
+                sr += part[q][0];
+                si += part[q][1];
+            }
+        }
         const double fr = bt * sr, fi = bt * si;
         double nn = 0.0;
 #pragma unroll
         for (int q = 0; q < (W > 0 ? W : 1); ++q) {
-            const int r = j + lane + 32 * q;
+            const int r = r0 + 32 * q;
             if (r < m) {
                 const double2 w = ub[r];
                 double2 a = v[q];
@@ -354,7 +369,17 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
             }
         }
         nn = warp_sum(nn);
-        if (lane == 0) nrm2[(size_t)b * n + c] = nn;
+        if (NW > 1) {
+            if (lane == 0) part[wp][2] = nn;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int q = 0; q < NW; ++q) t += part[q][2];
+                nrm2[(size_t)b * n + c] = t;
+            }
+        } else if (lane == 0) {
+            nrm2[(size_t)b * n + c] = nn;
+        }
     } else {
         for (int r = j + lane; r < m; r += 32) {
             const double2 a = col[r], w = ub[r];
@@ -386,16 +411,22 @@ static hzb_status cpqr_run(hzb_ctx *c, int m, int n, int batch, double2 *A, size
 {
     const int steps = std::min(m, n);
     auto update = [&](int j, int batch_) {
-        const int len = m - j;
-        const dim3 g((unsigned)((n - j - 1 + 7) / 8), batch_);
+        const int len = m - j, nc = n - j - 1;
+        const dim3 g8((unsigned)((nc + 7) / 8), batch_), g1((unsigned)nc, batch_);
         if (len <= 4 * 32)
-            cpqr_update_kernel<4><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+            cpqr_update_kernel<1, 4><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else if (len <= 16 * 32)
-            cpqr_update_kernel<16><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+            cpqr_update_kernel<1, 16><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else if (len <= 32 * 32)
-            cpqr_update_kernel<32><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+            cpqr_update_kernel<1, 32><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+        else if (len <= 2 * 32 * 32)
+            cpqr_update_kernel<2, 32><<<g1, 64, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+        else if (len <= 3 * 32 * 32)
+            cpqr_update_kernel<3, 32><<<g1, 96, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+        else if (len <= 4 * 32 * 32)
+            cpqr_update_kernel<4, 32><<<g1, 128, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else
-            cpqr_update_kernel<0><<<g, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+            cpqr_update_kernel<1, 0><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
     };
     ranks.assign(batch, -1);
     for (int j = 0; j < steps; ++j) {
