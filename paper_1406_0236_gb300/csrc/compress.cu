@@ -306,11 +306,12 @@ __global__ void __launch_bounds__(1024) cpqr_pivot_kernel(int j, int m, int n, d
 }
 
 // Step j: apply the reflector to every trailing column c > j and store the exact norm of
-// its rows j+1..m-1 as the column's new trailing norm.  NW warps per column (the column
-// part j..m-1 in registers, W values per lane) with the two sums shared through shared
-// memory when NW > 1; eight columns per block when NW = 1.  W = 0: one warp per column,
-// two passes over memory (columns longer than the register form holds).
-// Grid (columns / columns per block, batch).
+// its rows j+1..m-1 as the column's new trailing norm.  One warp per column, eight per
+// block, no block-wide synchronisation: the column part j..m-1 is held in registers, W
+// values per lane, when it fits; W = 0 makes two passes over memory.  NW > 1 spreads a
+// column over NW warps with the sums shared in shared memory (64-128 thread blocks, one
+// column each); it measured slower than the two-pass form for 1,024-2,600 rows and is
+// not dispatched.  Grid (ceil((n-j-1)/8), batch) for NW = 1.
 template <int NW, int W>
 __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, double2 *__restrict__ A, size_t sA,
                                                           double *__restrict__ nrm2, const int *__restrict__ rank,
@@ -412,19 +413,13 @@ static hzb_status cpqr_run(hzb_ctx *c, int m, int n, int batch, double2 *A, size
     const int steps = std::min(m, n);
     auto update = [&](int j, int batch_) {
         const int len = m - j, nc = n - j - 1;
-        const dim3 g8((unsigned)((nc + 7) / 8), batch_), g1((unsigned)nc, batch_);
+        const dim3 g8((unsigned)((nc + 7) / 8), batch_);
         if (len <= 4 * 32)
             cpqr_update_kernel<1, 4><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else if (len <= 16 * 32)
             cpqr_update_kernel<1, 16><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else if (len <= 32 * 32)
             cpqr_update_kernel<1, 32><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
-        else if (len <= 2 * 32 * 32)
-            cpqr_update_kernel<2, 32><<<g1, 64, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
-        else if (len <= 3 * 32 * 32)
-            cpqr_update_kernel<3, 32><<<g1, 96, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
-        else if (len <= 4 * 32 * 32)
-            cpqr_update_kernel<4, 32><<<g1, 128, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else
             cpqr_update_kernel<1, 0><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
     };
