@@ -212,3 +212,42 @@ def test_spheroids8_green_identity_through_compressed_solve(big):
     u = s.eval_field(tg)[:, 0]
     ue = fields.point_source_field(tg, src, wl.k)
     assert np.abs(u - ue).max() < 1e-7 * np.abs(ue).max()
+
+
+def test_compressed_solve_many_rhs_and_guess(sep):
+    """R = 3 plane waves through the reduced system, then the same data with a guess
+    (restricted by T before the reduced GMRES) and the solutions as guesses."""
+    from oracle import dense_solve, fields
+    wl, P, D = sep
+    s = gpu_solver(wl, precision=1, tol=1e-11)
+    s.compress(1e-10)
+    dirs = W.uniform_directions(3, 21)
+    st = s.solve_plane_waves(dirs)
+    assert st.converged
+    V = fields.plane_wave(P.nodes.x, dirs, P.k)
+    ref = np.stack([dense_solve(D, V[:, r]) for r in range(3)], axis=1)
+    got = s.get_density()
+    for r in range(3):
+        assert rel_l2(got[:, r], ref[:, r]) < 1e-8
+    st2 = s.solve_data(np.ascontiguousarray(V), x0=np.ascontiguousarray(got))
+    assert st2.converged and st2.iterations < st.iterations
+    assert rel_l2(s.get_density(), ref) < 1e-8
+
+
+def test_set_skeleton_refuses_bad_input(sep):
+    from paper_1406_0236_gb300 import HzbError
+    wl, P, _ = sep
+    s = gpu_solver(wl)
+    n = wl.bodies[0].shape.n_nodes
+    J, T = _given_skeleton(n, 50, 3)
+    bad = [(np.array([0, 0, 1]), T[:3]),                       # repeated index
+           (np.array([-1, 2, 3]), T[:3]),                      # out of range
+           (np.array([1, 2, n]), T[:3])]
+    for Jb, Tb in bad:
+        with pytest.raises(HzbError) as e:
+            s.set_skeleton(0, Jb, Tb)
+        assert e.value.status == -1
+    assert s.reduced_size == 0
+    with pytest.raises(HzbError) as e:
+        s.compress(1.5)
+    assert e.value.status == -1
