@@ -251,3 +251,29 @@ def test_set_skeleton_refuses_bad_input(sep):
     with pytest.raises(HzbError) as e:
         s.compress(1.5)
     assert e.value.status == -1
+
+
+def test_mixed27_uneven_shapes_compressed():
+    """27 bodies of 27 distinct shapes (uneven sizes): every shape compressed, 64 plane
+    waves through the reduced system (FP32 inner sums on the tensor-core engine), and
+    Green's identity through the compressed solve."""
+    require_gpu()
+    from oracle import fields
+    wl = W.mixed27()
+    s = gpu_solver(wl, precision=1, tol=1e-9)
+    s.compress(1e-8)
+    ks = np.array([s.get_skeleton_size(q) for q in range(len(wl.bodies))])
+    ns = np.array([b.shape.n_nodes for b in wl.bodies])
+    assert (ks > 0).all() and (ks < 0.2 * ns).all()
+    assert s.reduced_size == ks.sum()
+    st = s.solve_plane_waves(wl.directions)
+    assert st.converged
+    x, _, _ = s.get_nodes()
+    src = W.point_sources(wl, 5)
+    tg = W.exterior_targets(wl, 10, 6)
+    v = -fields.point_source_field(x, src, wl.k)
+    st = s.solve_data(np.ascontiguousarray(v[:, None]))
+    assert st.converged
+    u = s.eval_field(tg)[:, 0]
+    ue = fields.point_source_field(tg, src, wl.k)
+    assert np.abs(u - ue).max() < 1e-7 * np.abs(ue).max()
