@@ -277,3 +277,24 @@ def test_mixed27_uneven_shapes_compressed():
     u = s.eval_field(tg)[:, 0]
     ue = fields.point_source_field(tg, src, wl.k)
     assert np.abs(u - ue).max() < 1e-7 * np.abs(ue).max()
+
+
+def test_compressed_solve_with_device_tensors(sep):
+    """hzb_solve_data on device data and guess (torch CUDA tensors) through the reduced
+    system gives the host-data answer."""
+    import torch
+    from oracle import fields
+    wl, P, _ = sep
+    s = gpu_solver(wl, precision=1, tol=1e-11)
+    s.compress(1e-10)
+    dirs = W.uniform_directions(2, 5)
+    v = np.ascontiguousarray(fields.plane_wave(P.nodes.x, dirs, P.k))
+    s.solve_data(v)
+    host = s.get_density().copy()
+    vd = torch.from_numpy(v).cuda()
+    x0 = torch.from_numpy(host).cuda() * 0.99
+    st = s.solve_data(vd, x0=x0)
+    assert st.converged
+    out = torch.empty_like(vd)
+    s.get_density(out)
+    assert rel_l2(out.cpu().numpy(), host) < 1e-9
