@@ -138,23 +138,29 @@ static void dft_smem_limit(size_t bytes)
 }
 
 // Batched complex GEMM C[p] = A[p] B[p], A: n x n, B and C: n x nc, row-major.
-// 32 x 32 output tile per block, 256 threads, 2 x 2 outputs per thread, K step 16.
-template <typename T>
+// 32 x (16 TB) output tile per block, 256 threads, 2 x TB outputs per thread, K step 16;
+// TB = 1 for panels of at most 16 columns (one body of a shape and R = 1 ... 8 bodies
+// with R = 1 fill 16), so no half of the tile multiplies zeros.
+template <typename T, int TB>
 __global__ void __launch_bounds__(256)
 modal_gemm_kernel(int n, int nc, const typename C2<T>::t *__restrict__ A, const typename C2<T>::t *__restrict__ B,
                   typename C2<T>::t *__restrict__ C)
 {
     typedef typename C2<T>::t ct;
     __shared__ ct As[32][17];
-    __shared__ ct Bs[16][33];
+    __shared__ ct Bs[16][16 * TB + 1];
     const int p = blockIdx.z;
     const ct *Ap = A + (size_t)p * n * n;
     const ct *Bp = B + (size_t)p * n * nc;
     ct *Cp = C + (size_t)p * n * nc;
-    const int row0 = blockIdx.y * 32, col0 = blockIdx.x * 32;
+    const int row0 = blockIdx.y * 32, col0 = blockIdx.x * (16 * TB);
     const int tid = threadIdx.x;
-    const int tr = tid / 16, tc = tid % 16;     // rows tr, tr+16; cols tc, tc+16
-    T accr[2][2] = {{0, 0}, {0, 0}}, acci[2][2] = {{0, 0}, {0, 0}};
+    const int tr = tid / 16, tc = tid % 16;     // rows tr, tr+16; cols tc (, tc+16)
+    T accr[2][TB], acci[2][TB];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < TB; ++b) accr[a][b] = acci[a][b] = (T)0;
     for (int k0 = 0; k0 < n; k0 += 16) {
         for (int e = tid; e < 32 * 16; e += 256) {
             int r = e / 16, kk = e % 16;
@@ -164,8 +170,8 @@ modal_gemm_kernel(int n, int nc, const typename C2<T>::t *__restrict__ A, const 
             if (gr < n && gk < n) v = Ap[(size_t)gr * n + gk];
             As[r][kk] = v;
         }
-        for (int e = tid; e < 16 * 32; e += 256) {
-            int kk = e / 32, cc = e % 32;
+        for (int e = tid; e < 16 * 16 * TB; e += 256) {
+            int kk = e / (16 * TB), cc = e % (16 * TB);
             int gk = k0 + kk, gc = col0 + cc;
             ct v;
             v.x = (T)0; v.y = (T)0;
@@ -175,19 +181,23 @@ modal_gemm_kernel(int n, int nc, const typename C2<T>::t *__restrict__ A, const 
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            ct a0 = As[tr][kk], a1 = As[tr + 16][kk];
-            ct b0 = Bs[kk][tc], b1 = Bs[kk][tc + 16];
-            accr[0][0] += a0.x * b0.x - a0.y * b0.y; acci[0][0] += a0.x * b0.y + a0.y * b0.x;
-            accr[0][1] += a0.x * b1.x - a0.y * b1.y; acci[0][1] += a0.x * b1.y + a0.y * b1.x;
-            accr[1][0] += a1.x * b0.x - a1.y * b0.y; acci[1][0] += a1.x * b0.y + a1.y * b0.x;
-            accr[1][1] += a1.x * b1.x - a1.y * b1.y; acci[1][1] += a1.x * b1.y + a1.y * b1.x;
+            const ct a[2] = {As[tr][kk], As[tr + 16][kk]};
+#pragma unroll
+            for (int b = 0; b < TB; ++b) {
+                const ct bb = Bs[kk][tc + 16 * b];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    accr[q][b] += a[q].x * bb.x - a[q].y * bb.y;
+                    acci[q][b] += a[q].x * bb.y + a[q].y * bb.x;
+                }
+            }
         }
         __syncthreads();
     }
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < TB; ++b) {
             int gr = row0 + tr + 16 * a, gc = col0 + tc + 16 * b;
             if (gr < n && gc < nc) {
                 ct v;
@@ -196,6 +206,16 @@ modal_gemm_kernel(int n, int nc, const typename C2<T>::t *__restrict__ A, const 
                 Cp[(size_t)gr * nc + gc] = v;
             }
         }
+}
+
+template <typename T>
+static void modal_gemm(cudaStream_t st, int n, int nc, int modes, const typename C2<T>::t *A,
+                       const typename C2<T>::t *B, typename C2<T>::t *C)
+{
+    if (nc <= 16)
+        modal_gemm_kernel<T, 1><<<dim3((nc + 15) / 16, (n + 31) / 32, modes), 256, 0, st>>>(n, nc, A, B, C);
+    else
+        modal_gemm_kernel<T, 2><<<dim3((nc + 31) / 32, (n + 31) / 32, modes), 256, 0, st>>>(n, nc, A, B, C);
 }
 
 template <typename T>
@@ -240,7 +260,7 @@ static hzb_status local_inverse_t(hzb_ctx *c, int R, const double2 *y, const dou
         } else if (f32 && c->modal_engine == 1)
             launch_modal_gemm_tc(c, NG, ncols, M + 1, (const float2 *)S, (const float2 *)yh, (float2 *)th);
         else
-            modal_gemm_kernel<T><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(NG, ncols, S, yh, th);
+            modal_gemm<T>(c->stream, NG, ncols, M + 1, S, yh, th);
         dft_inverse_kernel<T><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, th, sigma,
                                                                                alpha, beta, tau);
         c->launches += 3;
@@ -282,8 +302,7 @@ hzb_status local_inverse64_scratch(hzb_ctx *c, int R, const double2 *y, const do
         if (smem > 200 * 1024) return fail(c, HZB_EINVAL, "n_modes * R too large for the modal apply");
         dft_smem_limit<double>(smem);
         dft_forward_kernel<double><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, y, yh);
-        modal_gemm_kernel<double><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(
-            NG, ncols, sd.S64.ptr, yh, th);
+        modal_gemm<double>(c->stream, NG, ncols, M + 1, sd.S64.ptr, yh, th);
         dft_inverse_kernel<double><<<dim3(NG, ms), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, doff, th,
                                                                                     sigma, alpha, beta, tau);
         c->launches += 3;
@@ -308,8 +327,7 @@ hzb_status shape_inverse64(hzb_ctx *c, ShapeDev &sd, int R, const double2 *X, do
     dft_smem_limit<double>(smem);
     dft_forward_kernel<double><<<dim3(NG, 1), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, c->zero_off.ptr, X,
                                                                              c->yhat64.ptr);
-    modal_gemm_kernel<double><<<dim3((ncols + 31) / 32, (NG + 31) / 32, M + 1), 256, 0, c->stream>>>(
-        NG, ncols, sd.S64.ptr, c->yhat64.ptr, c->that64.ptr);
+    modal_gemm<double>(c->stream, NG, ncols, M + 1, sd.S64.ptr, c->yhat64.ptr, c->that64.ptr);
     dft_inverse_kernel<double><<<dim3(NG, 1), DFT_THREADS, smem, c->stream>>>(NG, NF, R, ncols, c->zero_off.ptr,
                                                                              c->that64.ptr, nullptr, 0.0, 1.0, Y);
     c->launches += 3;
