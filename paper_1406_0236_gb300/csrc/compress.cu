@@ -774,6 +774,8 @@ __global__ void transpose_kernel(int k, int n, const double2 *__restrict__ T, do
     }
 }
 
+__global__ void split_df_kernel(size_t n, const double2 *__restrict__ a, float4 *__restrict__ out);
+
 // Install J (any order, distinct) and T (device, k x n rows in J's order) as the shape's
 // skeleton with J ascending, and form its reduced blocks.
 static hzb_status install_skeleton(hzb_ctx *c, ShapeDev &sd, const std::vector<int> &J, DevBuf<double2> &T)
@@ -799,6 +801,13 @@ static hzb_status install_skeleton(hzb_ctx *c, ShapeDev &sd, const std::vector<i
     }
     transpose_kernel<<<dim3((n + 31) / 32, (k + 31) / 32), dim3(32, 8), 0, c->stream>>>(k, n, sd.T64.ptr, sd.U64.ptr);
     c->launches++;
+    if (check_cuda(c, sd.Tdf.ensure((size_t)k * n), "alloc T") || check_cuda(c, sd.Udf.ensure((size_t)k * n), "alloc U")) {
+        src.release();
+        return HZB_ENOMEM;
+    }
+    split_df_kernel<<<(unsigned)(((size_t)k * n + 255) / 256), 256, 0, c->stream>>>((size_t)k * n, sd.T64.ptr, sd.Tdf.ptr);
+    split_df_kernel<<<(unsigned)(((size_t)k * n + 255) / 256), 256, 0, c->stream>>>((size_t)k * n, sd.U64.ptr, sd.Udf.ptr);
+    c->launches += 2;
     hzb_status st = check_cuda(c, cudaStreamSynchronize(c->stream), "skeleton");
     src.release();
     if (st) return st;
@@ -952,12 +961,14 @@ void release_compression(hzb_ctx *c)
         c->rctx = nullptr;
     }
     for (ShapeDev *s : c->shapes) {
-        s->T64.release(); s->U64.release(); s->St64.release(); s->St32.release(); s->red_offs.release();
+        s->T64.release(); s->U64.release(); s->Tdf.release(); s->Udf.release(); s->St64.release();
+        s->St32.release(); s->red_offs.release();
         s->skel_k = 0;
         s->skel_J.clear();
     }
     c->rb.release();
     c->rx.release();
+    c->ysplit.release();
     c->accel = false;
 }
 
@@ -1143,6 +1154,131 @@ __global__ void __launch_bounds__(256) body_gemv_kernel(int rows, int cols, int 
 
 static unsigned gemv_blocks(int rows) { return (unsigned)((rows + GEMV_ROWS - 1) / GEMV_ROWS); }
 
+// x -> (hi, lo) in FP32 with hi = fl(x), lo = fl(x - hi): x = hi + lo to about 2^-48 |x|
+__global__ void split_df_kernel(size_t n, const double2 *__restrict__ a, float4 *__restrict__ out)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double2 v = a[e];
+    const float hx = (float)v.x, hy = (float)v.y;
+    out[e] = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
+}
+
+// a + b exactly as (s, err) (Knuth's two-sum), FP32; the _rn intrinsics keep the
+// compiler from fusing these operations with a neighbouring multiply
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &err)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (uh + ul)(vh + vl) ~ p + e with p = fl(uh vh) and e its rounding error plus the
+// cross terms (the ul vl term, ~2^-48 of the product, is dropped)
+__device__ __forceinline__ void prod_df(float uh, float ul, float vh, float vl, float &p, float &e)
+{
+    p = __fmul_rn(uh, vh);
+    e = fmaf(uh, vh, -p);
+    e = fmaf(uh, vl, e);
+    e = fmaf(ul, vh, e);
+}
+
+__device__ __forceinline__ void acc_df(float &sh, float &sl, float p, float e)
+{
+    float s, err;
+    two_sum_f(sh, p, s, err);
+    sh = s;
+    sl += err + e;
+}
+
+// The GEMV of body_gemv_kernel in double-float on the FP32 pipe: A and y split into FP32
+// hi/lo pairs (split_df_kernel), each real product formed with its rounding error and
+// added by two-sum into a (hi, lo) accumulator; about 48 FP32 operations per complex
+// multiply-add instead of 4 FP64 ones (FP64 runs at 1/64 of the FP32 rate), relative
+// error about 1e-14 per term.  Used by the mixed path's restriction and recovery.
+__global__ void __launch_bounds__(256) body_gemv_df_kernel(int rows, int cols, int ms, int R,
+                                                           const long long *__restrict__ yoff,
+                                                           const long long *__restrict__ ooff,
+                                                           const float4 *__restrict__ A, const float4 *__restrict__ y,
+                                                           const double2 *__restrict__ sig, double alpha, double beta,
+                                                           double2 *__restrict__ out)
+{
+    __shared__ float4 ys[8][256];
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * GEMV_ROWS + (threadIdx.x >> 5);
+    const int ncol = ms * R;
+    for (int c0 = 0; c0 < ncol; c0 += 8) {
+        const int nc = min(8, ncol - c0);
+        float rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
+        for (int jc = 0; jc < cols; jc += 256) {
+            __syncthreads();
+            {
+                const int j = jc + threadIdx.x;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q < nc) {
+                        const int cc = c0 + q;
+                        ys[q][threadIdx.x] =
+                            j < cols ? y[(yoff[cc / R] + j) * R + cc % R] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+            __syncthreads();
+            if (i < rows) {
+                const int jn = min(256, cols - jc);
+#pragma unroll 2
+                for (int jj = lane; jj < jn; jj += 32) {
+                    const float4 a = A[(size_t)i * cols + jc + jj];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (q < nc) {
+                            const float4 v = ys[q][jj];
+                            float p, e;
+                            prod_df(a.x, a.z, v.x, v.z, p, e);          // ar yr
+                            acc_df(rh[q], rl[q], p, e);
+                            prod_df(-a.y, -a.w, v.y, v.w, p, e);        // - ai yi
+                            acc_df(rh[q], rl[q], p, e);
+                            prod_df(a.x, a.z, v.y, v.w, p, e);          // ar yi
+                            acc_df(ih[q], il[q], p, e);
+                            prod_df(a.y, a.w, v.x, v.z, p, e);          // ai yr
+                            acc_df(ih[q], il[q], p, e);
+                        }
+                    }
+                }
+            }
+        }
+        double sx[8], sy[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            sx[q] = (double)rh[q] + (double)rl[q];
+            sy[q] = (double)ih[q] + (double)il[q];
+            for (int o = 16; o > 0; o >>= 1) {
+                sx[q] += __shfl_xor_sync(0xffffffffu, sx[q], o);
+                sy[q] += __shfl_xor_sync(0xffffffffu, sy[q], o);
+            }
+        }
+        if (i < rows && lane < nc) {
+            double vx = 0.0, vy = 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q == lane) {
+                    vx = sx[q];
+                    vy = sy[q];
+                }
+            const int cc = c0 + lane;
+            const size_t o = (size_t)(ooff[cc / R] + i) * R + cc % R;
+            double2 res = make_double2(beta * vx, beta * vy);
+            if (alpha != 0.0) {
+                res.x += alpha * sig[o].x;
+                res.y += alpha * sig[o].y;
+            }
+            out[o] = res;
+        }
+    }
+}
+
 hzb_status reduced_local(hzb_ctx *c, int R, const double2 *y, const double2 *sigma, double alpha, double beta,
                          double2 *tau, bool fp32)
 {
@@ -1158,15 +1294,27 @@ hzb_status reduced_local(hzb_ctx *c, int R, const double2 *y, const double2 *sig
     return check_cuda(c, cudaGetLastError(), "reduced local operator");
 }
 
-// sig~ = s T w per body (restriction V_p^* of node vectors), out in reduced numbering
-static hzb_status restrict_all(hzb_ctx *c, int R, const double2 *w, double s, double2 *out)
+// sig~ = s T w per body (restriction V_p^* of node vectors), out in reduced numbering;
+// df: in double-float on the FP32 pipe (mixed path), else FP64
+static hzb_status restrict_all(hzb_ctx *c, int R, const double2 *w, double s, double2 *out, bool df)
 {
+    if (df) {
+        const size_t nw = (size_t)c->N * R;
+        if (check_cuda(c, c->ysplit.ensure(nw), "alloc")) return HZB_ENOMEM;
+        split_df_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, c->stream>>>(nw, w, c->ysplit.ptr);
+        c->launches++;
+    }
     for (ShapeDev *sp : c->shapes) {
         ShapeDev &sd = *sp;
         const int n = sd.geom.NG * sd.geom.NF;
-        body_gemv_kernel<false><<<gemv_blocks(sd.skel_k), 256, 0, c->stream>>>(sd.skel_k, n, (int)sd.bodies.size(), R,
-                                                                  sd.body_offs.ptr, sd.red_offs.ptr, sd.T64.ptr, w,
-                                                                  nullptr, 0.0, s, out);
+        if (df)
+            body_gemv_df_kernel<<<gemv_blocks(sd.skel_k), 256, 0, c->stream>>>(
+                sd.skel_k, n, (int)sd.bodies.size(), R, sd.body_offs.ptr, sd.red_offs.ptr, sd.Tdf.ptr, c->ysplit.ptr,
+                nullptr, 0.0, s, out);
+        else
+            body_gemv_kernel<false><<<gemv_blocks(sd.skel_k), 256, 0, c->stream>>>(
+                sd.skel_k, n, (int)sd.bodies.size(), R, sd.body_offs.ptr, sd.red_offs.ptr, sd.T64.ptr, w, nullptr,
+                0.0, s, out);
         c->launches++;
     }
     return check_cuda(c, cudaGetLastError(), "restrict");
@@ -1196,8 +1344,9 @@ hzb_status solve_reduced(hzb_ctx *c, int R, const double2 *v, const double2 *x0,
     hzb_status st;
     // v~ = T A^{-1} v per body; right-hand side -v~
     if ((st = local_inverse64(c, R, v, nullptr, 0.0, 1.0, c->w_a.ptr))) return st;
-    if ((st = restrict_all(c, R, c->w_a.ptr, -1.0, c->rb.ptr))) return st;
-    if (x0 && (st = restrict_all(c, R, x0, 1.0, c->rx.ptr))) return st;
+    const bool df = c->opt.precision != HZB_PREC_FP64;
+    if ((st = restrict_all(c, R, c->w_a.ptr, -1.0, c->rb.ptr, df))) return st;
+    if (x0 && (st = restrict_all(c, R, x0, 1.0, c->rx.ptr, df))) return st;
     hzb_stats rs{};
     hzb_status solve_st = solve_driver(r, R, nullptr, x0 ? c->rx.ptr : nullptr, &rs, c->rb.ptr);
     if (solve_st && solve_st != HZB_ENOCONV) return fail(c, solve_st, r->err);
@@ -1207,12 +1356,22 @@ hzb_status solve_reduced(hzb_ctx *c, int R, const double2 *v, const double2 *x0,
     // FP64 path: FP64; mixed path: double-float (about 1e-13 per term, far below its tolerance)
     st = c->opt.precision == HZB_PREC_FP64 ? interbody64(r, R, sig_t, r->s_r.ptr) : interbody_df(r, R, sig_t, r->s_r.ptr);
     if (st) return fail(c, st, r->err);
+    if (df) {
+        if (check_cuda(c, c->ysplit.ensure(std::max(RR, NR)), "alloc")) return HZB_ENOMEM;
+        split_df_kernel<<<(unsigned)((RR + 255) / 256), 256, 0, c->stream>>>(RR, r->s_r.ptr, c->ysplit.ptr);
+        c->launches++;
+    }
     for (ShapeDev *sp : c->shapes) {
         ShapeDev &sd = *sp;
         const int n = sd.geom.NG * sd.geom.NF;
-        body_gemv_kernel<false><<<gemv_blocks(n), 256, 0, c->stream>>>(n, sd.skel_k, (int)sd.bodies.size(), R, sd.red_offs.ptr,
-                                                          sd.body_offs.ptr, sd.U64.ptr, r->s_r.ptr, v, -1.0, -1.0,
-                                                          c->w_b.ptr);
+        if (df)
+            body_gemv_df_kernel<<<gemv_blocks(n), 256, 0, c->stream>>>(n, sd.skel_k, (int)sd.bodies.size(), R,
+                                                                      sd.red_offs.ptr, sd.body_offs.ptr, sd.Udf.ptr,
+                                                                      c->ysplit.ptr, v, -1.0, -1.0, c->w_b.ptr);
+        else
+            body_gemv_kernel<false><<<gemv_blocks(n), 256, 0, c->stream>>>(n, sd.skel_k, (int)sd.bodies.size(), R,
+                                                                          sd.red_offs.ptr, sd.body_offs.ptr, sd.U64.ptr,
+                                                                          r->s_r.ptr, v, -1.0, -1.0, c->w_b.ptr);
         c->launches++;
     }
     if (check_cuda(c, cudaGetLastError(), "extend")) return HZB_ECUDA;

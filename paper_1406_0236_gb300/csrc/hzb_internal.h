@@ -86,6 +86,7 @@ struct ShapeDev {
     std::vector<int> skel_J;              // skeleton nodes, shape-local, ascending
     DevBuf<double2> T64;                  // k x n row-major: V_p^* = T
     DevBuf<double2> U64;                  // n x k row-major: U_p = T^T
+    DevBuf<float4> Tdf, Udf;              // T and U split into FP32 (hi.re, hi.im, lo.re, lo.im)
     DevBuf<double2> St64;                 // k x k row-major: S_p = T A_pp^{-1} T^T
     DevBuf<float2> St32;                  // its FP32 copy
     DevBuf<long long> red_offs;           // first reduced-system node of each body of the shape
@@ -205,6 +206,7 @@ struct hzb_ctx {
     };
     std::vector<RShape> rshapes;               // reduced context: one per shape
     hzb::DevBuf<double2> rb, rx;               // reduced right-hand side and guess (parent)
+    hzb::DevBuf<float4> ysplit;                // a vector split into FP32 hi/lo (double-float GEMV)
     hzb::DevBuf<long long> zero_off;           // {0}: one body at offset 0
     // device timing of the inter-body kernels during a solve: event pairs
     std::vector<cudaEvent_t> evpool;
