@@ -308,32 +308,29 @@ __global__ void __launch_bounds__(1024) cpqr_pivot_kernel(int j, int m, int n, d
 // Step j: apply the reflector to every trailing column c > j and store the exact norm of
 // its rows j+1..m-1 as the column's new trailing norm.  One warp per column, eight per
 // block, no block-wide synchronisation: the column part j..m-1 is held in registers, W
-// values per lane, when it fits; W = 0 makes two passes over memory.  NW > 1 spreads a
-// column over NW warps with the sums shared in shared memory (64-128 thread blocks, one
-// column each); it measured slower than the two-pass form for 1,024-2,600 rows and is
-// not dispatched.  Grid (ceil((n-j-1)/8), batch) for NW = 1.
-template <int NW, int W>
+// values per lane, when it fits; W = 0 makes two passes over memory (spreading longer
+// columns over several warps with shared-memory sums measured slower).
+// Grid (ceil((n-j-1)/8), batch).
+template <int W>
 __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, double2 *__restrict__ A, size_t sA,
                                                           double *__restrict__ nrm2, const int *__restrict__ rank,
                                                           const double2 *__restrict__ u,
                                                           const double *__restrict__ beta)
 {
-    __shared__ double part[8][3];
     const int b = blockIdx.y;
     if (rank[b] >= 0) return;
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int c = NW == 1 ? j + 1 + blockIdx.x * 8 + wp : j + 1 + blockIdx.x;
-    const int r0 = j + (NW == 1 ? 0 : wp * 32 * W) + lane;      // this lane's first row
-    if (NW == 1 && c >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int c = j + 1 + blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= n) return;
     double2 *col = A + b * sA + (size_t)c * m;
     const double2 *ub = u + (size_t)b * m;
     const double bt = beta[b];
-    double sr = 0.0, si = 0.0;
+    double sr = 0.0, si = 0.0, nn = 0.0;
     if (W > 0) {
         double2 v[W > 0 ? W : 1];
 #pragma unroll
         for (int q = 0; q < (W > 0 ? W : 1); ++q) {
-            const int r = r0 + 32 * q;
+            const int r = j + lane + 32 * q;
             if (r < m) {
                 v[q] = col[r];
                 const double2 w = ub[r];
@@ -343,23 +340,10 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
         }
         sr = warp_sum(sr);
         si = warp_sum(si);
-        if (NW > 1) {
-            if (lane == 0) {
-                part[wp][0] = sr;
-                part[wp][1] = si;
-            }
-            __syncthreads();
-            sr = si = 0.0;
-            for (int q = 0; q < NW; ++q) {
-                sr += part[q][0];
-                si += part[q][1];
-            }
-        }
         const double fr = bt * sr, fi = bt * si;
-        double nn = 0.0;
 #pragma unroll
         for (int q = 0; q < (W > 0 ? W : 1); ++q) {
-            const int r = r0 + 32 * q;
+            const int r = j + lane + 32 * q;
             if (r < m) {
                 const double2 w = ub[r];
                 double2 a = v[q];
@@ -368,18 +352,6 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
                 col[r] = a;
                 if (r > j) nn += a.x * a.x + a.y * a.y;
             }
-        }
-        nn = warp_sum(nn);
-        if (NW > 1) {
-            if (lane == 0) part[wp][2] = nn;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double t = 0.0;
-                for (int q = 0; q < NW; ++q) t += part[q][2];
-                nrm2[(size_t)b * n + c] = t;
-            }
-        } else if (lane == 0) {
-            nrm2[(size_t)b * n + c] = nn;
         }
     } else {
         for (int r = j + lane; r < m; r += 32) {
@@ -390,7 +362,6 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
         sr = warp_sum(sr);
         si = warp_sum(si);
         const double fr = bt * sr, fi = bt * si;
-        double nn = 0.0;
         for (int r = j + lane; r < m; r += 32) {
             const double2 w = ub[r];
             double2 a = col[r];
@@ -399,9 +370,9 @@ __global__ void __launch_bounds__(256) cpqr_update_kernel(int j, int m, int n, d
             col[r] = a;
             if (r > j) nn += a.x * a.x + a.y * a.y;
         }
-        nn = warp_sum(nn);
-        if (lane == 0) nrm2[(size_t)b * n + c] = nn;
     }
+    nn = warp_sum(nn);
+    if (lane == 0) nrm2[(size_t)b * n + c] = nn;
 }
 
 // Column-pivoted QR of `batch` m x n column-major matrices (stride sA), in place, each
@@ -415,13 +386,13 @@ static hzb_status cpqr_run(hzb_ctx *c, int m, int n, int batch, double2 *A, size
         const int len = m - j, nc = n - j - 1;
         const dim3 g8((unsigned)((nc + 7) / 8), batch_);
         if (len <= 4 * 32)
-            cpqr_update_kernel<1, 4><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+            cpqr_update_kernel<4><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else if (len <= 16 * 32)
-            cpqr_update_kernel<1, 16><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+            cpqr_update_kernel<16><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else if (len <= 32 * 32)
-            cpqr_update_kernel<1, 32><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+            cpqr_update_kernel<32><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
         else
-            cpqr_update_kernel<1, 0><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
+            cpqr_update_kernel<0><<<g8, 256, 0, c->stream>>>(j, m, n, A, sA, nrm2, rank, u, beta);
     };
     ranks.assign(batch, -1);
     for (int j = 0; j < steps; ++j) {
