@@ -173,17 +173,22 @@ hzb_status hzb_build_scattering_matrices(hzb_ctx *ctx);
 
 /* Write the FP64 modal matrices A~_p and S_p (p = 0..M) of every distinct shape, with
  * k, eta and the shapes, to the file `path` (Sec. 3.2: the precomputation depends on
- * the shape and the wavenumber only, not on where the bodies sit).  Needs a built
- * context.  The format is this library's own (magic "HZBSCAT1", host byte order).
+ * the shape and the wavenumber only, not on where the bodies sit), and each shape's
+ * skeleton of the accelerated scheme when it has one (J, T, the reduced S_p and the
+ * proxy radius; Sec. 5: the ID is local to the shape).  Needs a built context.  The
+ * format is this library's own (magic "HZBSCAT1", version 3, host byte order).
  * Errors: HZB_ESTATE (not built), HZB_EINVAL (cannot write), HZB_ECUDA. */
 hzb_status hzb_save_scattering(hzb_ctx *ctx, const char *path);
 
 /* Instead of hzb_build_scattering_matrices: read the matrices written by
  * hzb_save_scattering for the same k, eta and the same list of distinct shapes (in
  * the order of their first hzb_add_body), then proceed as after a build.  The bodies'
- * positions and rotations may differ from the saving context's.  Errors: HZB_ESTATE
- * (no bodies, or already built), HZB_EINVAL (unreadable file, other version, or a
- * k / eta / shape mismatch: nothing is loaded), HZB_ENOMEM, HZB_ECUDA. */
+ * positions and rotations may differ from the saving context's.  Saved skeletons
+ * are restored where their proxy sphere still encloses every body of the shape and
+ * excludes all others (caller-given skeletons always); when every shape has one, the
+ * acceleration is on as after hzb_compress.  Version 2 files (no skeletons) load too.
+ * Errors: HZB_ESTATE (no bodies, or already built), HZB_EINVAL (unreadable file, other
+ * version, or a k / eta / shape mismatch: nothing is loaded), HZB_ENOMEM, HZB_ECUDA. */
 hzb_status hzb_load_scattering(hzb_ctx *ctx, const char *path);
 
 /* Autotuner of the inter-body kernels' launch shape (targets per thread, source

@@ -749,7 +749,8 @@ __global__ void split_df_kernel(size_t n, const double2 *__restrict__ a, float4 
 
 // Install J (any order, distinct) and T (device, k x n rows in J's order) as the shape's
 // skeleton with J ascending, and form its reduced blocks.
-static hzb_status install_skeleton(hzb_ctx *c, ShapeDev &sd, const std::vector<int> &J, DevBuf<double2> &T)
+hzb_status install_skeleton(hzb_ctx *c, ShapeDev &sd, const std::vector<int> &J, DevBuf<double2> &T,
+                            const double2 *S_host)
 {
     const int k = (int)J.size(), n = sd.geom.NG * sd.geom.NF;
     std::vector<int> order(k);
@@ -785,7 +786,16 @@ static hzb_status install_skeleton(hzb_ctx *c, ShapeDev &sd, const std::vector<i
     sd.skel_J.resize(k);
     for (int s = 0; s < k; ++s) sd.skel_J[s] = J[order[s]];
     sd.skel_k = k;
-    return reduced_blocks(c, sd);
+    if (!S_host) return reduced_blocks(c, sd);
+    const size_t kk = (size_t)k * k;
+    if (check_cuda(c, sd.St64.ensure(kk), "alloc S") || check_cuda(c, sd.St32.ensure(kk), "alloc S"))
+        return HZB_ENOMEM;
+    if (check_cuda(c, cudaMemcpyAsync(sd.St64.ptr, S_host, kk * sizeof(double2), cudaMemcpyHostToDevice, c->stream),
+                   "upload S"))
+        return HZB_ECUDA;
+    to_f32_kernel<<<(unsigned)((kk + 255) / 256), 256, 0, c->stream>>>(kk, sd.St64.ptr, sd.St32.ptr);
+    c->launches++;
+    return check_cuda(c, cudaStreamSynchronize(c->stream), "reduced blocks");
 }
 
 // Smallest distance from a body of the shape to another body's bounding sphere, and the
@@ -809,6 +819,13 @@ static void proxy_geometry(const hzb_ctx *c, int shape, double &rb, double &gap)
             gap = std::min(gap, d - rq);
         }
     }
+}
+
+bool proxy_fits(const hzb_ctx *c, int shape, double rho)
+{
+    double rb, gap;
+    proxy_geometry(c, shape, rb, gap);
+    return rho > rb && rho < gap;
 }
 
 static hzb_status compress_shape(hzb_ctx *c, int shape, double eps, int n_theta, double rho)
@@ -883,6 +900,7 @@ static hzb_status compress_shape(hzb_ctx *c, int shape, double eps, int n_theta,
     Z.release();
     st = install_skeleton(c, sd, J, T);
     T.release();
+    if (!st) sd.skel_rho = rho;
     return done(st);
 }
 
@@ -935,6 +953,7 @@ void release_compression(hzb_ctx *c)
         s->T64.release(); s->U64.release(); s->Tdf.release(); s->Udf.release(); s->St64.release();
         s->St32.release(); s->red_offs.release();
         s->skel_k = 0;
+        s->skel_rho = 0.0;
         s->skel_J.clear();
     }
     c->rb.release();
@@ -944,7 +963,7 @@ void release_compression(hzb_ctx *c)
 }
 
 // The reduced context over the skeleton nodes of every body (all shapes must have one).
-static hzb_status build_reduced(hzb_ctx *c)
+hzb_status build_reduced(hzb_ctx *c)
 {
     if (c->rctx) {
         hzb_ctx *r = c->rctx;
@@ -1438,6 +1457,7 @@ extern "C" hzb_status hzb_set_skeleton(hzb_ctx *c, int body, int k, const int *J
     if (!st) st = install_skeleton(c, sd, Jv, Td);
     Td.release();
     if (st) return st;
+    sd.skel_rho = 0.0;
     bool all = true;
     for (ShapeDev *s : c->shapes) all = all && s->skel_k > 0;
     if (all) {

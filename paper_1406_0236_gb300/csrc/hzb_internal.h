@@ -83,6 +83,7 @@ struct ShapeDev {
     bool tmA_ready = false;
     // accelerated scheme (compress.cu, Sec. 5): the shape's skeleton and reduced blocks
     int skel_k = 0;                       // skeleton size k (0: none)
+    double skel_rho = 0.0;                // proxy radius it was computed for (0: given by the caller)
     std::vector<int> skel_J;              // skeleton nodes, shape-local, ascending
     DevBuf<double2> T64;                  // k x n row-major: V_p^* = T
     DevBuf<double2> U64;                  // n x k row-major: U_p = T^T
@@ -273,6 +274,13 @@ hzb_status reduced_local(hzb_ctx *c, int R, const double2 *y, const double2 *sig
                          double beta, double2 *tau, bool fp32);
 hzb_status solve_reduced(hzb_ctx *c, int R, const double2 *v, const double2 *x0, hzb_stats *st);
 void release_compression(hzb_ctx *c);
+// install J (distinct, any order) and T (device, k x n, rows in J's order) for a shape; its
+// S_p from S_host (k x k, rows and columns in ascending J order) or computed when NULL
+hzb_status install_skeleton(hzb_ctx *c, ShapeDev &sd, const std::vector<int> &J, DevBuf<double2> &T,
+                            const double2 *S_host = nullptr);
+hzb_status build_reduced(hzb_ctx *c);
+// whether a proxy sphere of radius rho encloses every body of the shape and excludes the others
+bool proxy_fits(const hzb_ctx *c, int shape, double rho);
 
 // fields.cu
 hzb_status plane_waves(hzb_ctx *c, int R, const double *dirs_dev, double2 *v);

@@ -3,13 +3,21 @@
 // that shape at the same wavenumber), so that a later context skips the setup.
 //
 // File layout (little-endian, as the host writes it):
-//   char magic[8] = "HZBSCAT1"; int32 version = 2; int32 n_shapes;
+//   char magic[8] = "HZBSCAT1"; int32 version = 3; int32 n_shapes;
 //   double k, eta;
 //   per shape: hzb_shape spec (the struct as laid out by this library, padding zeroed),
 //              int32 NG, int32 M, int32 n_curve, n_curve doubles (the spline curve's
 //              (r, z) points, none for the analytic shapes), then (M+1) NG NG complex
 //              doubles of A~_p, then the same of S_p, p = 0..M, each matrix row-major
-//              (row = target ring).
+//              (row = target ring);
+//   then per shape the skeleton of the accelerated scheme (Sec. 5): int32 k (0: none),
+//              double rho (the proxy radius it was computed for, 0 if given by the
+//              caller); if k > 0: k int32 skeleton nodes (ascending), k n complex
+//              doubles of T (row-major), k k complex doubles of the reduced S_p.
+// Version 2 files (no skeleton section) load too.  A skeleton loads only where its
+// proxy sphere still separates the bodies of the new arrangement; when every shape
+// has one, the reduced system is built and solves use it.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -48,7 +56,7 @@ extern "C" hzb_status hzb_save_scattering(hzb_ctx *c, const char *path)
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(c, HZB_EINVAL, std::string("cannot open for writing: ") + path);
     bool ok = true;
-    const int version = 2, ns = (int)c->shapes.size();
+    const int version = 3, ns = (int)c->shapes.size();
     ok &= std::fwrite(HZB_SCAT_MAGIC, 1, 8, f) == 8;
     ok &= std::fwrite(&version, sizeof(int), 1, f) == 1;
     ok &= std::fwrite(&ns, sizeof(int), 1, f) == 1;
@@ -83,6 +91,27 @@ extern "C" hzb_status hzb_save_scattering(hzb_ctx *c, const char *path)
             ok &= std::fwrite(host.data(), sizeof(double2), nmat, f) == nmat;
         }
     }
+    for (int s = 0; s < ns && ok; ++s) {
+        const ShapeDev &sd = *c->shapes[s];
+        const int k = sd.skel_k, n = sd.geom.NG * sd.geom.NF;
+        ok &= std::fwrite(&k, sizeof(int), 1, f) == 1;
+        ok &= std::fwrite(&sd.skel_rho, sizeof(double), 1, f) == 1;
+        if (k == 0 || !ok) continue;
+        ok &= std::fwrite(sd.skel_J.data(), sizeof(int), k, f) == (size_t)k;
+        const size_t nt = (size_t)k * n, ns2 = (size_t)k * k;
+        host.resize(std::max(nt, ns2));
+        for (int which = 0; which < 2 && ok; ++which) {
+            const size_t cnt = which ? ns2 : nt;
+            const double2 *src = which ? sd.St64.ptr : sd.T64.ptr;
+            if (check_cuda(c, cudaMemcpyAsync(host.data(), src, cnt * sizeof(double2), cudaMemcpyDeviceToHost,
+                                              c->stream), "copy skeleton") ||
+                check_cuda(c, cudaStreamSynchronize(c->stream), "copy skeleton")) {
+                std::fclose(f);
+                return HZB_ECUDA;
+            }
+            ok &= std::fwrite(host.data(), sizeof(double2), cnt, f) == cnt;
+        }
+    }
     ok &= std::fclose(f) == 0;
     if (!ok) return fail(c, HZB_EINVAL, std::string("write failed: ") + path);
     return HZB_OK;
@@ -100,7 +129,7 @@ extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
     int version = 0, ns = 0;
     double k = 0.0, eta = 0.0;
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, HZB_SCAT_MAGIC, 8) == 0;
-    ok = ok && std::fread(&version, sizeof(int), 1, f) == 1 && version == 2;
+    ok = ok && std::fread(&version, sizeof(int), 1, f) == 1 && (version == 2 || version == 3);
     ok = ok && std::fread(&ns, sizeof(int), 1, f) == 1 && std::fread(&k, sizeof(double), 1, f) == 1 &&
          std::fread(&eta, sizeof(double), 1, f) == 1;
     if (!ok) {
@@ -152,11 +181,80 @@ extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
             return HZB_ECUDA;
         }
     }
-    std::fclose(f);
     hzb_status st = make_nodes(c);
-    if (st) return st;
-    if (check_cuda(c, cudaStreamSynchronize(c->stream), "load")) return HZB_ECUDA;
+    if (st) {
+        std::fclose(f);
+        return st;
+    }
+    if (check_cuda(c, cudaStreamSynchronize(c->stream), "load")) {
+        std::fclose(f);
+        return HZB_ECUDA;
+    }
     c->t_setup_ms = 0.0;
     c->state = 3;
+    if (version == 3) {
+        // skeletons: each is restored where its proxy sphere still fits the arrangement
+        bool all = true;
+        for (int s = 0; s < ns; ++s) {
+            ShapeDev &sd = *c->shapes[s];
+            const int n = sd.geom.NG * sd.geom.NF;
+            int k = 0;
+            double rho = 0.0;
+            if (std::fread(&k, sizeof(int), 1, f) != 1 || std::fread(&rho, sizeof(double), 1, f) != 1 || k < 0 ||
+                k > n) {
+                std::fclose(f);
+                release_compression(c);
+                return fail(c, HZB_EINVAL, "file ends early or holds a bad skeleton size");
+            }
+            if (k == 0) {
+                all = false;
+                continue;
+            }
+            std::vector<int> J(k);
+            std::vector<double2> T((size_t)k * n), S((size_t)k * k);
+            if (std::fread(J.data(), sizeof(int), k, f) != (size_t)k ||
+                std::fread(T.data(), sizeof(double2), T.size(), f) != T.size() ||
+                std::fread(S.data(), sizeof(double2), S.size(), f) != S.size()) {
+                std::fclose(f);
+                release_compression(c);
+                return fail(c, HZB_EINVAL, "file ends early");
+            }
+            bool valid = std::is_sorted(J.begin(), J.end()) && J.front() >= 0 && J.back() < n &&
+                         std::adjacent_find(J.begin(), J.end()) == J.end();
+            if (!valid) {
+                std::fclose(f);
+                release_compression(c);
+                return fail(c, HZB_EINVAL, "bad skeleton indices in the file");
+            }
+            if (rho > 0.0 && !proxy_fits(c, s, rho)) {
+                all = false;
+                continue;
+            }
+            DevBuf<double2> Td;
+            if (check_cuda(c, Td.ensure(T.size()), "alloc T")) {
+                std::fclose(f);
+                return HZB_ENOMEM;
+            }
+            st = check_cuda(c, cudaMemcpyAsync(Td.ptr, T.data(), T.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                                               c->stream), "upload T");
+            if (!st) st = install_skeleton(c, sd, J, Td, S.data());
+            Td.release();
+            if (st) {
+                std::fclose(f);
+                release_compression(c);
+                return st;
+            }
+            sd.skel_rho = rho;
+        }
+        if (all) {
+            if ((st = build_reduced(c))) {
+                std::fclose(f);
+                release_compression(c);
+                return st;
+            }
+            c->accel = true;
+        }
+    }
+    std::fclose(f);
     return HZB_OK;
 }

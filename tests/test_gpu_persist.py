@@ -71,3 +71,37 @@ def test_load_refuses_mismatch(tmp_path):
     with pytest.raises(HzbError):
         u.load_scattering(str(bad))
     u.load_scattering(path)                               # a refused load left the context usable
+
+
+def test_skeletons_saved_and_restored(tmp_path):
+    """The accelerated scheme's skeletons travel with the matrices: a loaded context
+    solves the reduced system like the compressing one; moved so close that the saved
+    proxy sphere no longer separates the bodies, the skeletons are left out and the
+    direct solve runs."""
+    require_gpu()
+    from paper_1406_0236_gb300 import Options, Solver
+    wl = W.separated_spheroids(spacing=4.0, n_panels=6, gl_order=8, n_modes=21)
+    s = gpu_solver(wl, precision=0, tol=1e-12)
+    s.compress(1e-10)
+    path = str(tmp_path / "scat_skel.bin")
+    s.save_scattering(path)
+    s.solve_plane_waves(wl.directions)
+    ref = s.get_density().copy()
+    loaded = Solver.from_workload(wl, Options(precision=0, gmres_tol=1e-12))
+    loaded.load_scattering(path)
+    assert loaded.reduced_size == s.reduced_size
+    J0, T0 = s.get_skeleton(0)
+    J1, T1 = loaded.get_skeleton(0)
+    assert np.array_equal(J0, J1) and np.array_equal(T0, T1)
+    loaded.solve_plane_waves(wl.directions)
+    assert rel_l2(loaded.get_density(), ref) < 1e-13
+    # bodies pushed together: the proxy sphere of the file would cut a neighbour
+    close = [W.Body(b.shape, b.center * 0.55, b.rot) for b in wl.bodies]
+    cw = W.Workload("close", close, wl.k, wl.eta, wl.directions)
+    t = Solver.from_workload(cw, Options(precision=0, gmres_tol=1e-12))
+    t.load_scattering(path)
+    assert t.reduced_size == 0 and t.get_skeleton(0) is None
+    t.solve_plane_waves(cw.directions)
+    fresh = gpu_solver(cw, precision=0, tol=1e-12)
+    fresh.solve_plane_waves(cw.directions)
+    assert rel_l2(t.get_density(), fresh.get_density()) < 1e-12
