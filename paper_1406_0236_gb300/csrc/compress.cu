@@ -997,7 +997,15 @@ hzb_status build_reduced(hzb_ctx *c)
         const long long o = (long long)gidx.size();
         offs[br.shape].push_back(o);
         for (int s : sd.skel_J) gidx.push_back(br.offset + s);
-        split_target_blocks(o, sd.skel_k, blocks);
+        const int k = sd.skel_k;
+        for (int s = 0; s < k; s += 512) {
+            TargetBlock t;
+            t.start = (int)(o + s);
+            t.count = std::min(512, k - s);
+            t.excl_lo = (int)o;
+            t.excl_hi = (int)(o + k);
+            blocks.push_back(t);
+        }
     }
     const long long nr = (long long)gidx.size();
     r->N = nr;

@@ -226,8 +226,6 @@ hzb_status check_cuda(hzb_ctx *c, cudaError_t e, const char *what);
 
 // setup.cu
 hzb_status make_nodes(hzb_ctx *c);
-// TargetBlocks of one body (nodes offset .. offset+n-1): ceil(n/512) blocks of equal size
-void split_target_blocks(long long offset, int n, std::vector<TargetBlock> &blocks);
 hzb_status build_shape_matrices(hzb_ctx *c, ShapeDev &s);
 
 // nbody.cu: y = B sigma; sigma, y device N x R complex FP64 (FP32 path converts internally)

@@ -80,22 +80,6 @@ __global__ void body_nodes_kernel(int NG, int NF, const double *__restrict__ rin
     body_of[g] = body;
 }
 
-void split_target_blocks(long long offset, int n, std::vector<TargetBlock> &blocks)
-{
-    const int TB = 512;
-    const int nb = (n + TB - 1) / TB;
-    int s = 0;
-    for (int q = 0; q < nb; ++q) {
-        TargetBlock t;
-        t.start = (int)(offset + s);
-        t.count = n / nb + (q < n % nb ? 1 : 0);
-        t.excl_lo = (int)offset;
-        t.excl_hi = (int)(offset + n);
-        blocks.push_back(t);
-        s += t.count;
-    }
-}
-
 hzb_status make_nodes(hzb_ctx *c)
 {
     if (c->nodes_ready) return HZB_OK;
@@ -146,11 +130,19 @@ hzb_status make_nodes(hzb_ctx *c)
                                                     c->nrm32.ptr, c->body_of.ptr);
         if (check_cuda(c, cudaGetLastError(), "body_nodes_kernel")) return HZB_ECUDA;
     }
-    // target blocks of the inter-body sum: contiguous ranges inside one body, at most 512
-    // nodes, each body split into blocks of equal size (within one) so that no block pair
-    // of a pair-symmetric kernel runs a nearly empty block against a full one
+    // target blocks of the inter-body sum: contiguous ranges inside one body
+    const int TB = 512;
     std::vector<TargetBlock> blocks;
-    for (const BodyRec &b : c->bodies) split_target_blocks(b.offset, b.n_nodes, blocks);
+    for (const BodyRec &b : c->bodies) {
+        for (int s = 0; s < b.n_nodes; s += TB) {
+            TargetBlock t;
+            t.start = (int)(b.offset + s);
+            t.count = std::min(TB, b.n_nodes - s);
+            t.excl_lo = (int)b.offset;
+            t.excl_hi = (int)(b.offset + b.n_nodes);
+            blocks.push_back(t);
+        }
+    }
     c->n_tblocks = (int)blocks.size();
     if (check_cuda(c, c->tblocks.ensure(blocks.size()), "alloc blocks")) return HZB_ENOMEM;
     if (check_cuda(c, cudaMemcpyAsync(c->tblocks.ptr, blocks.data(), blocks.size() * sizeof(TargetBlock),
