@@ -336,10 +336,14 @@ hzb_status ensure_block_pairs(hzb_ctx *c)
                                       cudaMemcpyDeviceToHost, c->stream), "copy blocks") ||
         check_cuda(c, cudaStreamSynchronize(c->stream), "copy blocks"))
         return HZB_ECUDA;
+    // the CTA's threads own the targets of pair.x and step through the sources of pair.y:
+    // the larger block goes first, so a body's short last block is always the source side
+    // (a short CTA) and never leaves most of a CTA's threads idle for a full pass
     std::vector<int2> pr;
     for (int i = 0; i < (int)tb.size(); ++i)
         for (int j = i + 1; j < (int)tb.size(); ++j)
-            if (tb[i].excl_lo != tb[j].excl_lo) pr.push_back(make_int2(i, j));
+            if (tb[i].excl_lo != tb[j].excl_lo)
+                pr.push_back(tb[j].count > tb[i].count ? make_int2(j, i) : make_int2(i, j));
     if (pr.empty()) {
         c->n_blockpairs = -1;                   // one body: B = 0
         return HZB_OK;
