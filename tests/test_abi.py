@@ -16,7 +16,10 @@ def test_header_declares_the_boundary():
     names = set(declared_symbols())
     for n in ("hzb_create", "hzb_destroy", "hzb_set_wave", "hzb_add_body", "hzb_build_scattering_matrices",
               "hzb_solve_plane_waves", "hzb_solve_data", "hzb_get_density", "hzb_far_field", "hzb_apply",
-              "hzb_interbody", "hzb_local_inverse", "hzb_eval_field", "hzb_last_error"):
+              "hzb_interbody", "hzb_local_inverse", "hzb_eval_field", "hzb_last_error",
+              "hzb_save_scattering", "hzb_load_scattering", "hzb_add_body_curve",
+              "hzb_compress", "hzb_set_skeleton", "hzb_get_skeleton", "hzb_set_acceleration",
+              "hzb_reduced_size", "hzb_apply_reduced", "hzb_interp_decomp"):
         assert n in names
 
 
