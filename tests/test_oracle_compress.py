@@ -110,3 +110,48 @@ def test_green_identity_through_compressed_solve(wl, P):
     u = fields.field(P.nodes, sig, wl.k, wl.eta, tg)
     ue = fields.point_source_field(tg, src, wl.k)
     assert np.abs(u - ue).max() < 1e-8 * np.abs(ue).max()
+
+
+def test_fourier_route_to_the_id(P):
+    """Reading P21 (the GPU's route to the ID), checked on the mathematics alone: the
+    proxy matrix M is block-circulant in the azimuth (each block is (1/N_F) F^* diag(M^_p) F
+    with M^_p = M^_{-p}); truncating a pivoted QR of every M^_p at 0.3 eps |M|_col and
+    stacking the rows R_p[s, i] e^{-2 pi i p l / N_F} / sqrt(N_F) gives Z with |Zx| ~ |Mx|
+    for all x, so the ID of Z reproduces M to about eps."""
+    import scipy.linalg as sla
+    from oracle.compress import default_proxy_radius, proxy_matrix, proxy_sphere, shape_nodes
+    shp = P.wl.bodies[0].shape
+    rg = P.rings[shp]
+    nf, ng = shp.n_modes, rg.n
+    nt = max(16, int(np.ceil(1.2 * ng)))
+    x, n, w = shape_nodes(rg, nf)
+    z, nz = proxy_sphere(nf, default_proxy_radius(P.wl, shp), nt)
+    M = proxy_matrix(x, n, w, z, nz, P.k, P.eta)                    # (3 nt nf) x (ng nf)
+    # rows (b, r, a), columns (i, l): M[(b, r, a), (i, l)] = f_{b r i}(a - l)
+    f = M.reshape(3, nt, nf, ng, nf)[:, :, :, :, 0]                  # l = 0: f(a)
+    Mh = np.fft.fft(f, axis=2)                                       # sum_a f(a) e^{-2 pi i p a / nf}
+    Mh = np.moveaxis(Mh, 2, 0).reshape(nf, 3 * nt, ng)               # mode index p mod nf
+    for p in range(1, (nf - 1) // 2 + 1):
+        assert np.allclose(Mh[p], Mh[nf - p], atol=1e-12 * np.abs(Mh).max())
+    colmax = np.sqrt((np.abs(M) ** 2).sum(0).max())
+    eps = 1e-8
+    rows = []
+    l = np.arange(nf)
+    for p in range(nf):
+        _, R, piv = sla.qr(Mh[p], mode="economic", pivoting=True)
+        trail = np.array([np.linalg.norm(R[s:, s:], axis=0).max() for s in range(R.shape[0])] + [0.0])
+        r = int(np.argmax(trail <= 0.3 * eps * colmax))
+        Zp = np.zeros((r, ng), dtype=complex)
+        Zp[:, piv] = R[:r]
+        ph = np.exp(-2j * np.pi * p * l / nf) / np.sqrt(nf)
+        rows.append((Zp[:, :, None] * ph[None, None, :]).reshape(r, ng * nf))
+    Z = np.vstack(rows)
+    assert Z.shape[0] < 0.8 * M.shape[1]
+    g = np.random.default_rng(2)
+    X = g.standard_normal((M.shape[1], 6)) + 1j * g.standard_normal((M.shape[1], 6))
+    nm, nzx = np.linalg.norm(M @ X, axis=0), np.linalg.norm(Z @ X, axis=0)
+    assert np.abs(nm - nzx).max() < 1e-3 * eps * colmax * np.linalg.norm(X, axis=0).max()
+    from oracle.compress import interpolative_decomposition
+    idd = interpolative_decomposition(Z, eps)
+    err = np.linalg.norm(M - M[:, idd.J] @ idd.T, 2)
+    assert err < 3 * eps * np.linalg.norm(M, 2)
