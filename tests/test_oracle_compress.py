@@ -155,3 +155,41 @@ def test_fourier_route_to_the_id(P):
     idd = interpolative_decomposition(Z, eps)
     err = np.linalg.norm(M - M[:, idd.J] @ idd.T, 2)
     assert err < 3 * eps * np.linalg.norm(M, 2)
+
+
+@pytest.mark.parametrize("kind,q", [("sphere", 1), ("shell", 3), ("spline", 1)])
+def test_factorisation_for_other_shape_kinds(kind, q):
+    """Eq. (ip0) on the dense blocks for the other generating curves: a sphere, an open
+    shell (whose cavity lies inside the proxy sphere with the body) and a spline pear.
+    The shell at N_F = 17 needs the proxy sampled at 3 N_F azimuths (q = 3): at N_F
+    azimuths its off-diagonal blocks keep an error floor near 1e-6."""
+    import math
+    if kind == "sphere":
+        shp = W.ShapeSpec(W.SPHERE, (0.8,), 5, 8, 17)
+    elif kind == "shell":
+        shp = W.ShapeSpec(W.OPEN_SHELL, (1.0, 0.8, math.radians(60.0), 0.1), 12, 6, 17)
+    else:
+        pts = W.pear_curve(7)
+        shp = W.ShapeSpec(W.CURVE_SPLINE, pts, 6, 8, 17)
+    rot = [W.rotation_taking_z_to(a) for a in ([0.3, 0.2, 1.0], [1.0, -0.4, 0.2], [-0.2, 1.0, 0.5])]
+    cen = [np.array([0.0, 0.0, 0.0]), np.array([4.2, 0.5, -0.3]), np.array([1.5, 3.9, 0.8])]
+    wl = W.Workload(kind, [W.Body(shp, c, r) for c, r in zip(cen, rot)], 2.0, 2.0, np.array([[0.0, 0.0, 1.0]]))
+    P = Problem(wl)
+    D = P.dense_matrix()
+    sl = P.body_slices()
+
+    def worst(C):
+        idd = C.ids[shp]
+        w = 0.0
+        for p in range(3):
+            for r in range(3):
+                if p != r:
+                    A = D[sl[p], sl[r]]
+                    w = max(w, np.linalg.norm(A - idd.T.T @ A[np.ix_(idd.J, idd.J)] @ idd.T) / np.linalg.norm(A))
+        return idd.rank, w
+
+    eps = 1e-9
+    rank, err = worst(Compressed(P, eps, q=q))
+    assert rank < shp.n_nodes and err < eps, (kind, rank, err)
+    if kind == "shell":
+        assert worst(Compressed(P, eps, q=1))[1] > 100 * eps     # the floor that q = 3 removes
