@@ -193,3 +193,60 @@ def test_factorisation_for_other_shape_kinds(kind, q):
     assert rank < shp.n_nodes and err < eps, (kind, rank, err)
     if kind == "shell":
         assert worst(Compressed(P, eps, q=1))[1] > 100 * eps     # the floor that q = 3 removes
+
+
+def test_fourier_route_with_offset_proxy_rings():
+    """The route of reading P21 with the proxy sampled at 3 N_F azimuths (q = 3): the
+    points fall in three classes of N_F azimuths offset by 0, +1/3 and +2/3 (= -1/3 of the
+    next) of the azimuthal step, each class block-circulant; M^_{-p} and M^_p then have the
+    same Gram matrix (the +-1/3 classes trade places), so one pivoted QR per |p| still
+    gives Z with |Zx| ~ |Mx|, and the ID of Z meets eps on the open shell where q = 1 does
+    not."""
+    import math
+    import scipy.linalg as sla
+    from oracle.compress import default_proxy_radius, interpolative_decomposition, proxy_matrix, proxy_sphere, \
+        shape_nodes
+    shp = W.ShapeSpec(W.OPEN_SHELL, (1.0, 0.8, math.radians(60.0), 0.1), 12, 6, 17)
+    rot = [W.rotation_taking_z_to(a) for a in ([0.3, 0.2, 1.0], [1.0, -0.4, 0.2], [-0.2, 1.0, 0.5])]
+    cen = [np.array([0.0, 0.0, 0.0]), np.array([4.2, 0.5, -0.3]), np.array([1.5, 3.9, 0.8])]
+    wl = W.Workload("shell", [W.Body(shp, c, r) for c, r in zip(cen, rot)], 2.0, 2.0, np.array([[0.0, 0.0, 1.0]]))
+    P = Problem(wl)
+    rg = P.rings[shp]
+    nf, ng, q = shp.n_modes, rg.n, 3
+    nt = max(16, int(np.ceil(1.2 * ng)))
+    x, n, w = shape_nodes(rg, nf)
+    z, nz = proxy_sphere(nf, default_proxy_radius(wl, shp), nt, q)
+    M = proxy_matrix(x, n, w, z, nz, P.k, P.eta)                       # rows (blk, r, b), b < q nf
+    f = M.reshape(3, nt, q * nf, ng, nf)[:, :, :, :, 0]                # node azimuth l = 0
+    f = f.reshape(3, nt, nf, q, ng)                                     # b = q a + t
+    Mh = np.fft.fft(f, axis=2)                                          # DFT over a, per class t
+    Mh = np.moveaxis(Mh, 2, 0).reshape(nf, 3 * nt * q, ng)
+    for p in range(1, (nf - 1) // 2 + 1):                              # same Gram matrix for +-p
+        G1, G2 = Mh[p].conj().T @ Mh[p], Mh[nf - p].conj().T @ Mh[nf - p]
+        assert np.abs(G1 - G2).max() < 1e-11 * np.abs(G1).max()
+    colmax = np.sqrt((np.abs(M) ** 2).sum(0).max())
+    eps = 1e-9
+    l = np.arange(nf)
+    rows = []
+    for p in range(nf):
+        pp = p if p <= (nf - 1) // 2 else nf - p                         # one QR per |p|
+        _, R, piv = sla.qr(Mh[pp], mode="economic", pivoting=True)
+        trail = np.array([np.linalg.norm(R[s:, s:], axis=0).max() for s in range(R.shape[0])] + [0.0])
+        r = int(np.argmax(trail <= 0.3 * eps * colmax))
+        Zp = np.zeros((r, ng), dtype=complex)
+        Zp[:, piv] = R[:r]
+        ph = np.exp(-2j * np.pi * p * l / nf) / np.sqrt(nf)
+        rows.append((Zp[:, :, None] * ph[None, None, :]).reshape(r, ng * nf))
+    Z = np.vstack(rows)
+    g = np.random.default_rng(3)
+    X = g.standard_normal((M.shape[1], 6)) + 1j * g.standard_normal((M.shape[1], 6))
+    nm, nzx = np.linalg.norm(M @ X, axis=0), np.linalg.norm(Z @ X, axis=0)
+    assert np.abs(nm - nzx).max() < 1e-3 * eps * colmax * np.linalg.norm(X, axis=0).max()
+    idd = interpolative_decomposition(Z, eps)
+    D = P.dense_matrix()
+    sl = P.body_slices()
+    for a in range(3):
+        for b in range(3):
+            if a != b:
+                A = D[sl[a], sl[b]]
+                assert np.linalg.norm(A - idd.T.T @ A[np.ix_(idd.J, idd.J)] @ idd.T) < eps * np.linalg.norm(A)
