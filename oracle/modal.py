@@ -165,20 +165,28 @@ def near_panel_entries(rg: Rings, i: int, b: int, k: float, eta: float, M: int) 
     return np.einsum("s,sj,sp->pj", wt * r * sp, Lb, modes)
 
 
+def _modal_row(rg: Rings, i: int, k: float, eta: float, M: int) -> np.ndarray:
+    """Row i of K_p for p = 0..M as (M+1, N_G): far panels by the trapezoid rule of
+    C3 (Eq. (nystromnaive) per mode), near panels by product integration (C4)."""
+    row = np.zeros((M + 1, rg.n), dtype=np.complex128)
+    nb = near_panels(rg, i)
+    far = np.nonzero(~np.isin(rg.panel, nb))[0]
+    if far.size:
+        md = _modes_trapezoid(rg, i, far, k, eta, M)
+        row[:, far] = (md * (rg.r[far] * rg.ds[far])[:, None]).T
+    for b in nb:
+        row[:, rg.panel_nodes(b)] = near_panel_entries(rg, i, b, k, eta, M)
+    return row
+
+
 def modal_matrices(rg: Rings, k: float, eta: float, M: Optional[int] = None) -> np.ndarray:
-    """K_p for p = 0..M as an (M+1, N_G, N_G) complex array."""
+    """K_p for p = 0..M as an (M+1, N_G, N_G) complex array (row i depends only on
+    target ring i)."""
     if M is None:
         M = (rg.shape.n_modes - 1) // 2
-    NG = rg.n
-    K = np.zeros((M + 1, NG, NG), dtype=np.complex128)
-    for i in range(NG):
-        nb = near_panels(rg, i)
-        far = np.nonzero(~np.isin(rg.panel, nb))[0]
-        if far.size:
-            md = _modes_trapezoid(rg, i, far, k, eta, M)
-            K[:, i, far] = (md * (rg.r[far] * rg.ds[far])[:, None]).T
-        for b in nb:
-            K[:, i, rg.panel_nodes(b)] = near_panel_entries(rg, i, b, k, eta, M)
+    K = np.zeros((M + 1, rg.n, rg.n), dtype=np.complex128)
+    for i in range(rg.n):
+        K[:, i, :] = _modal_row(rg, i, k, eta, M)
     return K
 
 
@@ -206,19 +214,13 @@ def cached_scattering(rg: Rings, k: float, eta: float) -> np.ndarray:
 
 def modal_rows(rg: Rings, rows, k: float, eta: float, M: Optional[int] = None) -> np.ndarray:
     """Rows i in `rows` of A~_p = 1/2 I + K_p for p = 0..M, as (M+1, len(rows), N_G):
-    the same entries modal_matrices builds, computed only for the requested targets
-    (row i depends only on target ring i)."""
+    the rows modal_system builds (same per-row routine), computed only for the
+    requested targets."""
     if M is None:
         M = (rg.shape.n_modes - 1) // 2
     rows = np.atleast_1d(rows)
     out = np.zeros((M + 1, rows.size, rg.n), dtype=np.complex128)
     for a, i in enumerate(rows):
-        nb = near_panels(rg, int(i))
-        far = np.nonzero(~np.isin(rg.panel, nb))[0]
-        if far.size:
-            md = _modes_trapezoid(rg, int(i), far, k, eta, M)
-            out[:, a, far] = (md * (rg.r[far] * rg.ds[far])[:, None]).T
-        for b in nb:
-            out[:, a, rg.panel_nodes(b)] = near_panel_entries(rg, int(i), b, k, eta, M)
+        out[:, a, :] = _modal_row(rg, int(i), k, eta, M)
         out[:, a, int(i)] += 0.5
     return out

@@ -15,7 +15,7 @@ from scipy import integrate, special
 import oracle._native as nat
 import workloads as W
 from oracle import fields, rings
-from oracle.modal import modal_system, modes_graded, modes_trapezoid_at
+from oracle.modal import modal_rows, modal_system, modes_graded, modes_trapezoid_at
 
 
 def _quad_mode(r, rs, dr, dz, nr, nz, k, eta, p):
@@ -83,3 +83,35 @@ def test_sphere_eigenvalues(k, eta):
             lam = fields.sphere_eigenvalue(n, a, k, eta)
             err = np.abs(A[m] @ P - lam * P).max() / np.abs(lam * P).max()
             assert err < 1e-11, (m, n, err)
+
+
+def test_modal_rows_pinned_by_sphere_eigenvalues():
+    """modal_rows on its own (the checker of the full-size setup tests): its rows of
+    A~_m, applied to P_n^m(cos t) at the ring nodes, give lambda_n P_n^m at those rows,
+    the exact sphere eigenvalue; a dropped 1/2 I, a wrong near-panel set or a wrong
+    weight moves the result by far more than the tolerance."""
+    a, k, eta = 1.0, 2.0, 2.0
+    rg = rings(W.ShapeSpec(W.SPHERE, (a,), 8, 10, 13))
+    rows = np.array([0, 9, 33, 79])
+    Ar = modal_rows(rg, rows, k, eta)
+    ct = np.cos(rg.t)
+    for m in (0, 2, 6):
+        for n in (m, m + 1):
+            P = special.lpmv(m, n, ct)
+            lam = fields.sphere_eigenvalue(n, a, k, eta)
+            err = np.abs(Ar[m] @ P - lam * P[rows]).max() / np.abs(lam * P).max()
+            assert err < 1e-11, (m, n, err)
+
+
+@pytest.mark.parametrize("spec", [W.ShapeSpec(W.SPHEROID, (1.0, 2.0), 4, 6, 9),
+                                  W.ShapeSpec(W.OPEN_SHELL, (1.0, 0.8, np.pi / 3, 0.1), 6, 5, 9)])
+def test_modal_rows_equal_modal_system_rows(spec):
+    """The requested rows of modal_system, with the 1/2 on the diagonal, for a
+    spheroid and an open shell (where the near-panel set crosses the rim)."""
+    k, eta = 3.0, 3.0
+    rg = rings(spec)
+    A = modal_system(rg, k, eta)
+    rows = np.array([0, rg.n // 3, rg.n - 1])
+    Ar = modal_rows(rg, rows, k, eta)
+    assert Ar.shape == (A.shape[0], rows.size, rg.n)
+    assert np.abs(Ar - A[:, rows, :]).max() <= 1e-15 * np.abs(A).max()
