@@ -55,6 +55,24 @@ typedef enum {
     HZB_ESTATE = -7      /* call out of order */
 } hzb_status;
 
+/* Failure detection.  GMRES reports a non-finite residual as HZB_ENAN (a NaN or Inf in
+ * the data, the guess or the operator), and non-convergence as HZB_ENOCONV.  Every
+ * wait of a kernel on an mbarrier is bounded: when one runs out the kernel frees its
+ * tensor memory, writes NaN to its outputs and sets a flag that the call reports as
+ * HZB_ETIMEOUT (the flag is then cleared, so the context stays usable).  Geometry is
+ * checked when the nodes are generated: intersecting bodies and non-finite or
+ * degenerate nodes give HZB_EINVAL.
+ *
+ * Host fault injection, for tests of these paths: the environment variable HZB_FAULT,
+ * read by hzb_create, is a comma-separated list of
+ *   alloc    every device allocation of the context fails (HZB_ENOMEM);
+ *   geom     the first node generation writes a NaN weight (HZB_EINVAL);
+ *   nan      the first solve's preconditioned right-hand side gets a NaN (HZB_ENAN);
+ *   timeout  the first tcgen05 inter-body launch (FP32 engine 5) finds its error flag
+ *            set before it starts and takes its timeout exit before issuing any MMA
+ *            (HZB_ETIMEOUT).
+ * The last three fire once per context.  Nothing is injected on the GPU itself. */
+
 typedef enum {
     HZB_PREC_FP64 = 0,        /* every kernel in FP64 */
     HZB_PREC_MIXED_FP32 = 1,  /* FP64 outer refinement, FP32 inter-body sum and modal apply inside */
@@ -267,7 +285,8 @@ hzb_status hzb_interbody(hzb_ctx *ctx, int R, const double *sigma, double *y,
                          int on_device, int precision);
 
 /* tau = alpha * sigma + beta * D^{-1} y (the per-body FFT -> S_p -> inverse FFT of
- * the Remark after Eq. (precond)).  sigma may be NULL when alpha = 0. */
+ * the Remark after Eq. (precond)).  sigma may be NULL when alpha = 0.  Always the
+ * direct D^{-1} on all N nodes, also while the accelerated scheme is on. */
 hzb_status hzb_local_inverse(hzb_ctx *ctx, int R, const double *y, const double *sigma,
                              double alpha, double beta, double *tau, int on_device,
                              int precision);
@@ -281,7 +300,8 @@ hzb_status hzb_local_inverse(hzb_ctx *ctx, int R, const double *y, const double 
  * a shape's mode panel (M+1) x N_G x (2 m_s R) exceeds 524,288 complex values.  All
  * calls on a device share that array: calls that overlap on the GPU race.  The first
  * call on a device looks up the array's address; make it before any stream capture.
- * The paper has no counterpart of this entry point. */
+ * Like hzb_local_inverse, it applies the direct D^{-1}, also while the accelerated
+ * scheme is on.  The paper has no counterpart of this entry point. */
 hzb_status hzb_local_inverse_noalloc(hzb_ctx *ctx, int R, const double *y, const double *sigma,
                                      double alpha, double beta, double *tau);
 

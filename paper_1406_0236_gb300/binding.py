@@ -161,6 +161,32 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+
+def check_device_vectors(N: int, device: int, first, *others, expect_cuda: bool = True):
+    """Raise ValueError unless `first` and every non-None tensor in `others` is a
+    contiguous complex128 tensor of shape (N,) or (N, R), all of the same shape, on
+    CUDA device `device` (expect_cuda=False checks CPU tensors the same way, for
+    tests on machines without a GPU).  The C entry points take raw device addresses
+    and trust the sizes, so a short, strided or complex64 tensor would make the
+    kernels read and write outside the caller's buffers."""
+    import torch
+    for t in (first,) + tuple(x for x in others if x is not None):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("expected a torch tensor, got %s" % type(t).__name__)
+        if expect_cuda and (not t.is_cuda or t.device.index != int(device)):
+            raise ValueError("expected a CUDA tensor on cuda:%d, got one on %s" % (device, t.device))
+        if not expect_cuda and t.is_cuda:
+            raise ValueError("expected a CPU tensor")
+        if t.dtype != torch.complex128:
+            raise ValueError("expected complex128, got %s" % t.dtype)
+        if not t.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        if t.dim() not in (1, 2) or t.shape[0] != N:
+            raise ValueError("expected shape (N,) or (N, R) with N = %d, got %s" % (N, tuple(t.shape)))
+        if t.shape != first.shape:
+            raise ValueError("operands differ in shape: %s and %s" % (tuple(first.shape), tuple(t.shape)))
+
+
 class Solver:
     """One context of the C library.  Typical use:
 
@@ -325,12 +351,14 @@ class Solver:
     # ------------------------------------------------------------ operators
     def _io(self, a):
         dev = _is_dev(a)
+        N = self.N
         if dev:
-            if not a.is_contiguous():
-                raise ValueError("device tensors must be contiguous")
+            check_device_vectors(N, self._opt.device, a)
             out = a.new_empty(a.shape)
         else:
             a = np.ascontiguousarray(a, dtype=np.complex128)
+            if a.ndim not in (1, 2) or a.shape[0] != N:
+                raise ValueError("expected an N or N x R complex array, N = %d; got shape %s" % (N, a.shape))
             out = np.empty_like(a)
         R = 1 if a.ndim == 1 else int(a.shape[1])
         return a, out, R, int(dev)
@@ -344,7 +372,13 @@ class Solver:
         a, out, R, dev = self._io(y)
         sp = None
         if sigma is not None:
-            s2 = sigma if dev else np.ascontiguousarray(sigma, dtype=np.complex128)
+            if dev:
+                check_device_vectors(self.N, self._opt.device, a, sigma)
+                s2 = sigma
+            else:
+                s2 = np.ascontiguousarray(sigma, dtype=np.complex128)
+                if s2.shape != a.shape:
+                    raise ValueError("sigma must have the shape of y")
             sp = _ptr(s2)
         self._check(lib().hzb_local_inverse(self._h, R, _ptr(a), sp, float(alpha), float(beta), _ptr(out), dev,
                                             int(precision)))
@@ -352,12 +386,15 @@ class Solver:
 
     def local_inverse_noalloc(self, y, sigma=None, alpha: float = 0.0, beta: float = 1.0, out=None):
         """FP64 D^{-1} apply through hzb_local_inverse_noalloc: device tensors only; the
-        library allocates nothing for this call (static scratch, see include/hzb.h)."""
-        if not _is_dev(y) or (sigma is not None and not _is_dev(sigma)):
-            raise ValueError("local_inverse_noalloc takes CUDA tensors only")
-        R = 1 if y.ndim == 1 else int(y.shape[1])
+        library allocates nothing for this call (static scratch, see include/hzb.h).
+        y, sigma and out are checked (contiguous complex128 CUDA tensors of shape N or
+        N x R on the context's device, all of one shape) before their addresses reach
+        the C call, which cannot check sizes itself."""
         if out is None:
+            check_device_vectors(self.N, self._opt.device, y)
             out = y.new_empty(y.shape)
+        check_device_vectors(self.N, self._opt.device, y, sigma, out)
+        R = 1 if y.ndim == 1 else int(y.shape[1])
         sp = _ptr(sigma) if sigma is not None else None
         self._check(lib().hzb_local_inverse_noalloc(self._h, R, _ptr(y), sp, float(alpha), float(beta), _ptr(out)))
         return out
@@ -383,11 +420,23 @@ class Solver:
         return self._stats(st, rc)
 
     def solve_data(self, v, x0=None, allow_noconv: bool = False) -> Stats:
-        a = v if _is_dev(v) else np.ascontiguousarray(v, dtype=np.complex128)
+        N = self.N
+        if _is_dev(v):
+            check_device_vectors(N, self._opt.device, v, x0 if _is_dev(x0) else None)
+            a = v
+        else:
+            a = np.ascontiguousarray(v, dtype=np.complex128)
+            if a.ndim not in (1, 2) or a.shape[0] != N:
+                raise ValueError("expected v of shape (N,) or (N, R) with N = %d, got %s" % (N, a.shape))
         R = 1 if a.ndim == 1 else int(a.shape[1])
         xp = None
         if x0 is not None:
-            x0 = x0 if _is_dev(x0) else np.ascontiguousarray(x0, dtype=np.complex128)
+            if _is_dev(x0) != _is_dev(a):
+                raise ValueError("v and x0 must both be host arrays or both CUDA tensors")
+            if not _is_dev(x0):
+                x0 = np.ascontiguousarray(x0, dtype=np.complex128)
+                if x0.shape != a.shape:
+                    raise ValueError("x0 must have the shape of v")
             xp = _ptr(x0)
         st = _Stats()
         rc = lib().hzb_solve_data(self._h, R, _ptr(a), xp, int(_is_dev(a)), ctypes.byref(st))
@@ -456,6 +505,13 @@ class Solver:
         R = getattr(self, "_R", 1)
         if out is None:
             out = np.zeros((self.N, R), dtype=np.complex128)
+        elif _is_dev(out):
+            check_device_vectors(self.N, self._opt.device, out)
+            if out.numel() != self.N * R:
+                raise ValueError("out must hold N x R = %d x %d values" % (self.N, R))
+        elif not (isinstance(out, np.ndarray) and out.dtype == np.complex128 and out.flags.c_contiguous
+                  and out.size == self.N * R):
+            raise ValueError("out must be a C-contiguous complex128 array of N x R values")
         self._check(lib().hzb_get_density(self._h, _ptr(out), int(_is_dev(out))))
         return out
 

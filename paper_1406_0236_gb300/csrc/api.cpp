@@ -1,6 +1,7 @@
 // C ABI of the library (include/hzb.h): context, call order, argument checks and
 // host <-> device marshalling.  All arithmetic runs in the CUDA kernels.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -29,17 +30,29 @@ hzb_status check_cuda(hzb_ctx *c, cudaError_t e, const char *what)
     return HZB_ECUDA;
 }
 
+thread_local bool g_fail_alloc = false;
+
+int parse_fault_spec(const char *spec)
+{
+    int f = 0;
+    if (!spec) return 0;
+    std::string s(spec);
+    size_t a = 0;
+    while (a <= s.size()) {
+        size_t b = s.find(',', a);
+        if (b == std::string::npos) b = s.size();
+        const std::string t = s.substr(a, b - a);
+        if (t == "alloc") f |= FAULT_ALLOC;
+        else if (t == "geom") f |= FAULT_GEOM;
+        else if (t == "nan") f |= FAULT_NAN;
+        else if (t == "timeout") f |= FAULT_TIMEOUT;
+        a = b + 1;
+    }
+    return f;
+}
+
 }  // namespace hzb
 
-// Entry of every call: valid context, its device current, and no stale (non-sticky)
-// error of an unrelated earlier runtime call left for this call's checks to report.
-#define HZB_GUARD(c)                                                 \
-    do {                                                             \
-        if (!(c)) return HZB_EINVAL;                                 \
-        if (cudaSetDevice((c)->opt.device) != cudaSuccess)           \
-            return fail((c), HZB_ECUDA, "cudaSetDevice failed");     \
-        cudaGetLastError();                                          \
-    } while (0)
 
 extern "C" {
 
@@ -98,6 +111,7 @@ hzb_status hzb_create(const hzb_options *options, hzb_ctx **out)
     if (!c) return HZB_ENOMEM;
     c->opt = o;
     c->stream = (cudaStream_t)o.cuda_stream;
+    c->fault = parse_fault_spec(std::getenv("HZB_FAULT"));
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
         delete c;
         return HZB_ECUDA;
@@ -110,6 +124,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
 {
     if (!c) return HZB_EINVAL;
     cudaSetDevice(c->opt.device);
+    g_fail_alloc = false;
     // the caller's stream may already be gone: wait for the whole device instead
     cudaDeviceSynchronize();
     release_compression(c);
@@ -125,7 +140,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     c->io_in.release(); c->io_out.release(); c->io_small.release(); c->tiny.release(); c->sol.release();
     c->red.release(); c->krylov.release(); c->small.release();
     c->sctab.release(); c->nb_part64.release(); c->nb_part32.release(); c->sig32.release(); c->blockpairs.release(); c->kerr.release(); c->Ximg.release();
-    c->dfa.release(); c->dfb.release(); c->dfc.release(); c->dftab.release();
+    c->dfa.release(); c->dfb.release(); c->dfc.release(); c->dftab.release(); c->nodecheck.release();
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
     release_graphs(c);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);

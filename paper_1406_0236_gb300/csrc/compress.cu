@@ -1387,13 +1387,7 @@ hzb_status solve_reduced(hzb_ctx *c, int R, const double2 *v, const double2 *x0,
 
 using namespace hzb;
 
-#define CP_GUARD(c)                                                  \
-    do {                                                             \
-        if (!(c)) return HZB_EINVAL;                                 \
-        if (cudaSetDevice((c)->opt.device) != cudaSuccess)           \
-            return fail((c), HZB_ECUDA, "cudaSetDevice failed");     \
-        cudaGetLastError();                                          \
-    } while (0)
+#define CP_GUARD(c) HZB_GUARD(c)
 
 extern "C" hzb_status hzb_compress(hzb_ctx *c, double eps, int n_theta, double proxy_radius)
 {

@@ -48,6 +48,22 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
 // evaluate gamma and gamma' of a piece at t
 void piece_eval(const Piece &pc, double t, double &r, double &z, double &dr, double &dz);
 
+// ---------------------------------------------------------------- host fault injection
+
+// Faults injected on the host for tests of the error paths (environment variable
+// HZB_FAULT, read once by hzb_create: a comma-separated list of the names below).
+// No fault touches the GPU's state beyond the context's own buffers and flags.
+enum {
+    FAULT_ALLOC = 1,     // "alloc": every device allocation of the context fails (HZB_ENOMEM)
+    FAULT_GEOM = 2,      // "geom": the first node generation writes a NaN weight (HZB_EINVAL)
+    FAULT_NAN = 4,       // "nan": the first solve's preconditioned right-hand side gets a NaN (HZB_ENAN)
+    FAULT_TIMEOUT = 8    // "timeout": the first tcgen05 inter-body launch takes its bounded-wait
+                         // exit before any MMA is issued (HZB_ETIMEOUT)
+};
+int parse_fault_spec(const char *spec);
+// set by every ABI entry from its context: DevBuf::ensure fails while it is true
+extern thread_local bool g_fail_alloc;
+
 // ---------------------------------------------------------------- device buffers
 
 template <typename T>
@@ -56,6 +72,7 @@ struct DevBuf {
     size_t n = 0;
     cudaError_t ensure(size_t count) {
         if (count <= n) return cudaSuccess;
+        if (g_fail_alloc) return cudaErrorMemoryAllocation;
         if (ptr) cudaFree(ptr);
         ptr = nullptr;
         n = 0;
@@ -213,7 +230,23 @@ struct hzb_ctx {
     std::vector<cudaEvent_t> evpool;
     std::vector<int> evkind;                   // 0: FP64, 1: FP32, per recorded pair
     bool prof_on = false;
+    // host fault injection (FAULT_* bits from HZB_FAULT) and the one-shot faults already fired
+    int fault = 0;
+    int fault_spent = 0;
+    hzb::DevBuf<int> nodecheck;                // node validation: [bad count, first bad node]
 };
+
+// Entry of every ABI call: valid context, its device current, the context's injected
+// allocation fault (if any) armed, and no stale (non-sticky) error of an unrelated
+// earlier runtime call left for this call's checks to report.
+#define HZB_GUARD(c)                                                     \
+    do {                                                                 \
+        if (!(c)) return HZB_EINVAL;                                     \
+        if (cudaSetDevice((c)->opt.device) != cudaSuccess)               \
+            return hzb::fail((c), HZB_ECUDA, "cudaSetDevice failed");    \
+        hzb::g_fail_alloc = ((c)->fault & hzb::FAULT_ALLOC) != 0;        \
+        cudaGetLastError();                                              \
+    } while (0)
 
 // ---------------------------------------------------------------- kernels' host entry points
 namespace hzb {

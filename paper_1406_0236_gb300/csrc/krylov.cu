@@ -555,6 +555,15 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
         cleanup();
         return st;
     }
+    if ((c->fault & FAULT_NAN) && !(c->fault_spent & FAULT_NAN)) {         // injected: NaN in b
+        c->fault_spent |= FAULT_NAN;
+        static const double2 qnan2 = {std::nan(""), 0.0};
+        if (check_cuda(c, cudaMemcpyAsync(bbuf.ptr, &qnan2, sizeof(double2), cudaMemcpyHostToDevice, c->stream),
+                       "inject NaN")) {
+            cleanup();
+            return HZB_ECUDA;
+        }
+    }
     double2 *x = c->sol.ptr;
     int it = 0, conv = 0, outer = 0;
     double rr = 0.0;

@@ -137,7 +137,9 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
 #pragma unroll
     for (int q = 0; q < RC; ++q) acc[q] = 0.f;
     uint32_t phase = 0;
-    bool failed = false;
+    // a negative error flag set by the host before the launch (injected fault) sends the CTA
+    // to its timeout exit before any MMA is issued: nothing asynchronous is then in flight
+    bool failed = *(volatile int *)err < 0;
     const int c0 = blockIdx.z * chunk, c1 = min(N, c0 + chunk);
     // the tile sequence: range 0 = [c0, min(c1, excl_lo)), range 1 = [max(c0, excl_hi), c1)
     const int lo0 = c0, hi0 = min(c1, tb.excl_lo), lo1 = max(c0, tb.excl_hi), hi1 = c1;
@@ -162,7 +164,7 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
             bv[q] = (bduty && s < cnt && rb < R) ? sw[(size_t)(j0 + s) * R + rb] : make_float2(0.f, 0.f);
         }
     };
-    const int ntile = n0 + n1;
+    const int ntile = failed ? 0 : n0 + n1;
     if (ntile > 0) prefetch(0);
     for (int it = 0; it < ntile; ++it) {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -544,6 +546,11 @@ hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
             return HZB_ECUDA;
         attr_done[dev] = true;
     }
+    if ((c->fault & FAULT_TIMEOUT) && !(c->fault_spent & FAULT_TIMEOUT) && !c->capturing && !ws) {
+        c->fault_spent |= FAULT_TIMEOUT;   // injected: every CTA takes the timeout exit (flag -1)
+        if (check_cuda(c, cudaMemsetAsync(c->kerr.ptr, 0xff, sizeof(int), c->stream), "inject timeout"))
+            return HZB_ECUDA;
+    }
     c->interbody_calls++;
     c->launches += (nsplit > 1) ? 3 : 2;
     const int slot = prof_begin(c, 1);
@@ -578,7 +585,11 @@ hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
                        "read error flag") ||
             check_cuda(c, cudaStreamSynchronize(c->stream), "nbody_tc5_kernel"))
             return HZB_ECUDA;
-        if (flag) return fail(c, HZB_ETIMEOUT, "tensor-core wait timed out in nbody_tc5_kernel");
+        if (flag) {                    // report once; the context stays usable for the next call
+            if (check_cuda(c, cudaMemsetAsync(c->kerr.ptr, 0, sizeof(int), c->stream), "clear error flag"))
+                return HZB_ECUDA;
+            return fail(c, HZB_ETIMEOUT, "tensor-core wait timed out in nbody_tc5_kernel");
+        }
     }
     return HZB_OK;
 }

@@ -17,6 +17,9 @@
 //   * the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress, with that device current); make that first call before
 //     any stream capture;
+//   * like hzb_local_inverse on the same context, it applies the direct D^{-1} of Eq.
+//     (precond), also while the accelerated scheme is on (the reduced operator of
+//     Eq. (ip6) belongs to the context's internal reduced system, not to this call);
 //   * nothing in the array needs to start at zero: every element the call reads was
 //     written earlier in the same call (the previous call's contents are overwritten).
 #include <mutex>

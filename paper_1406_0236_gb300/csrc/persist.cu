@@ -49,9 +49,8 @@ using namespace hzb;
 
 extern "C" hzb_status hzb_save_scattering(hzb_ctx *c, const char *path)
 {
-    if (!c || !path) return HZB_EINVAL;
-    if (cudaSetDevice(c->opt.device) != cudaSuccess) return fail(c, HZB_ECUDA, "cudaSetDevice");
-    cudaGetLastError();
+    if (!path) return HZB_EINVAL;
+    HZB_GUARD(c);
     if (c->state != 3) return fail(c, HZB_ESTATE, "scattering matrices not built");
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(c, HZB_EINVAL, std::string("cannot open for writing: ") + path);
@@ -119,9 +118,8 @@ extern "C" hzb_status hzb_save_scattering(hzb_ctx *c, const char *path)
 
 extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
 {
-    if (!c || !path) return HZB_EINVAL;
-    if (cudaSetDevice(c->opt.device) != cudaSuccess) return fail(c, HZB_ECUDA, "cudaSetDevice");
-    cudaGetLastError();
+    if (!path) return HZB_EINVAL;
+    HZB_GUARD(c);
     if (c->state != 2) return fail(c, HZB_ESTATE, "hzb_load_scattering needs bodies and no earlier build");
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(c, HZB_EINVAL, std::string("cannot open: ") + path);

@@ -24,8 +24,10 @@
 //               substitution psi = w sinh(mu (x+1)/2), mu = asinh(1/(4w)), which
 //               removes the peak of half-width w = d / sqrt(r r') at psi = 0; on
 //               [1/4, pi] a fixed composite 12 x 16-point Gauss-Legendre rule.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <string>
 #include <vector>
 
 #include "curve.h"
@@ -80,10 +82,105 @@ __global__ void body_nodes_kernel(int NG, int NF, const double *__restrict__ rin
     body_of[g] = body;
 }
 
+// Validation of the generated surface rule: finite positions and normals, |n| = 1 to
+// 1e-9, weights finite and > 0.  out[0] counts bad nodes, out[1] holds the smallest
+// bad index (both start at 0 and INT_MAX).
+__global__ void check_nodes_kernel(long long N, const double4 *__restrict__ pos, const double4 *__restrict__ nrm,
+                                   int *out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double4 p = pos[i], n = nrm[i];
+    const double nn = n.x * n.x + n.y * n.y + n.z * n.z;
+    const bool ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w) && p.w > 0.0 &&
+                    isfinite(nn) && fabs(nn - 1.0) < 1e-9;
+    if (!ok) {
+        atomicAdd(out, 1);
+        atomicMin(out + 1, (int)i);
+    }
+}
+
+// The closed profile of a shape in its (r, z) half-plane: the curve's first end, the ring
+// nodes in order, its last end (both ends lie on the axis), closed along the axis.
+static void shape_profile(const ShapeGeom &g, std::vector<double> &pr, std::vector<double> &pz)
+{
+    double r, z, dr, dz;
+    pr.clear();
+    pz.clear();
+    piece_eval(g.pieces.front(), g.pieces.front().t0, r, z, dr, dz);
+    pr.push_back(std::fabs(r)); pz.push_back(z);
+    for (int i = 0; i < g.NG; ++i) { pr.push_back(g.r[i]); pz.push_back(g.z[i]); }
+    piece_eval(g.pieces.back(), g.pieces.back().t1, r, z, dr, dz);
+    pr.push_back(std::fabs(r)); pz.push_back(z);
+}
+
+// even-odd crossing test of (r, z) against the closed polygon (pr, pz)
+static bool inside_profile(const std::vector<double> &pr, const std::vector<double> &pz, double r, double z)
+{
+    bool in = false;
+    const size_t n = pr.size();
+    for (size_t a = 0, b = n - 1; a < n; b = a++) {
+        if ((pz[a] > z) != (pz[b] > z)) {
+            const double rc = pr[a] + (z - pz[a]) * (pr[b] - pr[a]) / (pz[b] - pz[a]);
+            if (r < rc) in = !in;
+        }
+    }
+    return in;
+}
+
+// Bodies must not intersect: for every pair whose bounding spheres meet, the ring nodes of
+// each (at up to 32 azimuths) are tested against the other's solid (its profile rotated
+// about its axis).  Returns false with p, q set for the first overlapping pair.
+static bool bodies_disjoint(const hzb_ctx *c, int &p_out, int &q_out)
+{
+    const size_t nb = c->bodies.size(), ns = c->shapes.size();
+    std::vector<std::vector<double>> PR(ns), PZ(ns);
+    std::vector<double> bound(ns, 0.0);
+    for (size_t s = 0; s < ns; ++s) {
+        shape_profile(c->shapes[s]->geom, PR[s], PZ[s]);
+        for (size_t a = 0; a < PR[s].size(); ++a) bound[s] = std::max(bound[s], std::hypot(PR[s][a], PZ[s][a]));
+        bound[s] *= 1.001;
+    }
+    for (size_t p = 0; p < nb; ++p)
+        for (size_t q = 0; q < nb; ++q) {
+            if (p == q) continue;
+            const BodyRec &A = c->bodies[p], &B = c->bodies[q];
+            const double dc = std::sqrt((A.c[0] - B.c[0]) * (A.c[0] - B.c[0]) + (A.c[1] - B.c[1]) * (A.c[1] - B.c[1]) +
+                                        (A.c[2] - B.c[2]) * (A.c[2] - B.c[2]));
+            if (dc > bound[A.shape] + bound[B.shape]) continue;
+            const ShapeGeom &ga = c->shapes[A.shape]->geom;
+            const int step = std::max(1, ga.NF / 32);
+            for (int i = 0; i < ga.NG; ++i)
+                for (int l = 0; l < ga.NF; l += step) {
+                    const double th = 2.0 * M_PI * l / ga.NF;
+                    const double lx = ga.r[i] * std::cos(th), ly = ga.r[i] * std::sin(th), lz = ga.z[i];
+                    double x[3], y[3];
+                    for (int e = 0; e < 3; ++e)
+                        x[e] = A.c[e] + A.rot[3 * e] * lx + A.rot[3 * e + 1] * ly + A.rot[3 * e + 2] * lz - B.c[e];
+                    for (int e = 0; e < 3; ++e)          // into B's frame: rot^T (x - c_B)
+                        y[e] = B.rot[e] * x[0] + B.rot[3 + e] * x[1] + B.rot[6 + e] * x[2];
+                    if (y[0] * y[0] + y[1] * y[1] + y[2] * y[2] > bound[B.shape] * bound[B.shape]) continue;
+                    if (inside_profile(PR[B.shape], PZ[B.shape], std::hypot(y[0], y[1]), y[2])) {
+                        p_out = (int)p;
+                        q_out = (int)q;
+                        return false;
+                    }
+                }
+        }
+    return true;
+}
+
 hzb_status make_nodes(hzb_ctx *c)
 {
     if (c->nodes_ready) return HZB_OK;
     size_t N = (size_t)c->N;
+    {
+        int bp = -1, bq = -1;
+        if (!bodies_disjoint(c, bp, bq))
+            return fail(c, HZB_EINVAL, "bodies " + std::to_string(bp) + " and " + std::to_string(bq) +
+                                           " overlap (a node of body " + std::to_string(bp) +
+                                           " lies inside body " + std::to_string(bq) + ")");
+    }
     if (check_cuda(c, c->pos64.ensure(N), "alloc nodes") || check_cuda(c, c->nrm64.ensure(N), "alloc") ||
         check_cuda(c, c->pos32.ensure(N), "alloc") || check_cuda(c, c->nrm32.ensure(N), "alloc") ||
         check_cuda(c, c->body_of.ensure(N), "alloc"))
@@ -148,7 +245,29 @@ hzb_status make_nodes(hzb_ctx *c)
     if (check_cuda(c, cudaMemcpyAsync(c->tblocks.ptr, blocks.data(), blocks.size() * sizeof(TargetBlock),
                                       cudaMemcpyHostToDevice, c->stream), "copy blocks"))
         return HZB_ECUDA;
-    if (check_cuda(c, cudaStreamSynchronize(c->stream), "nodes")) return HZB_ECUDA;
+    if (check_cuda(c, c->nodecheck.ensure(2), "alloc node check")) return HZB_ENOMEM;
+    if ((c->fault & FAULT_GEOM) && !(c->fault_spent & FAULT_GEOM)) {      // injected: a NaN weight
+        c->fault_spent |= FAULT_GEOM;
+        static const double qnan = std::nan("");
+        if (check_cuda(c, cudaMemcpyAsync(&c->pos64.ptr[N / 2].w, &qnan, sizeof(double), cudaMemcpyHostToDevice,
+                                          c->stream), "inject geometry fault"))
+            return HZB_ECUDA;
+    }
+    int hchk[2] = {0, 0x7fffffff};
+    if (check_cuda(c, cudaMemcpyAsync(c->nodecheck.ptr, hchk, sizeof(hchk), cudaMemcpyHostToDevice, c->stream),
+                   "node check"))
+        return HZB_ECUDA;
+    check_nodes_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>((long long)N, c->pos64.ptr, c->nrm64.ptr,
+                                                                           c->nodecheck.ptr);
+    if (check_cuda(c, cudaGetLastError(), "check_nodes_kernel") ||
+        check_cuda(c, cudaMemcpyAsync(hchk, c->nodecheck.ptr, sizeof(hchk), cudaMemcpyDeviceToHost, c->stream),
+                   "node check") ||
+        check_cuda(c, cudaStreamSynchronize(c->stream), "nodes"))
+        return HZB_ECUDA;
+    if (hchk[0] > 0)
+        return fail(c, HZB_EINVAL, std::to_string(hchk[0]) + " surface nodes are invalid (first: node " +
+                                       std::to_string(hchk[1]) +
+                                       "): non-finite position or normal, |n| != 1 or weight <= 0");
     c->nodes_ready = true;
     return HZB_OK;
 }

@@ -1,0 +1,158 @@
+"""Parity of the headline eight-spheroid workload's direct path, and of reduced forms
+of the 27-body (uneven sizes, 8 right-hand sides in one batch) and 48-body (open
+shells, k = 6) workloads, against the oracle and physics.
+
+  * eight spheroids (258,560 unknowns, N_G = 320, N_F = 101, k = 4): rows of A~_p and
+    all of S_p for several modes (Sec. 3.2, Eqs. (FAF), (singleinverse)); D^{-1} on a
+    full vector; Green's identity (Sec. 6 accuracy protocol) through the direct mixed
+    solve with the benchmark's options;
+  * mixed4_shells (a sphere, a spheroid, two open shells; 29,280 unknowns) and uneven3
+    (three bodies of different N_G and N_F, 8 plane waves): FP64 solves <= 1e-10 and
+    mixed solves <= 1e-7 in density and far field against the oracle's GMRES, and
+    Green's identity with a source in each body (in the wall of each shell)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._common import gpu_solver, rand_c, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def spheroids8():
+    require_gpu()
+    from oracle import Problem
+    wl = W.spheroids8()
+    s = gpu_solver(wl)
+    return wl, s, Problem(wl)
+
+
+def test_spheroids8_modal_blocks_against_oracle(spheroids8):
+    from oracle.modal import modal_rows
+    wl, s, P = spheroids8
+    shape = wl.bodies[0].shape
+    rg = P.rings[shape]
+    rows = np.array([0, 17, 160, 301, 319])
+    ref = modal_rows(rg, rows, wl.k, wl.eta)
+    S_ref = P.S(shape)                       # oracle's full A~_p inverted (all 320 rows)
+    for p in (0, 1, 13, 50):
+        A = s.get_modal_block(3, p, 0, rg.n)
+        assert np.abs(A[rows] - ref[p]).max() < 1e-11 * np.abs(ref[p]).max(), p
+        S = s.get_modal_block(5, p, 1, rg.n)
+        assert np.abs(S - S_ref[p]).max() < 1e-11 * np.abs(S_ref[p]).max(), p
+
+
+def test_spheroids8_local_inverse_against_oracle(spheroids8):
+    wl, s, P = spheroids8
+    y = rand_c(P.N, 801)
+    ref = P.local_inverse(y)
+    got = s.local_inverse(y)
+    assert rel_l2(got, ref) <= 1e-11
+    rows = np.random.default_rng(802).choice(P.N, 2048, replace=False)
+    assert np.abs(got[rows] - ref[rows]).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_spheroids8_green_identity_through_direct_mixed_solve():
+    """The benchmark's solve (FP32 inner sums, one FP64 residual, the a-priori stop)
+    reproduces the exterior field of interior point sources."""
+    require_gpu()
+    from oracle import fields
+    wl = W.spheroids8()
+    s = gpu_solver(wl, precision=1, tol=1e-8, inner_tol=1e-5, max_outer=6, verify_final=0)
+    x, _, _ = s.get_nodes()
+    src = W.point_sources(wl, 21)
+    tg = W.exterior_targets(wl, 10, 22)
+    st = s.solve_data(-fields.point_source_field(x, src, wl.k))
+    assert st.converged
+    u = s.eval_field(tg)[:, 0]
+    ue = fields.point_source_field(tg, src, wl.k)
+    err = np.abs(u - ue).max() / np.abs(ue).max()
+    print("spheroids8 Green identity through the mixed solve: %.2e" % err)
+    assert err < 1e-7
+
+
+def _oracle_solutions(wl):
+    from oracle import Problem, fields, gmres
+    P = Problem(wl)
+    v = fields.plane_wave(P.nodes.x, wl.directions, wl.k)
+    cols = []
+    for r in range(v.shape[1]):
+        res = gmres(P.apply, P.rhs(v[:, r]), 1e-12)
+        assert res.converged
+        cols.append(res.x)
+    return P, np.stack(cols, axis=1)
+
+
+@pytest.fixture(scope="module")
+def mixed4_ref():
+    require_gpu()
+    wl = W.mixed4_shells(n_rhs=1)
+    P, sig = _oracle_solutions(wl)
+    return wl, P, sig
+
+
+@pytest.fixture(scope="module")
+def uneven3_ref():
+    require_gpu()
+    wl = W.uneven3()
+    P, sig = _oracle_solutions(wl)
+    return wl, P, sig
+
+
+def _check_solve(wl, P, sig_ref, precision, tol, bar):
+    from oracle import fields
+    s = gpu_solver(wl, precision=precision, tol=tol)
+    st = s.solve_plane_waves(wl.directions)
+    assert st.converged
+    sig = s.get_density()
+    assert sig.shape == sig_ref.shape
+    for r in range(sig.shape[1]):
+        assert rel_l2(sig[:, r], sig_ref[:, r]) <= bar, r
+    xh = W.uniform_directions(16, 31)
+    ff = s.far_field(xh)
+    ffr = fields.far_field(P.nodes, sig_ref, wl.k, wl.eta, xh)
+    ffr = ffr.reshape(ff.shape)
+    for r in range(ff.shape[1]):
+        assert rel_l2(ff[:, r], ffr[:, r]) <= bar, r
+    return st
+
+
+def test_mixed4_shells_fp64_solve_against_oracle(mixed4_ref):
+    wl, P, sig = mixed4_ref
+    _check_solve(wl, P, sig, 0, 1e-12, 1e-10)
+
+
+def test_mixed4_shells_mixed_solve_against_oracle(mixed4_ref):
+    wl, P, sig = mixed4_ref
+    st = _check_solve(wl, P, sig, 1, 1e-9, 1e-7)
+    assert st.outer_iterations >= 1
+
+
+def test_uneven3_batch_fp64_against_oracle(uneven3_ref):
+    wl, P, sig = uneven3_ref
+    assert len({(b.shape.n_rings, b.shape.n_modes) for b in wl.bodies}) == 3 and sig.shape[1] == 8
+    _check_solve(wl, P, sig, 0, 1e-12, 1e-10)
+
+
+def test_uneven3_batch_mixed_against_oracle(uneven3_ref):
+    wl, P, sig = uneven3_ref
+    _check_solve(wl, P, sig, 1, 1e-9, 1e-7)
+
+
+def test_mixed4_shells_green_identity():
+    require_gpu()
+    from oracle import fields
+    wl = W.mixed4_shells(n_rhs=1)
+    for prec, tol, bar in ((0, 1e-12, 1e-3), (1, 1e-9, 1e-3)):
+        s = gpu_solver(wl, precision=prec, tol=tol)
+        x, _, _ = s.get_nodes()
+        src = W.point_sources(wl, 41)
+        tg = W.exterior_targets(wl, 10, 42)
+        st = s.solve_data(-fields.point_source_field(x, src, wl.k))
+        assert st.converged
+        u = s.eval_field(tg)[:, 0]
+        ue = fields.point_source_field(tg, src, wl.k)
+        err = np.abs(u - ue).max() / np.abs(ue).max()
+        print("mixed4_shells Green identity (precision %d): %.2e" % (prec, err))
+        assert err < bar

@@ -307,6 +307,56 @@ def mixed48(seed=DEFAULT_SEED, n_rhs=16, k=6.0, n_panels=24, gl_order=16, n_mode
                     gmres_tol=1e-10)
 
 
+def mixed4_shells(seed=DEFAULT_SEED, n_rhs=2, k=6.0, n_panels=12, gl_order=10, n_modes=61,
+                  min_gap_required=1.0) -> Workload:
+    """A reduced form of the 48-body workload that the oracle solves in minutes: a unit
+    sphere, a spheroid (1,1,2) and two open shells (1, 0.8, 60 degrees, rim 0.1) on a
+    jittered 2x2x1 grid of spacing 4.5 (jitter U[-0.5,0.5]^3, seeded orientations,
+    surface gaps >= 1); k = eta = 6; 12 panels x gl_order GL nodes and 61 azimuthal
+    nodes per body; n_rhs plane waves uniform on the sphere."""
+    rng = np.random.default_rng(seed + 5)
+    shapes = [ShapeSpec(SPHERE, (1.0,), n_panels, gl_order, n_modes),
+              ShapeSpec(SPHEROID, (1.0, 2.0), n_panels, gl_order, n_modes),
+              ShapeSpec(OPEN_SHELL, (1.0, 0.8, np.pi / 3.0, 0.1), n_panels, gl_order, n_modes),
+              ShapeSpec(OPEN_SHELL, (1.0, 0.8, np.pi / 3.0, 0.1), n_panels, gl_order, n_modes)]
+    bodies: List[Body] = []
+    samples = []
+    for idx, (ix, iy) in enumerate([(0, 0), (1, 0), (0, 1), (1, 1)]):
+        base = 4.5 * np.array([ix - 0.5, iy - 0.5, 0.0])
+        for _attempt in range(200):
+            cand = Body(shapes[idx], base + rng.uniform(-0.5, 0.5, 3), rotation_taking_z_to(rng.standard_normal(3)))
+            if not bodies or gap_to(bodies, cand, samples) >= min_gap_required:
+                break
+        else:
+            raise RuntimeError("could not place body %d with the required gap" % idx)
+        bodies.append(cand)
+        samples.append(_surface_samples(cand))
+    return Workload("mixed4_shells", bodies, k, k, uniform_directions(n_rhs, seed + 13), gmres_tol=1e-10)
+
+
+def uneven3(seed=DEFAULT_SEED, n_rhs=8, k=4.0) -> Workload:
+    """A reduced form of the 27-body workload: three bodies on a line of spacing 5, a
+    seeded mix of spheres (radius U[0.5,1.5]) and spheroids (1,1,c), c ~ U[1,2], each
+    with its own panel count in [6,12] (8 GL nodes each) and odd azimuthal count in
+    [21,41] (uneven sizes); k = eta = 4; n_rhs plane waves uniform on the sphere,
+    solved as one batch."""
+    rng = np.random.default_rng(seed + 3)
+    bodies = []
+    kinds = [SPHERE, SPHEROID, SPHEROID]
+    for q in range(3):
+        npan = int(rng.integers(6, 13))
+        nf = int(2 * rng.integers(10, 21) + 1)
+        c = np.array([5.0 * (q - 1), 0.0, 0.0]) + rng.uniform(-0.5, 0.5, 3)
+        if kinds[q] == SPHERE:
+            shape = ShapeSpec(SPHERE, (float(rng.uniform(0.5, 1.5)),), npan, 8, nf)
+            rot = np.eye(3)
+        else:
+            shape = ShapeSpec(SPHEROID, (1.0, float(rng.uniform(1.0, 2.0))), npan, 8, nf)
+            rot = rotation_taking_z_to(rng.standard_normal(3))
+        bodies.append(Body(shape, c, rot))
+    return Workload("uneven3", bodies, k, k, uniform_directions(n_rhs, seed + 17), gmres_tol=1e-10)
+
+
 def point_sources(wl: Workload, seed: int) -> np.ndarray:
     """One point source inside each body (world coordinates), as in the paper's
     accuracy protocol (Sec. 6).  Spheres and spheroids: centre plus 0.3 x (smallest
@@ -347,5 +397,7 @@ def by_name(name: str, **kw) -> Workload:
         "spheroids8_258560": spheroids8,
         "mixed27": mixed27,
         "mixed48_shells": mixed48,
+        "mixed4_shells": mixed4_shells,
+        "uneven3": uneven3,
     }
     return table[name](**kw)
