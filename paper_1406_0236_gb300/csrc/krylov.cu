@@ -114,10 +114,14 @@ __global__ void cycle_start_kernel(int R, int m, GmresState s, double tol, int f
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
-    double beta = sqrt(fmax(s.nrm2[r].x, 0.0));
+    // a non-finite norm (NaN or Inf in b, the guess or the operator) must reach the host
+    // as a non-finite residual: fmax(NaN, 0) would turn it into a zero, i.e. "converged"
+    const double n2 = s.nrm2[r].x;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    double beta = isfinite(n2) ? sqrt(fmax(n2, 0.0)) : qnan;
     if (first) s.bnorm[r] = beta;
     double bn = s.bnorm[r];
-    double rel = bn > 0.0 ? beta / bn : 0.0;
+    double rel = (isfinite(beta) && isfinite(bn)) ? (bn > 0.0 ? beta / bn : 0.0) : qnan;
     s.res[r] = rel;
     int act = (bn > 0.0 && rel > tol && isfinite(beta)) ? 1 : 0;
     s.active[r] = act;
@@ -135,6 +139,12 @@ __global__ void givens_kernel(int R, int m, int j, GmresState s, double tol)
     if (r >= R) return;
     if (!s.active[r]) {
         s.inv[r] = 0.0;
+        return;
+    }
+    if (!isfinite(s.nrm2[r].x)) {          // non-finite basis vector: report, do not treat as breakdown
+        s.res[r] = __longlong_as_double(0x7ff8000000000000ll);
+        s.inv[r] = 0.0;
+        s.active[r] = 0;
         return;
     }
     double hn = sqrt(fmax(s.nrm2[r].x, 0.0));

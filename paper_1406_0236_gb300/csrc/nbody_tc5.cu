@@ -87,6 +87,7 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
     extern __shared__ __align__(1024) unsigned char t5_smem_raw[];
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ int s_forced;                           // host-set flag: take the timeout exit
     __shared__ __align__(16) float s_src[6][T5_K];     // x, y, z, nx, ny, nz of the tile's sources
     // operand tiles on a 1024-byte boundary (the swizzle atom)
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(t5_smem_raw);
@@ -126,6 +127,7 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_forced = *(volatile int *)err < 0 ? 1 : 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -139,7 +141,8 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
     uint32_t phase = 0;
     // a negative error flag set by the host before the launch (injected fault) sends the CTA
     // to its timeout exit before any MMA is issued: nothing asynchronous is then in flight
-    bool failed = *(volatile int *)err < 0;
+    // (read once by thread 0 before the set-up barrier, so the whole CTA takes one branch)
+    bool failed = s_forced != 0;
     const int c0 = blockIdx.z * chunk, c1 = min(N, c0 + chunk);
     // the tile sequence: range 0 = [c0, min(c1, excl_lo)), range 1 = [max(c0, excl_hi), c1)
     const int lo0 = c0, hi0 = min(c1, tb.excl_lo), lo1 = max(c0, tb.excl_hi), hi1 = c1;

@@ -141,10 +141,13 @@ def test_uneven3_batch_mixed_against_oracle(uneven3_ref):
 
 
 def test_mixed4_shells_green_identity():
+    """At 121 azimuthal nodes (58,080 unknowns); the oracle's own solve at this
+    resolution reproduces the exterior field to 3.1e-6 (1.4e-4 at 61 nodes, where the
+    azimuthal rule limits the accuracy of the shells' walls)."""
     require_gpu()
     from oracle import fields
-    wl = W.mixed4_shells(n_rhs=1)
-    for prec, tol, bar in ((0, 1e-12, 1e-3), (1, 1e-9, 1e-3)):
+    wl = W.mixed4_shells(n_rhs=1, n_modes=121)
+    for prec, tol, bar in ((0, 1e-12, 1e-5), (1, 1e-9, 1e-5)):
         s = gpu_solver(wl, precision=prec, tol=tol)
         x, _, _ = s.get_nodes()
         src = W.point_sources(wl, 41)
