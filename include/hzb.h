@@ -271,7 +271,11 @@ hzb_status hzb_set_interbody_engine(hzb_ctx *ctx, int engine);
  * shared), about 1.5x fewer operations; both directions are added into y with FP64
  * atomics, so runs agree to rounding but not bit for bit; -1 (default) = 1 for R <= 4
  * right-hand sides, 0 above (the one-directional kernels amortise the pair geometry over
- * up to 8 right-hand sides per CTA).  Returns HZB_EINVAL for other values.  Not part of the paper: a GB300 choice (FP64 runs at
+ * up to 8 right-hand sides per CTA); 2 = pair-symmetric, with the double-float sum in its
+ * earlier form (every double-float operation renormalised; the FP64 sum as for 1).  The
+ * pair-symmetric double-float sum of engine 1 leaves its products and sums unnormalised
+ * and takes e^{ikr} from a 1024-entry table (about 1.7x fewer FP32 operations).  Returns
+ * HZB_EINVAL for other values.  Not part of the paper: a GB300 choice (FP64 runs at
  * 1/64 of the FP32 rate). */
 hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *ctx, int engine);
 

@@ -141,6 +141,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     c->red.release(); c->krylov.release(); c->small.release();
     c->sctab.release(); c->nb_part64.release(); c->nb_part32.release(); c->sig32.release(); c->blockpairs.release(); c->kerr.release(); c->Ximg.release();
     c->dfa.release(); c->dfb.release(); c->dfc.release(); c->dftab.release(); c->nodecheck.release();
+    c->dfltab.release();
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
     release_graphs(c);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
@@ -504,7 +505,7 @@ hzb_status hzb_tuned_config(const hzb_ctx *c, int R, int out[6])
     out[0] = e == 2 ? 4 : (e == 1 ? 3 : v);
     out[1] = c->tune32_tpt;
     out[2] = c->tune32_split;
-    out[3] = (c->nbody64_engine == 1 || (c->nbody64_engine < 0 && R <= 4)) ? 1 : 0;
+    out[3] = (c->nbody64_engine >= 1 || (c->nbody64_engine < 0 && R <= 4)) ? 1 : 0;
     out[4] = c->tune64_tpt;
     out[5] = c->tune64_split;
     return HZB_OK;
@@ -531,7 +532,7 @@ hzb_status hzb_set_modal_engine(hzb_ctx *c, int engine)
 hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *c, int engine)
 {
     if (!c) return HZB_EINVAL;
-    if (engine < -1 || engine > 1) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1}");
+    if (engine < -1 || engine > 2) return fail(c, HZB_EINVAL, "engine in {-1, 0, 1, 2}");
     c->nbody64_engine = engine;
     return HZB_OK;
 }

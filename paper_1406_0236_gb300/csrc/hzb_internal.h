@@ -179,7 +179,8 @@ struct hzb_ctx {
     hzb::DevBuf<int2> blockpairs;              // unordered TargetBlock pairs on different bodies (nbody_sym.cu)
     long long n_blockpairs = 0;                // 0: not built, -1: none (one body)
     int nbody64_engine = -1;                   // FP64/double-float sums: -1 auto (pair-symmetric for R <= 4),
-                                               // 0 one-directional, 1 pair-symmetric
+                                               // 0 one-directional, 1 pair-symmetric (lean double-float),
+                                               // 2 pair-symmetric (double-float with normalised operations)
     hzb::DevBuf<int> kerr;                     // device error flag of kernels with bounded waits
     hzb::DevBuf<float> Ximg;                   // embedded, TF32-split modal panel (TMA modal GEMM)
     bool kerr_ready = false;
@@ -193,6 +194,8 @@ struct hzb_ctx {
     // double-float inter-body kernel: split positions/normals, cos/sin table, launch shape
     hzb::DevBuf<float4> dfa, dfb, dfc, dftab;
     bool df_ready = false;
+    hzb::DevBuf<float4> dfltab;                // lean double-float kernel: cos/sin(2 pi m / 1024)
+    bool dfltab_ready = false;
     int tunedf_tpt = 0, tunedf_split = 0;
     // GMRES execution: steps between host checks (0 = auto) and CUDA graphs (-1 auto, 0 off, 1 on)
     int check_every = 0;
@@ -265,6 +268,7 @@ hzb_status build_shape_matrices(hzb_ctx *c, ShapeDev &s);
 hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   // nbody_df.cu
+hzb_status interbody_dfl_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   // nbody_dfl.cu
 hzb_status interbody_tc(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);
 hzb_status modal_gemm_tma(hzb_ctx *c, ShapeDev &sd, int ncols, const float2 *X, float2 *Cout);  // modal_tma.cu
 hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit,

@@ -515,7 +515,7 @@ static int default_nsplit_tc5(hzb_ctx *c, int R)
 
 hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 {
-    if (c->nbody64_engine == 1 || (c->nbody64_engine < 0 && R <= 4)) return interbody64_sym(c, R, sigma, y);
+    if (c->nbody64_engine >= 1 || (c->nbody64_engine < 0 && R <= 4)) return interbody64_sym(c, R, sigma, y);
     int tpt = c->tune64_tpt > 0 ? c->tune64_tpt : 2;
     int ns = c->tune64_split > 0 ? c->tune64_split : default_nsplit(c, R, tpt);
     return interbody64_cfg(c, R, sigma, y, tpt, ns);

@@ -2,7 +2,7 @@
 
     python -m paper_1406_0236_gb300.profile_case --workload spheroids8_258560 \
         --op interbody32 --repeat 2 [--rhs 1] [--autotune] [--engine -1] [--modal-engine -1] \
-        [--accel-eps 1e-8]
+        [--fp64-engine -1] [--accel-eps 1e-8]
 
 ops: interbody32, interbody64, interbody_df (B sigma), local_inverse64, local_inverse32 (D^{-1} y),
 apply64, apply32, solve_mixed, solve_fp64, compress.  Prints the mean time per call measured
@@ -33,6 +33,8 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--engine", type=int, default=-1)
     ap.add_argument("--modal-engine", type=int, default=-1)
+    ap.add_argument("--fp64-engine", type=int, default=-1,
+                    help="FP64 / double-float inter-body engine (Solver.set_fp64_interbody_engine)")
     ap.add_argument("--accel-eps", type=float, default=0.0)
     args = ap.parse_args()
 
@@ -48,6 +50,7 @@ def main():
                              stream=torch.cuda.current_stream().cuda_stream)
     s.set_interbody_engine(args.engine)
     s.set_modal_engine(args.modal_engine)
+    s.set_fp64_interbody_engine(args.fp64_engine)
     needs_build = not args.op.startswith("interbody")
     if needs_build:
         s.build_scattering_matrices()

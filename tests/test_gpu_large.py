@@ -33,7 +33,7 @@ def _sampled_interbody(s, wl, R, nrows, seed, tol32, double_float=True):
     assert rel_l2(y32[rows], ref) < tol32
     if double_float:
         ydf = s.interbody(np.ascontiguousarray(sig[:, :1]), precision=2)
-        assert np.abs(ydf[rows, 0] - ref[:, 0]).max() < 1e-11 * np.abs(ref[:, 0]).max()
+        assert np.abs(ydf[rows, 0] - ref[:, 0]).max() < 1e-12 * np.abs(ref[:, 0]).max()
 
 
 def test_mixed27_setup_and_interbody_rows():
