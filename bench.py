@@ -10,9 +10,12 @@ One step = one full solve (right-hand side b = -D^{-1} v, GMRES with the apply
 sigma + D^{-1} B sigma, density in HBM), i.e. every step of the hot path; the
 setup (scattering matrices) is done once before timing.  The headline `value` is
 right-hand-side solves per second of the mixed-precision path (FP32 inter-body sum
-and modal GEMMs inside GMRES, FP64 refinement residual) stopped at a residual that
-gives a density error <= 1e-7 against an FP64-accurate reference (checked every
-run); `fp64_gpu` reports the plain FP64 GPU path on the same geometry.
+and modal GEMMs inside GMRES; refinement residual with its inter-body sum in
+double-float on the FP32 pipe, FP64 accumulation, D^{-1} and Arnoldi in FP64) stopped at
+a residual that gives a density error <= 1e-7 against an FP64-accurate reference
+(checked every run); `mixed_fp64_residual` is the same solve with the residual's sum on
+the FP64 pipe, `fp64_gpu` the plain FP64 GPU path on the same geometry.  Roofline
+denominators are measured on the GPU by the library's microbenchmarks.
 Multi-GPU (torchrun): each rank solves its own right-hand side (independent
 problems, no data-path collective): weak scaling.
 
@@ -37,12 +40,18 @@ METRIC = "RHS solves/s to 1e-7 rel err (mixed+MLP vs FP64 GPU); matvec Ginteract
 WORKLOAD = "spheroids8_258560"
 TOL_MIXED = 1e-8          # residual tolerance of the timed mixed solves
 TOL_REF = 1e-12           # reference density (FP64-accurate, untimed)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
-FP64_PEAK_TFLOPS = 1.25                              # nominal GB300 FP64 (no FP64 entry is measured)
-FLOPS_PER_PAIR = 36       # algorithmic flops of one pair interaction at R = 1 (FMA = 2)
+TOL_FP64 = 1e-11          # the plain FP64 GPU path (density error <= 1e-10 against the reference)
+FLOPS_PER_PAIR = 36       # algorithmic flops of one pair interaction at R = 1 (FMA = 2; see DESIGN.md)
+# FP64 GMRES iterations of the FP64 GPU path on this workload at residual 3e-8, the stop that
+# gives a density error <= 1e-7 (3.9e-8; measured on GB300); the reference arm's oracle
+# solve is its apply time times this count (a full oracle GMRES would take hours)
+ORACLE_ITERS = 16
 # DRAM bytes (read + write) per launch on this workload from one ncu capture of each kernel
 # (profiles/); None for a kernel without a capture of its current version.
 DRAM_BYTES_NCU = {"nbody64_sym_kernel": 25.96e6, "nbody32_sym_kernel": 15.42e6}
+# FP32-pipe (FMA) thread operations per unordered node pair of the lean double-float kernel,
+# counted by ncu (profiles/nbody_dfl_sym_kernel_mixed4_shells.md)
+DFL_OPS_PER_UNORDERED_PAIR = 440
 
 
 def dist_env():
@@ -179,7 +188,7 @@ def run_reference(args, rank, world):
         return
     import workloads as W
     wl = W.spheroids8()
-    iters = 10
+    iters = ORACLE_ITERS
     steps = []
     res = None
     for _ in range(args.warmup + args.steps):
@@ -189,12 +198,43 @@ def run_reference(args, rank, world):
     v = args.steps / sum(timed)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "RHS solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(timed) / args.steps,
+            "ms_per_step_extrapolated": True,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "rhs_per_step": 1, "n_unknowns": 258560},
             "cpu_baseline": {"value": v, "unit": "RHS solves/s", "cores": res["cores"], "kind": "oracle",
                              "sample": res["sample"]},
             "e2e": {"value": v, "unit": "RHS solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def timed_solves(torch, s, d, n, flush, barrier, ev0, ev1):
+    """n solves of the plane wave d, each bracketed by an L2 flush and CUDA events on the
+    solver's stream; returns (per-solve ms list, stats list)."""
+    times, stats = [], []
+    for _ in range(n):
+        flush_l2(torch, flush)
+        barrier()
+        ev0.record()
+        st = s.solve_plane_waves(d)
+        ev1.record()
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        stats.append(st)
+    return times, stats
+
+
+def measured_peaks(s):
+    """Pipe throughputs measured on this GPU by the library's microbenchmarks
+    (hzb_measure_peak): FP32 FMA scalar and packed (TFLOP/s), FP64 FMA (TFLOP/s), the
+    transcendental unit (T ops/s), TF32 through tcgen05 (TFLOP/s)."""
+    out = {}
+    for kind in s.PEAK_KINDS:
+        try:
+            out[kind] = s.measure_peak(kind)
+        except Exception as e:                        # reported, never silently replaced
+            out[kind] = None
+            out[kind + "_error"] = str(e)
+    return out
 
 
 def main():
@@ -236,7 +276,7 @@ def main():
     wl = W.spheroids8()
     d = rank_direction(rank)
     opt = Options(device=local, precision=HZB_PREC_MIXED_FP32, gmres_tol=TOL_MIXED, inner_tol=1e-5, max_outer=6,
-                  verify_final=0)
+                  verify_final=0, residual=HZB_PREC_DOUBLE_FLOAT)
     s = Solver.from_workload(wl, opt, stream=torch.cuda.current_stream().cuda_stream)
     t_pre = time.perf_counter()
     s.build_scattering_matrices()
@@ -244,34 +284,30 @@ def main():
     tuned = s.autotune(1, 1)            # FP32 inter-body kernel variant and launch shape
     kernels = s.tuned_config(1)         # what the timed solves launch
     N = s.N
+    peaks = measured_peaks(s)
 
-    # FP64-accurate reference density (mixed refinement to 1e-12, untimed)
-    s.set_options(gmres_tol=TOL_REF)
+    # FP64-accurate reference density: mixed refinement to 1e-12 with the refinement residual
+    # on the FP64 pipe (independent of the double-float kernel the timed solves use), untimed
+    s.set_options(gmres_tol=TOL_REF, residual=HZB_PREC_FP64)
     st_ref = s.solve_plane_waves(d)
     sig_ref = s.get_density()[:, 0].copy()
-    s.set_options(gmres_tol=TOL_MIXED)
+    s.set_options(gmres_tol=TOL_MIXED, residual=HZB_PREC_DOUBLE_FLOAT)
+
+    def err_vs_ref():
+        sig = s.get_density()[:, 0]
+        return float(np.linalg.norm(sig - sig_ref) / np.linalg.norm(sig_ref))
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    # headline: mixed precision, refinement residual's inter-body sum in double-float
     for _ in range(args.warmup):
         s.solve_plane_waves(d)
     barrier()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    times, stats = [], []
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush_l2(torch, flush)
-            barrier()
-            ev0.record()
-            st = s.solve_plane_waves(d)
-            ev1.record()
-            torch.cuda.synchronize()
-            times.append(ev0.elapsed_time(ev1))
-            stats.append(st)
-    total_ms = sum(times)
-    total_ms = max_over_ranks(total_ms, dist, "cuda")
-    sig = s.get_density()[:, 0]
-    dens_err = float(np.linalg.norm(sig - sig_ref) / np.linalg.norm(sig_ref))
+        times, stats = timed_solves(torch, s, d, args.steps, flush, barrier, ev0, ev1)
+    total_ms = max_over_ranks(sum(times), dist, "cuda")
+    dens_err = err_vs_ref()
 
     # end to end through the C ABI with host buffers: H2D of v, solve, D2H of sigma
     x, _, _ = s.get_nodes()
@@ -288,49 +324,33 @@ def main():
             e2e_t.append(time.perf_counter() - t0)
     e2e_val = world * len(e2e_t) / sum(e2e_t)
 
-    # mixed precision with the refinement residual in double-float on the FP32 pipe
-    s.set_options(residual=HZB_PREC_DOUBLE_FLOAT)
-    s.autotune(1, 1)
-    for _ in range(max(1, args.warmup)):
-        s.solve_plane_waves(d)
-    dft, dfst = [], []
-    for _ in range(args.steps):
-        flush_l2(torch, flush)
-        barrier()
-        ev0.record()
-        stdf = s.solve_plane_waves(d)
-        ev1.record()
-        torch.cuda.synchronize()
-        dft.append(ev0.elapsed_time(ev1))
-        dfst.append(stdf)
-    sigdf = s.get_density()[:, 0]
-    mixed_df = {"value": 1e3 * len(dft) / sum(dft), "unit": "RHS solves/s", "ms_per_solve": sum(dft) / len(dft),
-                "density_err_vs_fp64_reference": float(np.linalg.norm(sigdf - sig_ref) / np.linalg.norm(sig_ref)),
-                "residual_kernel": ("nbody_df_sym_kernel" if kernels["fp64_kernel"] == "nbody64_sym_kernel"
-                                    else "nbody_df_kernel") + " (double-float, ~48-bit significand)",
-                "nbody_df_ms_per_launch": dfst[-1].t_nbodydf_ms / max(dfst[-1].n_nbodydf, 1),
-                "nbody32_ms_per_launch": dfst[-1].t_nbody32_ms / max(dfst[-1].n_nbody32, 1),
-                "outer_iterations": dfst[-1].outer_iterations, "inner_iterations": dfst[-1].iterations}
+    # the same solve with the refinement residual's inter-body sum on the FP64 pipe
     s.set_options(residual=HZB_PREC_FP64)
+    s.solve_plane_waves(d)
+    ft, fst = timed_solves(torch, s, d, max(1, min(args.steps, 2)), flush, barrier, ev0, ev1)
+    mixed_fp64 = {"value": 1e3 * len(ft) / sum(ft), "unit": "RHS solves/s", "ms_per_solve": sum(ft) / len(ft),
+                  "density_err_vs_fp64_reference": err_vs_ref(),
+                  "residual_kernel": kernels["fp64_kernel"] + " (FP64)",
+                  "nbody64_ms_per_launch": fst[-1].t_nbody64_ms / max(fst[-1].n_nbody64, 1),
+                  "outer_iterations": fst[-1].outer_iterations, "inner_iterations": fst[-1].iterations}
+    s.set_options(residual=HZB_PREC_DOUBLE_FLOAT)
 
     # FP64 GPU path on the same geometry
     fp64 = None
     if args.fp64_steps > 0:
-        s.set_options(precision=HZB_PREC_FP64, gmres_tol=1e-9)
-        ft = []
-        for _ in range(args.fp64_steps):
-            flush_l2(torch, flush)
-            barrier()
-            ev0.record()
-            st64 = s.solve_plane_waves(d)
-            ev1.record()
-            torch.cuda.synchronize()
-            ft.append(ev0.elapsed_time(ev1))
-        sig64 = s.get_density()[:, 0]
+        s.set_options(precision=HZB_PREC_FP64, gmres_tol=TOL_FP64)
+        ft, fst = timed_solves(torch, s, d, args.fp64_steps, flush, barrier, ev0, ev1)
+        st64 = fst[-1]
+        per64 = st64.t_nbody64_ms / max(st64.n_nbody64, 1)
+        pairs = interbody_pairs(wl)
+        ach64 = FLOPS_PER_PAIR * pairs / (per64 * 1e-3) / 1e12
         fp64 = {"value": 1e3 * len(ft) / sum(ft), "unit": "RHS solves/s", "ms_per_solve": sum(ft) / len(ft),
-                "iterations": st64.iterations, "tol": 1e-9,
-                "density_err": float(np.linalg.norm(sig64 - sig_ref) / np.linalg.norm(sig_ref)),
-                "nbody64_ms_per_apply": st64.t_nbody64_ms / max(st64.n_nbody64, 1)}
+                "iterations": st64.iterations, "tol": TOL_FP64, "density_err": err_vs_ref(),
+                "nbody64_ms_per_apply": per64,
+                "roofline": {"kernel": kernels["fp64_kernel"], "bound": "alu", "achieved": ach64,
+                             "peak": peaks.get("dfma"), "unit": "TFLOP/s",
+                             "frac": ach64 / peaks["dfma"] if peaks.get("dfma") else None,
+                             "peak_source": "measured DFMA throughput (hzb_measure_peak)"}}
         s.set_options(precision=HZB_PREC_MIXED_FP32, gmres_tol=TOL_MIXED)
 
     # accelerated scheme (Sec. 5): skeletons once per geometry (untimed setup, reported),
@@ -344,42 +364,18 @@ def main():
         nk = s.reduced_size
         for _ in range(max(1, args.warmup)):
             s.solve_plane_waves(d)
-        at, ast = [], []
-        for _ in range(args.steps):
-            flush_l2(torch, flush)
-            barrier()
-            ev0.record()
-            sta = s.solve_plane_waves(d)
-            ev1.record()
-            torch.cuda.synchronize()
-            at.append(ev0.elapsed_time(ev1))
-            ast.append(sta)
-        siga = s.get_density()[:, 0]
-        # the same with the refinement residual in double-float
-        s.set_options(residual=HZB_PREC_DOUBLE_FLOAT)
-        s.solve_plane_waves(d)
-        adt = []
-        for _ in range(args.steps):
-            flush_l2(torch, flush)
-            barrier()
-            ev0.record()
-            s.solve_plane_waves(d)
-            ev1.record()
-            torch.cuda.synchronize()
-            adt.append(ev0.elapsed_time(ev1))
-        sigadf = s.get_density()[:, 0]
+        at, ast = timed_solves(torch, s, d, args.steps, flush, barrier, ev0, ev1)
+        erra = err_vs_ref()
         s.set_options(residual=HZB_PREC_FP64)
+        s.solve_plane_waves(d)
+        aft, _ = timed_solves(torch, s, d, max(1, min(args.steps, 3)), flush, barrier, ev0, ev1)
+        errafp = err_vs_ref()
         s.set_options(precision=HZB_PREC_FP64, gmres_tol=1e-9)
         s.solve_plane_waves(d)
-        flush_l2(torch, flush)
-        barrier()
-        ev0.record()
-        sta64 = s.solve_plane_waves(d)
-        ev1.record()
-        torch.cuda.synchronize()
-        t64a = ev0.elapsed_time(ev1)
-        siga64 = s.get_density()[:, 0]
-        s.set_options(precision=HZB_PREC_MIXED_FP32, gmres_tol=TOL_MIXED)
+        a64t, a64s = timed_solves(torch, s, d, 1, flush, barrier, ev0, ev1)
+        erra64 = err_vs_ref()
+        sta64 = a64s[-1]
+        s.set_options(precision=HZB_PREC_MIXED_FP32, gmres_tol=TOL_MIXED, residual=HZB_PREC_DOUBLE_FLOAT)
         s.set_acceleration(False)
         kpb = [s.get_skeleton_size(q) for q in range(len(wl.bodies))]
         rpairs = float(sum(kpb)) ** 2 - float(sum(k * k for k in kpb))
@@ -387,50 +383,51 @@ def main():
         ach = FLOPS_PER_PAIR * rpairs / (per64 * 1e-3) / 1e12
         accel = {"value": 1e3 * len(at) / sum(at), "unit": "RHS solves/s", "ms_per_solve": sum(at) / len(at),
                  "eps": args.accel_eps, "reduced_unknowns": nk, "skeleton_per_body": kpb,
-                 "compress_s": t_compress,
-                 "density_err_vs_fp64_reference": float(np.linalg.norm(siga - sig_ref) / np.linalg.norm(sig_ref)),
+                 "compress_s": t_compress, "residual": "double-float inter-body sum",
+                 "density_err_vs_fp64_reference": erra,
                  "outer_iterations": ast[-1].outer_iterations, "inner_iterations": ast[-1].iterations,
-                 "nbody64_ms_per_launch": ast[-1].t_nbody64_ms / max(ast[-1].n_nbody64, 1),
+                 "nbodydf_ms_per_launch": ast[-1].t_nbodydf_ms / max(ast[-1].n_nbodydf, 1),
                  "nbody32_ms_per_launch": ast[-1].t_nbody32_ms / max(ast[-1].n_nbody32, 1),
                  "gpu_launches_per_solve": ast[-1].kernel_launches,
-                 "mixed_df_residual": {"value": 1e3 * len(adt) / sum(adt), "unit": "RHS solves/s",
-                                       "ms_per_solve": sum(adt) / len(adt),
-                                       "density_err_vs_fp64_reference":
-                                           float(np.linalg.norm(sigadf - sig_ref) / np.linalg.norm(sig_ref))},
-                 "fp64": {"value": 1e3 / t64a, "unit": "RHS solves/s", "ms_per_solve": t64a, "tol": 1e-9,
-                          "iterations": sta64.iterations,
-                          "density_err": float(np.linalg.norm(siga64 - sig_ref) / np.linalg.norm(sig_ref))},
+                 "mixed_fp64_residual": {"value": 1e3 * len(aft) / sum(aft), "unit": "RHS solves/s",
+                                         "ms_per_solve": sum(aft) / len(aft),
+                                         "density_err_vs_fp64_reference": errafp},
+                 "fp64": {"value": 1e3 / a64t[0], "unit": "RHS solves/s", "ms_per_solve": a64t[0], "tol": 1e-9,
+                          "iterations": sta64.iterations, "density_err": erra64},
                  "roofline": {"kernel": kernels["fp64_kernel"] + " on skeleton nodes", "bound": "alu",
-                              "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": ach / FP64_PEAK_TFLOPS, "pairs_per_apply": rpairs,
-                              "ms_per_launch": per64}}
+                              "achieved": ach, "peak": peaks.get("dfma"), "unit": "TFLOP/s",
+                              "frac": ach / peaks["dfma"] if peaks.get("dfma") else None,
+                              "pairs_per_apply": rpairs, "ms_per_launch": per64}}
 
-    # dominant kernel of the timed solves and its live roofline
+    # dominant kernel of the timed solves and its live roofline (CUDA events on the solver's
+    # stream around every inter-body launch, summed by the library)
     t32 = sum(x.t_nbody32_ms for x in stats); n32 = sum(x.n_nbody32 for x in stats)
-    t64 = sum(x.t_nbody64_ms for x in stats); n64 = sum(x.n_nbody64 for x in stats)
+    tdf = sum(x.t_nbodydf_ms for x in stats); ndf = sum(x.n_nbodydf for x in stats)
     pairs = interbody_pairs(wl)
-    if t32 >= t64:
-        per = t32 / max(n32, 1)
-        ach = FLOPS_PER_PAIR * pairs / (per * 1e-3) / 1e12
-        roof = {"kernel": kernels["fp32_kernel"], "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                "traffic": DRAM_BYTES_NCU.get(kernels["fp32_kernel"]),
-                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 x 2.07 GHz (unit counts and clock)",
-                "ms_per_launch": per}
-    else:
-        per = t64 / max(n64, 1)
-        ach = FLOPS_PER_PAIR * pairs / (per * 1e-3) / 1e12
-        roof = {"kernel": kernels["fp64_kernel"], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": DRAM_BYTES_NCU.get(kernels["fp64_kernel"]),
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s", "ms_per_launch": per}
-    gint32 = pairs / (t32 / max(n32, 1) * 1e-3) / 1e9 if n32 else None
-    gint64 = pairs / (t64 / max(n64, 1) * 1e-3) / 1e9 if n64 else None
+    per32 = t32 / max(n32, 1)
+    ach32 = FLOPS_PER_PAIR * pairs / (per32 * 1e-3) / 1e12
+    p32 = peaks.get("ffma2") or peaks.get("ffma")
+    roof32 = {"kernel": kernels["fp32_kernel"], "bound": "alu", "achieved": ach32, "peak": p32, "unit": "TFLOP/s",
+              "frac": ach32 / p32 if p32 else None, "traffic": DRAM_BYTES_NCU.get(kernels["fp32_kernel"]),
+              "peak_source": "measured packed-FP32 FMA throughput (hzb_measure_peak ffma2)",
+              "ms_per_launch": per32, "share_of_step": t32 / sum(times)}
+    perdf = tdf / max(ndf, 1)
+    opsdf = DFL_OPS_PER_UNORDERED_PAIR * pairs / 2
+    roofdf = {"kernel": "nbody_dfl_sym_kernel", "bound": "alu", "ms_per_launch": perdf,
+              "share_of_step": tdf / sum(times),
+              "achieved": FLOPS_PER_PAIR * pairs / (perdf * 1e-3) / 1e12 if ndf else None, "unit": "TFLOP/s",
+              "note": "achieved counts the pair kernel's 36 algorithmic flops per ordered pair; in double-float "
+                      "each unordered pair executes %d FP32-pipe operations (ncu)" % DFL_OPS_PER_UNORDERED_PAIR,
+              "fp32_pipe_ops_per_s": opsdf / (perdf * 1e-3) / 1e12 if ndf else None,
+              "fp32_pipe_frac": (opsdf / (perdf * 1e-3) / 1e12) / (peaks["ffma"] / 2) if ndf and peaks.get("ffma")
+              else None}
+    roof = roof32 if t32 >= tdf else dict(roofdf, peak=p32, frac=roofdf["fp32_pipe_frac"])
+    gint32 = pairs / (per32 * 1e-3) / 1e9 if n32 else None
+    gintdf = pairs / (perdf * 1e-3) / 1e9 if ndf else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        iters = fp64["iterations"] if fp64 else max(stats[-1].iterations, 1)
-        cpu = cpu_oracle_baseline(wl, iters)
+        cpu = cpu_oracle_baseline(wl, ORACLE_ITERS)
         cpu.pop("t_apply_s", None)
 
     if rank == 0:
@@ -438,23 +435,29 @@ def main():
         line = {
             "metric": METRIC, "value": whole_job_rate(K, 1, world, total_ms), "unit": "RHS solves/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_unknowns": N, "rhs_per_step_per_gpu": 1,
-                       "precision": "FP32 inter-body sum and modal GEMMs, FP64 refinement residual and Arnoldi",
+                       "precision": "FP32 inter-body sum and modal GEMMs inside GMRES; refinement residual: "
+                                    "inter-body sum in double-float (pair kernels on the FP32 pipe, FP64 "
+                                    "accumulation into y), D^{-1} and Arnoldi in FP64",
                        "tol_residual": TOL_MIXED, "density_err_vs_fp64_reference": dens_err,
+                       "reference": "mixed refinement to %g with the FP64-pipe residual" % TOL_REF,
                        "l2": "flushed (512 MB write) between timed steps",
                        "outer_iterations": stats[-1].outer_iterations, "inner_iterations": stats[-1].iterations,
-                       "fp64_residual_applies": stats[-1].n_nbody64, "fp32_applies": stats[-1].n_nbody32,
-                       "stop_rule": "a-priori refinement bound after one FP64 residual (verify_final=0); "
+                       "df_residual_applies": stats[-1].n_nbodydf, "fp32_applies": stats[-1].n_nbody32,
+                       "stop_rule": "a-priori refinement bound after one high-precision residual (verify_final=0); "
                                     "density error checked against the reference every run",
                        "autotuned_fp32_ms_per_launch": float(tuned[0]), "kernels": kernels,
                        "t_pre_s": t_pre},
-            "matvec_ginteractions_per_s": {"fp32": gint32, "fp64": gint64,
+            "matvec_ginteractions_per_s": {"fp32": gint32, "double_float": gintdf,
+                                            "fp64": fp64 and pairs / (fp64["nbody64_ms_per_apply"] * 1e-3) / 1e9,
                                             "pairs_per_apply": pairs},
+            "mixed_fp64_residual": mixed_fp64,
             "fp64_gpu": fp64,
-            "mixed_df_residual": mixed_df,
             "accelerated": accel,
             "roofline": roof,
+            "roofline_residual_kernel": roofdf,
+            "measured_peaks": peaks,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "RHS solves/s", "h2d_bytes_per_step": int(N * 16),
                     "d2h_bytes_per_step": int(N * 16)},

@@ -279,6 +279,16 @@ hzb_status hzb_set_interbody_engine(hzb_ctx *ctx, int engine);
  * 1/64 of the FP32 rate). */
 hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *ctx, int engine);
 
+/* Measured throughput of one arithmetic pipe of the context's GPU, the denominators of
+ * the kernels' rooflines (not part of the paper): kind 0 = FP32 fused multiply-add
+ * (TFLOP/s, FMA = 2), 1 = the same with packed f32x2 instructions, 2 = FP64 fused
+ * multiply-add (TFLOP/s), 3 = transcendental unit (T operations/s: one rsqrt, sin and
+ * cos per round), 4 = TF32 tensor cores through tcgen05.mma (dense TFLOP/s, M = 128,
+ * N = 256, operands resident in shared memory).  Each runs for tens of milliseconds on
+ * every SM, timed with CUDA events on the context's stream.  Errors: HZB_EINVAL (kind
+ * or null value), HZB_ETIMEOUT (a tensor-core wait ran out), HZB_ECUDA. */
+hzb_status hzb_measure_peak(hzb_ctx *ctx, int kind, double *value);
+
 /* Copy A~_p (which = 0) or S_p (which = 1) of the shape of body `body`, mode p in
  * 0..M, to host out (N_G x N_G complex, row-major). */
 hzb_status hzb_get_modal_block(hzb_ctx *ctx, int body, int p, int which, double *out);

@@ -142,6 +142,7 @@ def lib():
         "hzb_reduced_size": (i, [p, ctypes.POINTER(ctypes.c_longlong)]),
         "hzb_apply_reduced": (i, [p, i, p, p, i]),
         "hzb_interp_decomp": (i, [p, i, i, p, d, ctypes.POINTER(i), p, p]),
+        "hzb_measure_peak": (i, [p, i, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -318,6 +319,15 @@ class Solver:
         best = np.zeros(2)
         self._check(lib().hzb_autotune(self._h, int(R), int(which), _ptr(best)))
         return best
+
+    PEAK_KINDS = ("ffma", "ffma2", "dfma", "mufu", "tf32_tcgen05")
+
+    def measure_peak(self, kind: str) -> float:
+        """Measured throughput of one pipe (hzb_measure_peak): TFLOP/s for the FMA and
+        tensor-core kinds, T operations/s for the transcendental unit ("mufu")."""
+        v = ctypes.c_double()
+        self._check(lib().hzb_measure_peak(self._h, self.PEAK_KINDS.index(kind), ctypes.byref(v)))
+        return v.value
 
     FP32_KERNELS = ("nbody32_kernel", "nbody32x2_kernel", "nbody32_sym_kernel", "nbody_tc_kernel", "nbody_tc5_kernel")
 

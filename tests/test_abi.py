@@ -19,7 +19,8 @@ def test_header_declares_the_boundary():
               "hzb_interbody", "hzb_local_inverse", "hzb_eval_field", "hzb_last_error",
               "hzb_save_scattering", "hzb_load_scattering", "hzb_add_body_curve",
               "hzb_compress", "hzb_set_skeleton", "hzb_get_skeleton", "hzb_set_acceleration",
-              "hzb_reduced_size", "hzb_apply_reduced", "hzb_interp_decomp"):
+              "hzb_reduced_size", "hzb_apply_reduced", "hzb_interp_decomp", "hzb_measure_peak",
+              "hzb_local_inverse_noalloc"):
         assert n in names
 
 
