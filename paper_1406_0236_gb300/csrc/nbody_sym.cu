@@ -164,7 +164,10 @@ nbody64_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict
 // each register pair, and meets one source per step as above, so one f32x2
 // instruction serves two unordered node pairs.  The rotating source sums keep the
 // two halves apart and add them at the end of the tile.  Densities come pre-weighted
-// in FP32 (weighted_sigma32); the phase is reduced as in nbody32x2_kernel.
+// in FP32 (weighted_sigma32).  With E = e^{ikr}/r, both directions' kernels are
+// G = X P + Q, P = E (1 - ikr), Q = -i eta E (X = n.d / r^2 with the source-side normal),
+// so that P and Q, computed once per node pair, leave two FMAs per direction;
+// e^{ikr} comes straight from the transcendental unit (its own argument scaling).
 template <int RC, int TP>
 __global__ void __launch_bounds__(SYM_T / (2 * TP), 1)
 nbody32_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict__ blocks, int R,
@@ -181,8 +184,8 @@ nbody32_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict
     const TargetBlock bi = blocks[pr.x], bj = blocks[pr.y];
     const int r0 = blockIdx.y * RC;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    f2x tx[TP], ty[TP], tz[TP], mx[TP], my[TP], mz[TP];
-    f2x wr[TP][RC], wi[TP][RC], nwr[TP][RC], atx[TP][RC], aty[TP][RC];
+    f2x tx[TP], ty[TP], tz[TP], mx[TP], my[TP], mz[TP];      // target positions, negated normals
+    f2x wr[TP][RC], wi[TP][RC], nwi[TP][RC], atx[TP][RC], aty[TP][RC];
 #pragma unroll
     for (int p = 0; p < TP; ++p) {
         float4 P[2], Q[2];
@@ -198,18 +201,17 @@ nbody32_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict
                 V[h][c] = (live && r0 + c < R) ? sw[(size_t)(bi.start + t) * R + r0 + c] : make_float2(0.f, 0.f);
         }
         tx[p] = f2_pack(P[0].x, P[1].x); ty[p] = f2_pack(P[0].y, P[1].y); tz[p] = f2_pack(P[0].z, P[1].z);
-        mx[p] = f2_pack(Q[0].x, Q[1].x); my[p] = f2_pack(Q[0].y, Q[1].y); mz[p] = f2_pack(Q[0].z, Q[1].z);
+        mx[p] = f2_pack(-Q[0].x, -Q[1].x); my[p] = f2_pack(-Q[0].y, -Q[1].y); mz[p] = f2_pack(-Q[0].z, -Q[1].z);
 #pragma unroll
         for (int c = 0; c < RC; ++c) {
             wr[p][c] = f2_pack(V[0][c].x, V[1][c].x);
             wi[p][c] = f2_pack(V[0][c].y, V[1][c].y);
-            nwr[p][c] = f2_pack(-V[0][c].x, -V[1][c].x);
+            nwi[p][c] = f2_pack(-V[0][c].y, -V[1][c].y);
             atx[p][c] = aty[p][c] = 0ull;
         }
     }
     const bool warp_live = warp * 32 < bi.count;
-    const f2x k2 = f2_splat(k), nk2 = f2_splat(-k), eta2 = f2_splat(eta), kt2 = f2_splat(kt);
-    const f2x rnd2 = f2_splat(12582912.0f), twopi2 = f2_splat(6.283185307179586f);
+    const f2x k2 = f2_splat(k), nk2 = f2_splat(-k), eta2 = f2_splat(eta), neta2 = f2_splat(-eta);
     for (int j0 = 0; j0 < bj.count; j0 += SYM_S) {
         const int cnt = min(SYM_S, bj.count - j0);
         __syncthreads();
@@ -253,30 +255,32 @@ nbody32_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict
                     float r2a, r2b;
                     f2_unpack(r2, r2a, r2b);
                     const f2x ir = f2_pack(rsqrtf(r2a), rsqrtf(r2b));
-                    const f2x ir2 = f2_mul(ir, ir), eir = f2_mul(eta2, ir);
-                    const f2x t = f2_mul(f2_mul(r2, ir), kt2);
-                    const f2x th = f2_mul(f2_sub(t, f2_sub(f2_add(t, rnd2), rnd2)), twopi2);
-                    float tha, thb, sa, ca, sb, cb;
-                    f2_unpack(th, tha, thb);
-                    __sincosf(tha, &sa, &ca);
-                    __sincosf(thb, &sb, &cb);
-                    const f2x s2 = f2_pack(sa, sb), c2 = f2_pack(ca, cb);
-                    // target <- source q
+                    const f2x ir2 = f2_mul(ir, ir);
+                    const f2x r = f2_mul(r2, ir);
+                    const f2x kr = f2_mul(r, k2), nkr = f2_mul(r, nk2);
+                    // e^{ikr}: the transcendental unit reduces the argument itself (its
+                    // scaling to turns rounds like an explicit reduction would)
+                    float kra, krb, sa, ca, sb, cb;
+                    f2_unpack(kr, kra, krb);
+                    __sincosf(kra, &sa, &ca);
+                    __sincosf(krb, &sb, &cb);
+                    // E = e^{ikr} / r;  G = E [X - i (k r X + eta)] = X P + Q,
+                    // P = E (1 - i k r), Q = -i eta E: shared by both directions
+                    const f2x Er = f2_mul(f2_pack(ca, cb), ir), Ei = f2_mul(f2_pack(sa, sb), ir);
+                    const f2x Pr = f2_fma(Ei, kr, Er), Pi = f2_fma(Er, nkr, Ei);
+                    const f2x Qr = f2_mul(eta2, Ei), Qi = f2_mul(neta2, Er);
+                    // target <- source q: X1 = n_q.d / r^2
                     const f2x X1 = f2_mul(f2_fma(snx, dx, f2_fma(sny, dy, f2_mul(snz, dz))), ir2);
-                    const f2x A1 = f2_mul(X1, ir), B1 = f2_fma(k2, X1, eir);
-                    const f2x g1r = f2_fma(c2, A1, f2_mul(s2, B1));
-                    const f2x g1i = f2_sub(f2_mul(s2, A1), f2_mul(c2, B1));
-                    // source q <- target (d reversed)
-                    const f2x X2p = f2_mul(f2_fma(mx[p], dx, f2_fma(my[p], dy, f2_mul(mz[p], dz))), ir2);
-                    const f2x A2n = f2_mul(X2p, ir), B2 = f2_fma(nk2, X2p, eir);
-                    const f2x g2r = f2_sub(f2_mul(s2, B2), f2_mul(c2, A2n));
-                    const f2x h = f2_fma(s2, A2n, f2_mul(c2, B2));
+                    const f2x g1r = f2_fma(X1, Pr, Qr), g1i = f2_fma(X1, Pi, Qi);
+                    // source q <- target (d reversed): X2 = -m.d / r^2 (the target normals are stored negated)
+                    const f2x X2 = f2_mul(f2_fma(mx[p], dx, f2_fma(my[p], dy, f2_mul(mz[p], dz))), ir2);
+                    const f2x g2r = f2_fma(X2, Pr, Qr), g2i = f2_fma(X2, Pi, Qi);
 #pragma unroll
                     for (int c = 0; c < RC; ++c) {
                         atx[p][c] = f2_fma(g1r, swr[c], f2_fma(g1i, nswi[c], atx[p][c]));
                         aty[p][c] = f2_fma(g1r, swi[c], f2_fma(g1i, swr[c], aty[p][c]));
-                        asx[c] = f2_fma(g2r, wr[p][c], f2_fma(h, wi[p][c], asx[c]));
-                        asy[c] = f2_fma(g2r, wi[p][c], f2_fma(h, nwr[p][c], asy[c]));
+                        asx[c] = f2_fma(g2r, wr[p][c], f2_fma(g2i, nwi[p][c], asx[c]));
+                        asy[c] = f2_fma(g2r, wi[p][c], f2_fma(g2i, wr[p][c], asy[c]));
                     }
                 }
 #pragma unroll
