@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RHS solves/s to 1e-7 rel err (mixed+MLP vs FP64 GPU); matvec Ginteractions/s"
 WORKLOAD = "spheroids8_258560"
-TOL_MIXED = 1e-8          # residual tolerance of the timed mixed solves
+TOL_MIXED = 1e-7          # residual tolerance of the timed mixed solves (density error ~6e-9)
 TOL_REF = 1e-12           # reference density (FP64-accurate, untimed)
 TOL_FP64 = 1e-11          # the plain FP64 GPU path (density error <= 1e-10 against the reference)
 FLOPS_PER_PAIR = 36       # algorithmic flops of one pair interaction at R = 1 (FMA = 2)

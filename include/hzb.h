@@ -298,6 +298,16 @@ hzb_status hzb_get_modal_block(hzb_ctx *ctx, int body, int p, int which, double 
 hzb_status hzb_interbody(hzb_ctx *ctx, int R, const double *sigma, double *y,
                          int on_device, int precision);
 
+/* Rows of y = B sigma (Sec. 3.3) for the targets of bodies [body_begin, body_end) only,
+ * against all sources: sigma is the full N x R block, y receives the rows of those
+ * bodies (n_rows x R, in node order).  The rank-local inter-body sum of a solve whose
+ * bodies are partitioned over several GPUs (each rank owns a contiguous body range and
+ * all-gathers sigma before this call).  precision: HZB_PREC_FP64 or HZB_PREC_MIXED_FP32
+ * (one-directional kernels).  Errors: HZB_EINVAL (empty or out-of-range body range,
+ * double-float precision), HZB_ESTATE (no bodies). */
+hzb_status hzb_interbody_bodies(hzb_ctx *ctx, int R, const double *sigma, int body_begin, int body_end, double *y,
+                                int on_device, int precision);
+
 /* tau = alpha * sigma + beta * D^{-1} y (the per-body FFT -> S_p -> inverse FFT of
  * the Remark after Eq. (precond)).  sigma may be NULL when alpha = 0.  Always the
  * direct D^{-1} on all N nodes, also while the accelerated scheme is on. */

@@ -143,6 +143,7 @@ def lib():
         "hzb_apply_reduced": (i, [p, i, p, p, i]),
         "hzb_interp_decomp": (i, [p, i, i, p, d, ctypes.POINTER(i), p, p]),
         "hzb_measure_peak": (i, [p, i, ctypes.POINTER(d)]),
+        "hzb_interbody_bodies": (i, [p, i, p, i, i, p, i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -376,6 +377,19 @@ class Solver:
     def interbody(self, sigma, precision: int = HZB_PREC_FP64):
         a, out, R, dev = self._io(sigma)
         self._check(lib().hzb_interbody(self._h, R, _ptr(a), _ptr(out), dev, int(precision)))
+        return out
+
+    def interbody_bodies(self, sigma, body_begin: int, body_end: int, precision: int = HZB_PREC_FP64):
+        """Rows of B sigma for the targets of bodies [body_begin, body_end) (sigma: all N rows)."""
+        a, _, R, dev = self._io(sigma)
+        offs = np.concatenate([[0], np.cumsum(self._body_n)]).astype(int)
+        if not (0 <= body_begin < body_end <= len(self._body_n)):
+            raise ValueError("body range out of bounds or empty")
+        nr = int(offs[body_end] - offs[body_begin])
+        shape = (nr,) if a.ndim == 1 else (nr, R)
+        out = a.new_empty(shape) if dev else np.empty(shape, dtype=np.complex128)
+        self._check(lib().hzb_interbody_bodies(self._h, R, _ptr(a), int(body_begin), int(body_end), _ptr(out), dev,
+                                               int(precision)))
         return out
 
     def local_inverse(self, y, sigma=None, alpha: float = 0.0, beta: float = 1.0, precision: int = HZB_PREC_FP64):

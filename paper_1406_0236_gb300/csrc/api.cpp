@@ -378,6 +378,46 @@ hzb_status hzb_interbody(hzb_ctx *c, int R, const double *sigma, double *y, int 
     return finish_out(c, out, y, n, on_device);
 }
 
+hzb_status hzb_interbody_bodies(hzb_ctx *c, int R, const double *sigma, int body_begin, int body_end, double *y,
+                                int on_device, int precision)
+{
+    HZB_GUARD(c);
+    hzb_status st = check_apply_args(c, R, sigma, y, precision, false);
+    if (st) return st;
+    if (precision == HZB_PREC_DOUBLE_FLOAT) return fail(c, HZB_EINVAL, "body-range sums run in FP64 or FP32");
+    if (body_begin < 0 || body_end > (int)c->bodies.size() || body_begin >= body_end)
+        return fail(c, HZB_EINVAL, "body range out of bounds or empty");
+    if ((st = make_nodes(c))) return st;
+    const size_t n = (size_t)c->N * R;
+    const double2 *s;
+    if ((st = stage_in(c, c->io_in, sigma, n, on_device, &s))) return st;
+    if (check_cuda(c, c->w_c.ensure(n), "alloc")) return HZB_ENOMEM;
+    const long long r0 = c->bodies[body_begin].offset;
+    const long long r1 = c->bodies[body_end - 1].offset + c->bodies[body_end - 1].n_nodes;
+    // the one-directional kernels over the TargetBlocks of the range only
+    c->tblock_off = c->body_block0[body_begin];
+    c->tune_limit_blocks = c->body_block0[body_end] - c->body_block0[body_begin];
+    if (precision == HZB_PREC_FP64) {
+        const int tpt = c->tune64_tpt > 0 ? c->tune64_tpt : 1;
+        const int ns = c->tune64_split > 0 ? c->tune64_split : default_nsplit(c, R, tpt);
+        st = interbody64_cfg(c, R, s, c->w_c.ptr, tpt, ns);
+    } else {
+        const int tpt = c->tune32_tpt > 0 ? c->tune32_tpt : 4;
+        const int ns = c->tune32_split > 0 ? c->tune32_split : default_nsplit(c, R, tpt);
+        st = interbody32_cfg(c, R, s, c->w_c.ptr, tpt, ns, true);
+    }
+    c->tblock_off = 0;
+    c->tune_limit_blocks = 0;
+    if (st) return st;
+    const size_t nr = (size_t)(r1 - r0) * R;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (check_cuda(c, cudaMemcpyAsync(y, c->w_c.ptr + (size_t)r0 * R, nr * sizeof(double2), kind, c->stream),
+                   "copy rows") ||
+        check_cuda(c, cudaStreamSynchronize(c->stream), "body-range sum"))
+        return HZB_ECUDA;
+    return HZB_OK;
+}
+
 hzb_status hzb_local_inverse(hzb_ctx *c, int R, const double *y, const double *sigma, double alpha, double beta,
                              double *tau, int on_device, int precision)
 {

@@ -150,6 +150,8 @@ struct hzb_ctx {
     hzb::DevBuf<int> body_of;
     hzb::DevBuf<hzb::TargetBlock> tblocks;
     int n_tblocks = 0;
+    std::vector<int> body_block0;   // first TargetBlock of each body (and the total at the end)
+    int tblock_off = 0;             // one-directional kernels: first TargetBlock launched (body-range sums)
     hzb::DevBuf<double> body_xf;    // per body: c[3], rot[9]
 
     // workspaces

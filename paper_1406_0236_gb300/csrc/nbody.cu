@@ -381,7 +381,7 @@ hzb_status ensure_sctab(hzb_ctx *c)
 template <int RC, int TPT>
 static void launch64(hzb_ctx *c, dim3 g, int N, int R, int chunk, const double2 *sigma, double2 *out, size_t stride)
 {
-    nbody64_kernel<RC, TPT><<<g, TBLOCK / TPT, 0, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos64.ptr,
+    nbody64_kernel<RC, TPT><<<g, TBLOCK / TPT, 0, c->stream>>>(c->tblocks.ptr + c->tblock_off, N, R, chunk, c->pos64.ptr,
                                                                c->nrm64.ptr, sigma, c->sctab.ptr, c->k, c->eta,
                                                                c->k * (SC_N / (2.0 * M_PI)), out, stride);
 }
@@ -391,7 +391,7 @@ static void launch32(hzb_ctx *c, dim3 g, int N, int R, int chunk, const float2 *
                      size_t stride)
 {
     nbody32_kernel<RC, TPT><<<g, TBLOCK / TPT, 0, c->stream>>>(
-        c->tblocks.ptr, N, R, chunk, c->pos32.ptr, c->nrm32.ptr, sigma, (float)c->k, (float)c->eta,
+        c->tblocks.ptr + c->tblock_off, N, R, chunk, c->pos32.ptr, c->nrm32.ptr, sigma, (float)c->k, (float)c->eta,
         (float)(c->k / (2.0 * M_PI)), part, y, stride);
 }
 
@@ -408,7 +408,7 @@ static void launch32x2(hzb_ctx *c, dim3 g, int N, int R, int chunk, const float2
                        size_t stride)
 {
     nbody32x2_kernel<RC, TPT><<<g, TBLOCK / TPT, 0, c->stream>>>(
-        c->tblocks.ptr, N, R, chunk, c->pos32.ptr, c->nrm32.ptr, sigma, (float)c->k, (float)c->eta,
+        c->tblocks.ptr + c->tblock_off, N, R, chunk, c->pos32.ptr, c->nrm32.ptr, sigma, (float)c->k, (float)c->eta,
         (float)(c->k / (2.0 * M_PI)), part, y, stride);
 }
 
@@ -452,7 +452,8 @@ hzb_status interbody64_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, 
     c->interbody_calls++;
     c->launches += (nsplit > 1) ? 2 : 1;
     const int slot = prof_begin(c, 0);
-    const int nb = (c->tune_limit_blocks > 0) ? std::min(c->tune_limit_blocks, c->n_tblocks) : c->n_tblocks;
+    const int nb = (c->tune_limit_blocks > 0) ? std::min(c->tune_limit_blocks, c->n_tblocks - c->tblock_off)
+                                              : c->n_tblocks - c->tblock_off;
     dim3 g(nb, (R + rc - 1) / rc, nsplit);
     if (rc == 1) dispatch64<1>(c, tpt, g, N, R, chunk, sigma, out, n);
     else if (rc == 4) dispatch64<4>(c, tpt, g, N, R, chunk, sigma, out, n);
@@ -482,7 +483,8 @@ hzb_status interbody32_cfg(hzb_ctx *c, int R, const double2 *sigma, double2 *y, 
     const int slot = prof_begin(c, 1);
     const float2 *sw = weighted_sigma32(c, R, sigma);
     if (!sw) return HZB_ENOMEM;
-    const int nb = (c->tune_limit_blocks > 0) ? std::min(c->tune_limit_blocks, c->n_tblocks) : c->n_tblocks;
+    const int nb = (c->tune_limit_blocks > 0) ? std::min(c->tune_limit_blocks, c->n_tblocks - c->tblock_off)
+                                              : c->n_tblocks - c->tblock_off;
     dim3 g(nb, (R + rc - 1) / rc, nsplit);
     if (rc == 1) dispatch32<1>(c, tpt, x2, g, N, R, chunk, sw, part, y, n);
     else if (rc == 4) dispatch32<4>(c, tpt, x2, g, N, R, chunk, sw, part, y, n);

@@ -230,7 +230,9 @@ hzb_status make_nodes(hzb_ctx *c)
     // target blocks of the inter-body sum: contiguous ranges inside one body
     const int TB = 512;
     std::vector<TargetBlock> blocks;
+    c->body_block0.clear();
     for (const BodyRec &b : c->bodies) {
+        c->body_block0.push_back((int)blocks.size());
         for (int s = 0; s < b.n_nodes; s += TB) {
             TargetBlock t;
             t.start = (int)(b.offset + s);
@@ -241,6 +243,7 @@ hzb_status make_nodes(hzb_ctx *c)
         }
     }
     c->n_tblocks = (int)blocks.size();
+    c->body_block0.push_back(c->n_tblocks);
     if (check_cuda(c, c->tblocks.ensure(blocks.size()), "alloc blocks")) return HZB_ENOMEM;
     if (check_cuda(c, cudaMemcpyAsync(c->tblocks.ptr, blocks.data(), blocks.size() * sizeof(TargetBlock),
                                       cudaMemcpyHostToDevice, c->stream), "copy blocks"))

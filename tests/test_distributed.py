@@ -1,0 +1,129 @@
+"""The body-partitioned solve (paper_1406_0236_gb300.distributed) on two CPU ranks
+with the gloo backend: the bodies are split in contiguous, work-balanced ranges, sigma
+is all-gathered before each inter-body sum and the Gram-Schmidt dot products and norms
+are all-reduced; with oracle-backed rank-local operators, the two-rank GMRES equals
+the one-rank oracle solve."""
+import os
+import socket
+
+import numpy as np
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import workloads as W
+from paper_1406_0236_gb300.distributed import (Exchange, LocalOperator, gmres_distributed, partition_bodies,
+                                               row_ranges, solve_partitioned)
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _workload():
+    """Three bodies of different sizes (two shapes), two plane waves."""
+    wl = W.uneven3(n_rhs=2)
+    return wl
+
+
+class OracleOperator(LocalOperator):
+    """Rank-local pieces from the oracle: the inter-body sum of the owned targets against
+    all sources, and the block-diagonal inverse applied to the owned rows."""
+
+    def __init__(self, P, rows):
+        self.P = P
+        self.rows = rows
+
+    def _full(self, local):
+        f = np.zeros((self.P.N, local.shape[1]), dtype=np.complex128)
+        f[self.rows[0]:self.rows[1]] = local
+        return f
+
+    def apply_local(self, sigma_full):
+        r0, r1 = self.rows
+        y = self.P.interbody(sigma_full, targets=np.arange(r0, r1, dtype=np.int32))
+        return sigma_full[r0:r1] + self.P.local_inverse(self._full(y))[r0:r1]
+
+    def rhs_local(self, v_local):
+        r0, r1 = self.rows
+        return -self.P.local_inverse(self._full(v_local))[r0:r1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import Problem, fields
+    wl = _workload()
+    P = Problem(wl)
+    sizes = [b.shape.n_nodes for b in wl.bodies]
+    parts = partition_bodies(sizes, world)
+    rows = row_ranges(sizes, parts)
+    ex = Exchange(dist, rows)
+    op = OracleOperator(P, rows[rank])
+    v = fields.plane_wave(P.nodes.x, wl.directions, wl.k)
+    x_loc, it, conv, rel = solve_partitioned(op, ex, v[rows[rank][0]:rows[rank][1]], 1e-12, maxit=200)
+    full = ex.allgather_rows(x_loc)
+    out[rank] = (full, it, conv, parts)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_partitioned_solve_equals_one_rank_oracle_solve():
+    from oracle import Problem, fields, gmres
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    x0, it0, c0, parts = out[0]
+    x1, it1, c1, _ = out[1]
+    assert c0 and c1 and it0 == it1
+    assert np.array_equal(x0, x1)                     # every rank holds the same gathered solution
+    assert len(parts) == 2 and parts[0][0] == 0 and parts[0][1] == parts[1][0] and parts[1][1] == 3
+    wl = _workload()
+    P = Problem(wl)
+    v = fields.plane_wave(P.nodes.x, wl.directions, wl.k)
+    for r in range(v.shape[1]):
+        ref = gmres(P.apply, P.rhs(v[:, r]), 1e-13).x
+        assert np.linalg.norm(x0[:, r] - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_one_rank_partitioned_gmres_equals_oracle_gmres():
+    """World size 1 through the same driver (a stand-in exchange that returns its input)."""
+    from oracle import Problem, fields, gmres
+    wl = _workload()
+    P = Problem(wl)
+
+    class Single(Exchange):
+        def __init__(self):
+            self.rows = [(0, P.N)]
+
+        def allgather_rows(self, local):
+            return local
+
+        def allreduce_sum(self, a):
+            return a
+
+    v = fields.plane_wave(P.nodes.x, wl.directions, wl.k)
+    x, it, conv, rel = gmres_distributed(OracleOperator(P, (0, P.N)), Single(), P.rhs(v), 1e-12, maxit=200)
+    assert conv and np.all(rel <= 1e-12)
+    for r in range(v.shape[1]):
+        ref = gmres(P.apply, P.rhs(v[:, r]), 1e-13).x
+        assert np.linalg.norm(x[:, r] - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_partition_balances_pair_work():
+    sizes = [4100, 9000, 1200, 7000, 7000, 300, 12000]
+    N = sum(sizes)
+    w = [n * (N - n) for n in sizes]
+    for world in (1, 2, 3, 4, 7, 9):
+        parts = partition_bodies(sizes, world)
+        assert len(parts) == world
+        assert parts[0][0] == 0 and max(e for _, e in parts) == len(sizes)
+        assert all(parts[i][1] == parts[i + 1][0] for i in range(world - 1))
+        loads = [sum(w[b:e]) for b, e in parts]
+        # no contiguous split does better than the largest share, which is at least the mean
+        assert max(loads) >= sum(w) / world - 1e-9
+        assert max(loads) <= sum(w) / world + max(w)
+    rr = row_ranges(sizes, partition_bodies(sizes, 3))
+    assert rr[0][0] == 0 and rr[-1][1] == N
