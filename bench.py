@@ -223,6 +223,68 @@ def timed_solves(torch, s, d, n, flush, barrier, ev0, ev1):
     return times, stats
 
 
+def mlp_leg(torch, local, n_train=4096, n_held=512, batch=64, epochs=400):
+    """The metric's "+MLP" half on its own workload (two unit spheres, 8,200 unknowns,
+    k = 2): 4,096 training solves (untimed), POD basis and network training on the
+    library's kernels (timed, reported), then the 512 held-out directions in batches of
+    64 right-hand sides, each solved to a density error <= 1e-7: FP64 GPU path (zero
+    guess), mixed precision with the double-float residual from zero and from the
+    network's guess.  Density errors against mixed refinement to 1e-11."""
+    import numpy as np
+
+    import workloads as W
+    from paper_1406_0236_gb300 import Options, Solver
+    from paper_1406_0236_gb300.warm_start import WarmStart
+
+    wl = W.two_spheres()
+    s = Solver.from_workload(wl, Options(device=local, precision=1, gmres_tol=1e-11, verify_final=1),
+                             stream=torch.cuda.current_stream().cuda_stream)
+    s.build_scattering_matrices()
+    train = W.uniform_directions(n_train, 20140602)
+    held = W.uniform_directions(n_held, 20140603)
+    t0 = time.perf_counter()
+    ws = WarmStart(s)
+    X = ws.training_densities(train)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    ws.fit(train, X, epochs=epochs)
+    Xh = ws.training_densities(held)                     # references (mixed refinement to 1e-11)
+    G = ws.guess(held)
+    gerr = (torch.linalg.vector_norm(G - Xh, dim=0) / torch.linalg.vector_norm(Xh, dim=0)).cpu().numpy()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(prec, tol, warm, residual):
+        s.set_options(precision=prec, gmres_tol=tol, verify_final=1 if prec == 0 else 0, residual=residual)
+        vs = [s.plane_waves(held[a:a + batch]) for a in range(0, n_held, batch)]
+        out = torch.empty_like(Xh)
+        its = []
+        torch.cuda.synchronize()
+        ev0.record()
+        for q, a in enumerate(range(0, n_held, batch)):
+            d = held[a:a + batch]
+            st = s.solve_data(vs[q], x0=ws.guess(d) if warm else None)
+            its.append(st.iterations)
+            part = torch.empty((out.shape[0], d.shape[0]), dtype=out.dtype, device=out.device)
+            s.get_density(part)
+            out[:, a:a + d.shape[0]] = part
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        err = float((torch.linalg.vector_norm(out - Xh, dim=0) / torch.linalg.vector_norm(Xh, dim=0)).max())
+        return {"value": 1e3 * n_held / ms, "unit": "RHS solves/s", "ms": ms, "iterations_per_batch": its,
+                "density_err_max": err}
+
+    res = {"workload": "two_spheres_8200 (k = 2)", "train": n_train, "held_out": n_held, "batch_rhs": batch,
+           "pod_modes": ws.n_pod, "mlp": "3 -> 4 x 512 GELU -> 512, BF16 tensor-core products", "epochs": epochs,
+           "t_training_solves_s": t_data, "t_pod_s": ws.t_pod, "t_train_s": ws.t_train,
+           "guess_rel_err_median": float(np.median(gerr)), "guess_rel_err_max": float(gerr.max()),
+           "fp64_gpu_zero_guess": run(0, 3e-8, False, 0),
+           "mixed_zero_guess": run(1, 1e-7, False, 2),
+           "mixed_plus_mlp": run(1, 1e-7, True, 2)}
+    s.close()
+    return res
+
+
 def measured_peaks(s):
     """Pipe throughputs measured on this GPU by the library's microbenchmarks
     (hzb_measure_peak): FP32 FMA scalar and packed (TFLOP/s), FP64 FMA (TFLOP/s), the
@@ -247,6 +309,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--accel-eps", type=float, default=1e-8,
                     help="ID tolerance of the accelerated-scheme solves (0 = skip them)")
+    ap.add_argument("--no-mlp", action="store_true", help="skip the learned warm-start (+MLP) leg")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -425,6 +488,10 @@ def main():
     gint32 = pairs / (per32 * 1e-3) / 1e9 if n32 else None
     gintdf = pairs / (perdf * 1e-3) / 1e9 if ndf else None
 
+    mlp = None
+    if not args.no_mlp:
+        mlp = mlp_leg(torch, local)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_oracle_baseline(wl, ORACLE_ITERS)
@@ -455,6 +522,7 @@ def main():
             "mixed_fp64_residual": mixed_fp64,
             "fp64_gpu": fp64,
             "accelerated": accel,
+            "mlp_warm_start": mlp,
             "roofline": roof,
             "roofline_residual_kernel": roofdf,
             "measured_peaks": peaks,

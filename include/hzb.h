@@ -338,6 +338,12 @@ hzb_status hzb_apply(hzb_ctx *ctx, int R, const double *sigma, double *z, int on
  * some right-hand side missed the tolerance (best iterate kept). */
 hzb_status hzb_solve_plane_waves(hzb_ctx *ctx, int R, const double *dirs, hzb_stats *stats);
 
+/* The incident plane waves v = exp(i k d.x) at the nodes (Eq. (basic)) for R unit
+ * directions dirs (host, R x 3), written to v (N x R complex, host or device per the
+ * flag): the data hzb_solve_plane_waves solves for, for callers that pass it to
+ * hzb_solve_data with a guess.  Errors: HZB_EINVAL (non-unit direction), HZB_ESTATE. */
+hzb_status hzb_incident_plane_waves(hzb_ctx *ctx, int R, const double *dirs, double *v, int on_device);
+
 /* Solve for R general Dirichlet data sets: v is N x R complex (u = -v on Gamma).
  * x0 (N x R complex, may be NULL) is an initial guess in the same memory space. */
 hzb_status hzb_solve_data(hzb_ctx *ctx, int R, const double *v, const double *x0,
@@ -427,6 +433,15 @@ hzb_status hzb_interp_decomp(hzb_ctx *ctx, int rows, int cols, const double *Z, 
  * ------------------------------------------------------------------------------ */
 typedef struct hzb_mlp hzb_mlp;
 
+/* Products of the layers whose batch, inputs and outputs are multiples of 128 (the
+ * 512-wide hidden and output layers at batch sizes 128, 256, ...) run on the tensor
+ * cores (tcgen05.mma kind::f16: BF16 operands, FP32 accumulation in tensor memory): the
+ * layer input and the back-propagated gradient are rounded to BF16 for the product; the
+ * other layers (e.g. the first, 3 inputs) on the CUDA cores with FP32 activations.
+ * on = 0 forces the CUDA cores everywhere (default 1).  A bounded tensor-core wait that
+ * runs out makes the call return HZB_ETIMEOUT. */
+hzb_status hzb_mlp_set_tensor_cores(hzb_mlp *m, int on);
+
 /* Create on `device` launching on `stream` (NULL = default stream); weights drawn
  * uniformly in +-1/sqrt(fan_in) from a splitmix64 stream seeded by `seed`, biases 0. */
 hzb_status hzb_mlp_create(int device, void *stream, int n_in, int width, int depth, int n_out,
@@ -446,6 +461,27 @@ hzb_status hzb_mlp_gradients(hzb_mlp *m, int B, const float *x, const float *t, 
 /* One Adam step on the batch; *loss (may be NULL) receives the loss before the step. */
 hzb_status hzb_mlp_train_step(hzb_mlp *m, int B, const float *x, const float *t, float lr,
                               float *loss, int on_device);
+
+/* POD basis and guess of the warm start (no counterpart in the paper).  All arrays are
+ * device memory of the context's GPU, complex interleaved, row-major.
+ *   hzb_pod_basis:   U (N x k) with orthonormal columns spanning the dominant left
+ *                    singular subspace of the snapshot matrix X (N x T): a complex
+ *                    Gaussian sketch Z = X Omega (counter-based generator seeded by
+ *                    `seed`), power_steps rounds of Z = X (X^H Z) (0..8), then classical
+ *                    Gram-Schmidt applied twice in FP64 (the randomized range finder of
+ *                    Halko, Martinsson and Tropp).  1 <= k <= min(N, T).
+ *   hzb_pod_project: C (k x T) = U^H X.
+ *   hzb_pod_expand:  x0 (N x R) = U coef (coef k x R).
+ *   hzb_pod_guess:   x0 (N x R) = U coef with coef[j][r] = scale (y[r][2j] + i y[r][2j+1]),
+ *                    y (R x 2k, FP32) the network's outputs (hzb_mlp_forward).
+ * The products run in FP32 on complex operands (FP64 in and out).  Errors: HZB_EINVAL
+ * (sizes, null pointers), HZB_ENOMEM, HZB_ECUDA. */
+hzb_status hzb_pod_basis(hzb_ctx *ctx, int N, int T, const double *X, int k, int power_steps,
+                         unsigned long long seed, double *U);
+hzb_status hzb_pod_project(hzb_ctx *ctx, int N, int k, int T, const double *U, const double *X, double *C);
+hzb_status hzb_pod_expand(hzb_ctx *ctx, int N, int k, int R, const double *U, const double *coef, double *x0);
+hzb_status hzb_pod_guess(hzb_ctx *ctx, int N, int k, int R, const double *U, const float *y, double scale,
+                         double *x0);
 
 #ifdef __cplusplus
 }

@@ -29,12 +29,18 @@ def gelu_grad(a):
     return 0.5 * (1.0 + special.erf(a / np.sqrt(2.0))) + a * phi
 
 
-def forward(params: List[Tuple[np.ndarray, np.ndarray]], x: np.ndarray):
-    """params: [(W_l (out_l x in_l), b_l (out_l))]; returns (y, cache)."""
+def _keep(l, kind, a):
+    return a
+
+
+def forward(params: List[Tuple[np.ndarray, np.ndarray]], x: np.ndarray, operand=_keep):
+    """params: [(W_l (out_l x in_l), b_l (out_l))]; returns (y, cache).  `operand(l,
+    "h", h)` gives the layer input as it enters the product (identity by default; a
+    caller emulating reduced-precision operands passes a rounding)."""
     h = np.asarray(x, dtype=np.float64)
     cache = []
     for l, (W, b) in enumerate(params):
-        a = h @ W.T + b
+        a = operand(l, "h", h) @ W.T + b
         cache.append((h, a))
         h = gelu(a) if l < len(params) - 1 else a
     return h, cache
@@ -45,9 +51,10 @@ def loss(params, x, t) -> float:
     return float(((y - t) ** 2).sum() / x.shape[0])
 
 
-def gradients(params, x, t):
-    """(loss, [(dW_l, db_l)])."""
-    y, cache = forward(params, x)
+def gradients(params, x, t, operand=_keep):
+    """(loss, [(dW_l, db_l)]); `operand` as in forward, also applied (kind "g") to the
+    back-propagated gradient where it enters the two products of a layer."""
+    y, cache = forward(params, x, operand)
     B = x.shape[0]
     g = 2.0 * (y - t) / B                                   # dL/dy
     grads = [None] * len(params)
@@ -56,6 +63,7 @@ def gradients(params, x, t):
         if l < len(params) - 1:
             g = g * gelu_grad(a)                            # through the activation
         W, _ = params[l]
-        grads[l] = (g.T @ h_in, g.sum(axis=0))
-        g = g @ W                                           # to the layer input
+        gp = operand(l, "g", g)
+        grads[l] = (gp.T @ operand(l, "h", h_in), g.sum(axis=0))
+        g = gp @ W                                          # to the layer input
     return float(((y - t) ** 2).sum() / B), grads

@@ -144,6 +144,11 @@ def lib():
         "hzb_interp_decomp": (i, [p, i, i, p, d, ctypes.POINTER(i), p, p]),
         "hzb_measure_peak": (i, [p, i, ctypes.POINTER(d)]),
         "hzb_interbody_bodies": (i, [p, i, p, i, i, p, i, i]),
+        "hzb_pod_basis": (i, [p, i, i, p, i, i, ctypes.c_ulonglong, p]),
+        "hzb_incident_plane_waves": (i, [p, i, p, p, i]),
+        "hzb_pod_project": (i, [p, i, i, i, p, p, p]),
+        "hzb_pod_expand": (i, [p, i, i, i, p, p, p]),
+        "hzb_pod_guess": (i, [p, i, i, i, p, p, d, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -321,6 +326,45 @@ class Solver:
         self._check(lib().hzb_autotune(self._h, int(R), int(which), _ptr(best)))
         return best
 
+    # ------------------------------------------------------------ warm-start linear algebra
+    def pod_basis(self, X, k: int, power_steps: int = 2, seed: int = 7):
+        """U (N x k, orthonormal columns) of the dominant subspace of X (N x T CUDA complex128)."""
+        import torch
+        if not (_is_dev(X) and X.dtype == torch.complex128 and X.is_contiguous() and X.dim() == 2):
+            raise ValueError("X must be a contiguous N x T complex128 CUDA tensor")
+        U = X.new_empty((X.shape[0], int(k)))
+        self._check(lib().hzb_pod_basis(self._h, int(X.shape[0]), int(X.shape[1]), _ptr(X), int(k),
+                                        int(power_steps), int(seed), _ptr(U)))
+        return U
+
+    def pod_project(self, U, X):
+        """C = U^H X (k x T) for CUDA complex128 U (N x k) and X (N x T)."""
+        if U.shape[0] != X.shape[0] or not (U.is_contiguous() and X.is_contiguous()):
+            raise ValueError("U (N x k) and X (N x T) must be contiguous with the same N")
+        C = X.new_empty((U.shape[1], X.shape[1]))
+        self._check(lib().hzb_pod_project(self._h, int(U.shape[0]), int(U.shape[1]), int(X.shape[1]), _ptr(U),
+                                          _ptr(X), _ptr(C)))
+        return C
+
+    def pod_expand(self, U, coef):
+        """x0 = U coef (N x R) for CUDA complex128 U (N x k) and coef (k x R)."""
+        if U.shape[1] != coef.shape[0] or not (U.is_contiguous() and coef.is_contiguous()):
+            raise ValueError("U (N x k) and coef (k x R) must be contiguous with the same k")
+        x0 = U.new_empty((U.shape[0], coef.shape[1]))
+        self._check(lib().hzb_pod_expand(self._h, int(U.shape[0]), int(U.shape[1]), int(coef.shape[1]), _ptr(U),
+                                         _ptr(coef), _ptr(x0)))
+        return x0
+
+    def pod_guess(self, U, y, scale: float):
+        """x0 = U coef from the network's FP32 outputs y (R x 2k CUDA tensor), coef_j = scale (y_2j + i y_2j+1)."""
+        import torch
+        if not (y.dtype == torch.float32 and y.is_contiguous() and y.shape[1] == 2 * U.shape[1]):
+            raise ValueError("y must be a contiguous R x 2k float32 CUDA tensor")
+        x0 = U.new_empty((U.shape[0], y.shape[0]))
+        self._check(lib().hzb_pod_guess(self._h, int(U.shape[0]), int(U.shape[1]), int(y.shape[0]), _ptr(U),
+                                        _ptr(y), float(scale), _ptr(x0)))
+        return x0
+
     PEAK_KINDS = ("ffma", "ffma2", "dfma", "mufu", "tf32_tcgen05")
 
     def measure_peak(self, kind: str) -> float:
@@ -442,6 +486,19 @@ class Solver:
             self._check(rc)
         self._R = int(d.shape[0])
         return self._stats(st, rc)
+
+    def plane_waves(self, dirs, device: bool = True):
+        """v = exp(i k d.x) at the nodes (N x R) for unit directions dirs (R x 3), on the
+        library's kernel: a CUDA tensor (device=True) or a numpy array."""
+        d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+        R = d.shape[0]
+        if device:
+            import torch
+            v = torch.empty((self.N, R), dtype=torch.complex128, device="cuda:%d" % self._opt.device)
+        else:
+            v = np.empty((self.N, R), dtype=np.complex128)
+        self._check(lib().hzb_incident_plane_waves(self._h, R, _ptr(d), _ptr(v), int(device)))
+        return v
 
     def solve_data(self, v, x0=None, allow_noconv: bool = False) -> Stats:
         N = self.N
@@ -578,6 +635,7 @@ class Mlp:
                 ("hzb_mlp_last_error", ctypes.c_char_p, [p]),
                 ("hzb_mlp_num_params", i, [p, ctypes.POINTER(ctypes.c_longlong)]),
                 ("hzb_mlp_get_params", i, [p, p]),
+                ("hzb_mlp_set_tensor_cores", i, [p, i]),
                 ("hzb_mlp_set_params", i, [p, p]),
                 ("hzb_mlp_forward", i, [p, i, p, p, i]),
                 ("hzb_mlp_gradients", i, [p, i, p, p, ctypes.POINTER(f), p, i]),
@@ -605,6 +663,10 @@ class Mlp:
         n = ctypes.c_longlong()
         self._check(lib().hzb_mlp_num_params(self._h, ctypes.byref(n)))
         return n.value
+
+    def set_tensor_cores(self, on: bool):
+        """Tensor-core (tcgen05 BF16) products for whole-tile layers (default on)."""
+        self._check(lib().hzb_mlp_set_tensor_cores(self._h, int(bool(on))))
 
     def get_params(self) -> np.ndarray:
         out = np.zeros(self.num_params, dtype=np.float32)

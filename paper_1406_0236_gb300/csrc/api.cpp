@@ -479,6 +479,32 @@ hzb_status hzb_solve_plane_waves(hzb_ctx *c, int R, const double *dirs, hzb_stat
     return solve_driver(c, R, c->io_in.ptr, nullptr, stats);
 }
 
+hzb_status hzb_incident_plane_waves(hzb_ctx *c, int R, const double *dirs, double *v, int on_device)
+{
+    HZB_GUARD(c);
+    if (c->state < 2) return fail(c, HZB_ESTATE, "no bodies");
+    if (R < 1 || R > 4096 || !dirs || !v) return fail(c, HZB_EINVAL, "bad R or null pointer");
+    for (int r = 0; r < R; ++r) {
+        double nn = dirs[3 * r] * dirs[3 * r] + dirs[3 * r + 1] * dirs[3 * r + 1] + dirs[3 * r + 2] * dirs[3 * r + 2];
+        if (!(std::fabs(nn - 1.0) < 1e-8)) return fail(c, HZB_EINVAL, "directions must be unit vectors");
+    }
+    hzb_status st = make_nodes(c);
+    if (st) return st;
+    const size_t n = (size_t)c->N * R;
+    if (check_cuda(c, c->io_small.ensure(3 * (size_t)R), "alloc")) return HZB_ENOMEM;
+    double2 *out = (double2 *)v;
+    if (!on_device) {
+        if (check_cuda(c, c->io_out.ensure(n), "alloc")) return HZB_ENOMEM;
+        out = c->io_out.ptr;
+    }
+    if (check_cuda(c, cudaMemcpyAsync(c->io_small.ptr, dirs, 3 * R * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                   "copy dirs"))
+        return HZB_ECUDA;
+    if ((st = plane_waves(c, R, c->io_small.ptr, out))) return st;
+    if (!on_device) return finish_out(c, out, v, n, 0);
+    return check_cuda(c, cudaStreamSynchronize(c->stream), "plane waves");
+}
+
 hzb_status hzb_solve_data(hzb_ctx *c, int R, const double *v, const double *x0, int on_device, hzb_stats *stats)
 {
     HZB_GUARD(c);

@@ -8,6 +8,7 @@
 // output y = a_last.  Loss (1/B) sum (y - t)^2.  Adam with bias correction.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -15,6 +16,7 @@
 #include <vector>
 
 #include "hzb_internal.h"
+#include "tcgen05.cuh"
 
 struct hzb_mlp {
     int device = 0;
@@ -33,6 +35,12 @@ struct hzb_mlp {
     std::vector<float *> act_a, act_h;     // pre- and post-activation per layer
     float *gbuf0 = nullptr, *gbuf1 = nullptr;
     float *xbuf = nullptr, *tbuf = nullptr, *loss = nullptr;
+    // tensor-core products (layers whose sizes are multiples of the tile): BF16 operands
+    __nv_bfloat16 *hbf = nullptr;          // a layer input (B x I) or gradient (B x O) in BF16
+    __nv_bfloat16 *tA = nullptr, *tB = nullptr;   // transposed BF16 operands of the weight gradient
+    __nv_bfloat16 *wtbf = nullptr;         // transposed BF16 weights W^T (I x O) of the layer being back-propagated
+    int *kerr = nullptr;                   // bounded-wait flag of the tensor-core kernel
+    int use_tc = 1;                        // 0: CUDA-core products only
     std::string err;
 };
 
@@ -145,6 +153,128 @@ __global__ void to_bf16_kernel(size_t n, const float *p, __nv_bfloat16 *pb)
     if (e < n) pb[e] = __float2bfloat16_rn(p[e]);
 }
 
+// ------------------------------------------------------------------ tensor-core products
+//
+// C (M x N, FP32, row-major, ldc) = A (M x K) B (N x K)^T (+ bias[n]) with A and B BF16,
+// row-major (K contiguous), on tcgen05.mma.kind::f16 (BF16 operands, FP32 accumulation
+// in tensor memory).  M % 128 == 0, N % 128 == 0, K % 64 == 0.  A CTA of 128 threads owns
+// a 128 x 128 tile of C: per 64-wide K chunk its threads copy the two 128 x 64 operand
+// tiles into shared memory in the 128-byte-swizzled K-major layout, thread 0 issues four
+// MMAs (K = 16 each) and commits them to an mbarrier; after the last chunk the four warps
+// read their 32 rows x 128 columns of the accumulator (tcgen05.ld).  Every wait is bounded;
+// one that runs out sets *err, writes NaN and frees the tensor memory.
+static const int MM_M = 128, MM_N = 128, MM_KC = 64;
+static const int MM_TILE = MM_M * MM_KC * 2;           // 16 KB per operand tile
+static const int MM_SMEM = 2 * MM_TILE + 1024;
+
+__host__ __device__ constexpr uint32_t bf16_idesc(int n, int m)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+mlp_tc_gemm_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
+                   const float *__restrict__ bias, float *__restrict__ C, int ldc, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char mm_raw[];
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) unsigned long long s_mbar;
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(mm_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t sA = base, sB = base + MM_TILE;
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * MM_M, n0 = blockIdx.x * MM_N;
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(MM_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_taddr;
+    uint32_t phase = 0;
+    bool failed = false;
+    for (int k0 = 0; k0 < K; k0 += MM_KC) {
+        // operand tiles: row r, 16-byte chunk c (8 BF16) of the 64-wide K chunk
+        for (int e = tid; e < MM_M * 8; e += 128) {
+            const int r = e >> 3, c = e & 7;
+            const uint4 va = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * K + k0 + 8 * c);
+            const uint4 vb = *reinterpret_cast<const uint4 *>(B + (size_t)(n0 + r) * K + k0 + 8 * c);
+            t5_st4(sA + t5_chunk_off(r, c), va.x, va.y, va.z, va.w);
+            t5_st4(sB + t5_chunk_off(r, c), vb.x, vb.y, vb.z, vb.w);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int ks = 0; ks < MM_KC / 16; ++ks)
+                mma_bf16(tmem, t5_desc(sA + 32 * ks), t5_desc(sB + 32 * ks), bf16_idesc(MM_N, MM_M),
+                         (k0 | ks) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                         : "memory");
+        }
+        const bool ok = t5_wait(mbar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    // epilogue: warp w holds rows 32 w .. 32 w + 31 of the tile, 128 columns
+    const int row = m0 + 32 * warp + lane;
+#pragma unroll 1
+    for (int cb = 0; cb < MM_N; cb += 32) {
+        float v[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = 0.f;
+        if (!failed) t5_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, v);
+        float *out = C + (size_t)row * ldc + n0 + cb;
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            out[q] = failed ? __int_as_float(0x7fc00000) : v[q] + (bias ? bias[n0 + cb + q] : 0.f);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MM_N) : "memory");
+    if (failed && tid == 0) atomicExch(err, 1);
+}
+
+// out (C x R, BF16) = in^T for in (R x C, FP32 or BF16), 32 x 32 tiles through shared memory
+template <typename T>
+__global__ void transpose_bf16_kernel(int R, int Cn, const T *__restrict__ in, __nv_bfloat16 *__restrict__ out)
+{
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        const int r = r0 + q, c = c0 + threadIdx.x;
+        tile[q][threadIdx.x] = (r < R && c < Cn) ? (float)in[(size_t)r * Cn + c] : 0.f;
+    }
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        const int c = c0 + q, r = r0 + threadIdx.x;
+        if (c < Cn && r < R) out[(size_t)c * R + r] = __float2bfloat16_rn(tile[threadIdx.x][q]);
+    }
+}
+
 static unsigned nb(size_t n) { return (unsigned)((n + 255) / 256); }
 
 template <typename TA, typename TB>
@@ -153,6 +283,29 @@ static void gemm(cudaStream_t s, int M, int Nn, int K, const TA *A, long sam, lo
 {
     dim3 g((Nn + 31) / 32, (M + 31) / 32);
     gemm_kernel<TA, TB><<<g, 256, 0, s>>>(M, Nn, K, A, sam, sak, B, sbk, sbn, bias, C, scm, scn);
+}
+
+static void tc_gemm(hzb_mlp *m, int M, int Nn, int K, const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias,
+                    float *C, int ldc)
+{
+    mlp_tc_gemm_kernel<<<dim3(Nn / MM_N, M / MM_M), 128, MM_SMEM, m->stream>>>(M, Nn, K, A, B, bias, C, ldc, m->kerr);
+}
+
+// a layer's products go to the tensor cores when the batch, its inputs and its outputs
+// are whole tiles
+static bool layer_tc(const hzb_mlp *m, int B, int l)
+{
+    return m->use_tc && B % 128 == 0 && m->din[l] % 128 == 0 && m->dout[l] % 128 == 0;
+}
+
+static void transpose_bf16(cudaStream_t st, int R, int Cn, const float *in, __nv_bfloat16 *out)
+{
+    transpose_bf16_kernel<float><<<dim3((Cn + 31) / 32, (R + 31) / 32), dim3(32, 8), 0, st>>>(R, Cn, in, out);
+}
+
+static void transpose_bf16(cudaStream_t st, int R, int Cn, const __nv_bfloat16 *in, __nv_bfloat16 *out)
+{
+    transpose_bf16_kernel<__nv_bfloat16><<<dim3((Cn + 31) / 32, (R + 31) / 32), dim3(32, 8), 0, st>>>(R, Cn, in, out);
 }
 
 static hzb_status mfail(hzb_mlp *m, hzb_status s, const std::string &msg)
@@ -167,6 +320,7 @@ static hzb_status ensure_batch(hzb_mlp *m, int B)
     for (float *p : m->act_a) cudaFree(p);
     for (float *p : m->act_h) cudaFree(p);
     cudaFree(m->gbuf0); cudaFree(m->gbuf1); cudaFree(m->xbuf); cudaFree(m->tbuf);
+    cudaFree(m->hbf); cudaFree(m->tA); cudaFree(m->tB);
     m->act_a.assign(m->din.size(), nullptr);
     m->act_h.assign(m->din.size(), nullptr);
     int wmax = std::max(std::max(m->width, m->n_out), m->n_in);
@@ -179,6 +333,9 @@ static hzb_status ensure_batch(hzb_mlp *m, int B)
     ok &= cudaMalloc(&m->gbuf1, (size_t)B * wmax * sizeof(float)) == cudaSuccess;
     ok &= cudaMalloc(&m->xbuf, (size_t)B * m->n_in * sizeof(float)) == cudaSuccess;
     ok &= cudaMalloc(&m->tbuf, (size_t)B * m->n_out * sizeof(float)) == cudaSuccess;
+    ok &= cudaMalloc(&m->hbf, (size_t)B * wmax * sizeof(__nv_bfloat16)) == cudaSuccess;
+    ok &= cudaMalloc(&m->tA, (size_t)B * wmax * sizeof(__nv_bfloat16)) == cudaSuccess;
+    ok &= cudaMalloc(&m->tB, (size_t)B * wmax * sizeof(__nv_bfloat16)) == cudaSuccess;
     if (!ok) return mfail(m, HZB_ENOMEM, "MLP activation buffers");
     m->cap_batch = B;
     return HZB_OK;
@@ -192,8 +349,14 @@ static const float *forward(hzb_mlp *m, int B, const float *x)
     for (int l = 0; l < L; ++l) {
         const __nv_bfloat16 *W = m->wbf + m->woff[l];
         const float *b = m->master + m->boff[l];
-        gemm<float, __nv_bfloat16>(m->stream, B, m->dout[l], m->din[l], h, m->din[l], 1, W, 1, m->din[l], b,
-                                   m->act_a[l], m->dout[l], 1);
+        if (layer_tc(m, B, l)) {                      // a = bf16(h) W^T + b on the tensor cores
+            const size_t n = (size_t)B * m->din[l];
+            to_bf16_kernel<<<nb(n), 256, 0, m->stream>>>(n, h, m->hbf);
+            tc_gemm(m, B, m->dout[l], m->din[l], m->hbf, W, b, m->act_a[l], m->dout[l]);
+        } else {
+            gemm<float, __nv_bfloat16>(m->stream, B, m->dout[l], m->din[l], h, m->din[l], 1, W, 1, m->din[l], b,
+                                       m->act_a[l], m->dout[l], 1);
+        }
         if (l < L - 1) {
             size_t n = (size_t)B * m->dout[l];
             gelu_kernel<<<nb(n), 256, 0, m->stream>>>(n, m->act_a[l], m->act_h[l]);
@@ -218,12 +381,27 @@ static void backward(hzb_mlp *m, int B, const float *x, const float *t)
         int I = m->din[l], O = m->dout[l];
         if (l < L - 1) gelu_back_kernel<<<nb((size_t)B * O), 256, 0, m->stream>>>((size_t)B * O, m->act_a[l], g);
         const float *hin = (l == 0) ? x : m->act_h[l - 1];
+        const bool tc = layer_tc(m, B, l);
         // dW (O x I) = g^T (O x B) h_in (B x I)
-        gemm<float, float>(m->stream, O, I, B, g, 1, O, hin, I, 1, nullptr, m->grad + m->woff[l], I, 1);
+        if (tc) {                                     // bf16(g)^T bf16(h_in) on the tensor cores
+            transpose_bf16(m->stream, B, O, g, m->tA);
+            transpose_bf16(m->stream, B, I, hin, m->tB);
+            tc_gemm(m, O, I, B, m->tA, m->tB, nullptr, m->grad + m->woff[l], I);
+        } else {
+            gemm<float, float>(m->stream, O, I, B, g, 1, O, hin, I, 1, nullptr, m->grad + m->woff[l], I, 1);
+        }
         bias_grad_kernel<<<(O + 255) / 256, 256, 0, m->stream>>>(B, O, g, m->grad + m->boff[l]);
         if (l > 0) {
             // dh_in (B x I) = g (B x O) W (O x I)
-            gemm<float, __nv_bfloat16>(m->stream, B, I, O, g, O, 1, m->wbf + m->woff[l], I, 1, nullptr, g2, I, 1);
+            if (tc) {                                 // bf16(g) W with W^T (I x O) as the K-major operand
+                const size_t n = (size_t)B * O;
+                to_bf16_kernel<<<nb(n), 256, 0, m->stream>>>(n, g, m->hbf);
+                transpose_bf16(m->stream, O, I, m->wbf + m->woff[l], m->wtbf);
+                tc_gemm(m, B, I, O, m->hbf, m->wtbf, nullptr, g2, I);
+            } else {
+                gemm<float, __nv_bfloat16>(m->stream, B, I, O, g, O, 1, m->wbf + m->woff[l], I, 1, nullptr, g2, I,
+                                           1);
+            }
             std::swap(g, g2);
         }
     }
@@ -271,9 +449,14 @@ hzb_status hzb_mlp_create(int device, void *stream, int n_in, int width, int dep
         double s = 1.0 / std::sqrt((double)m->din[l]);
         for (size_t e = 0; e < (size_t)m->din[l] * m->dout[l]; ++e) p[m->woff[l] + e] = (float)((2.0 * next() - 1.0) * s);
     }
+    size_t wmax = 0;
+    for (size_t l = 0; l < m->din.size(); ++l) wmax = std::max(wmax, (size_t)m->din[l] * m->dout[l]);
     bool ok = cudaMalloc(&m->master, m->nparams * 4) == cudaSuccess && cudaMalloc(&m->grad, m->nparams * 4) == cudaSuccess &&
               cudaMalloc(&m->m, m->nparams * 4) == cudaSuccess && cudaMalloc(&m->v, m->nparams * 4) == cudaSuccess &&
-              cudaMalloc(&m->wbf, m->nparams * 2) == cudaSuccess && cudaMalloc(&m->loss, 4) == cudaSuccess;
+              cudaMalloc(&m->wbf, m->nparams * 2) == cudaSuccess && cudaMalloc(&m->loss, 4) == cudaSuccess &&
+              cudaMalloc(&m->wtbf, wmax * 2) == cudaSuccess && cudaMalloc(&m->kerr, sizeof(int)) == cudaSuccess &&
+              cudaFuncSetAttribute(mlp_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MM_SMEM) ==
+                  cudaSuccess;
     if (!ok) {
         *out = m;
         return HZB_ENOMEM;
@@ -281,6 +464,7 @@ hzb_status hzb_mlp_create(int device, void *stream, int n_in, int width, int dep
     cudaMemcpyAsync(m->master, p.data(), m->nparams * 4, cudaMemcpyHostToDevice, m->stream);
     cudaMemsetAsync(m->m, 0, m->nparams * 4, m->stream);
     cudaMemsetAsync(m->v, 0, m->nparams * 4, m->stream);
+    cudaMemsetAsync(m->kerr, 0, sizeof(int), m->stream);
     to_bf16_kernel<<<nb(m->nparams), 256, 0, m->stream>>>(m->nparams, m->master, m->wbf);
     if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
         *out = m;
@@ -299,12 +483,20 @@ hzb_status hzb_mlp_destroy(hzb_mlp *m)
     for (float *p : m->act_h) cudaFree(p);
     cudaFree(m->gbuf0); cudaFree(m->gbuf1); cudaFree(m->xbuf); cudaFree(m->tbuf);
     cudaFree(m->master); cudaFree(m->grad); cudaFree(m->m); cudaFree(m->v); cudaFree(m->wbf); cudaFree(m->loss);
+    cudaFree(m->hbf); cudaFree(m->tA); cudaFree(m->tB); cudaFree(m->wtbf); cudaFree(m->kerr);
     delete m;
     cudaGetLastError();
     return HZB_OK;
 }
 
 const char *hzb_mlp_last_error(const hzb_mlp *m) { return m ? m->err.c_str() : "null network"; }
+
+hzb_status hzb_mlp_set_tensor_cores(hzb_mlp *m, int on)
+{
+    if (!m || (on != 0 && on != 1)) return HZB_EINVAL;
+    m->use_tc = on;
+    return HZB_OK;
+}
 
 hzb_status hzb_mlp_num_params(const hzb_mlp *m, long long *n)
 {
@@ -333,6 +525,19 @@ hzb_status hzb_mlp_set_params(hzb_mlp *m, const float *in)
     return HZB_OK;
 }
 
+// a bounded tensor-core wait that ran out (outputs NaN): report once and clear
+static hzb_status check_tc_flag(hzb_mlp *m)
+{
+    int flag = 0;
+    if (cudaMemcpy(&flag, m->kerr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return mfail(m, HZB_ECUDA, "read error flag");
+    if (flag) {
+        cudaMemset(m->kerr, 0, sizeof(int));
+        return mfail(m, HZB_ETIMEOUT, "tensor-core wait timed out in mlp_tc_gemm_kernel");
+    }
+    return HZB_OK;
+}
+
 static hzb_status stage(hzb_mlp *m, float *dst, const float *src, size_t n, int on_device, const float **use)
 {
     if (on_device) {
@@ -358,7 +563,7 @@ hzb_status hzb_mlp_forward(hzb_mlp *m, int B, const float *x, float *y, int on_d
     if (cudaMemcpyAsync(y, yd, (size_t)B * m->n_out * 4, kind, m->stream) != cudaSuccess ||
         cudaStreamSynchronize(m->stream) != cudaSuccess)
         return mfail(m, HZB_ECUDA, "forward");
-    return HZB_OK;
+    return check_tc_flag(m);
 }
 
 hzb_status hzb_mlp_gradients(hzb_mlp *m, int B, const float *x, const float *t, float *loss, float *grads,
@@ -381,7 +586,7 @@ hzb_status hzb_mlp_gradients(hzb_mlp *m, int B, const float *x, const float *t, 
     if (loss) cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream);
     if (cudaStreamSynchronize(m->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return mfail(m, HZB_ECUDA, "gradients");
-    return HZB_OK;
+    return check_tc_flag(m);
 }
 
 hzb_status hzb_mlp_train_step(hzb_mlp *m, int B, const float *x, const float *t, float lr, float *loss, int on_device)
@@ -404,7 +609,7 @@ hzb_status hzb_mlp_train_step(hzb_mlp *m, int B, const float *x, const float *t,
     if (loss) cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream);
     if (cudaStreamSynchronize(m->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return mfail(m, HZB_ECUDA, "train step");
-    return HZB_OK;
+    return check_tc_flag(m);
 }
 
 }  // extern "C"

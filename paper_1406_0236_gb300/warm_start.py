@@ -2,14 +2,16 @@
 
 1. Training densities: the library solves the plane-wave problems of the training
    directions (batched right-hand sides, FP64 accuracy via mixed refinement).
-2. POD basis: the leading left singular vectors of the N x T snapshot matrix, by the
-   randomized range finder of Halko, Martinsson and Tropp in complex64 (offline;
-   library GEMM/QR/SVD of torch on a (n_pod + 64)-column sketch).
+2. POD basis: an orthonormal basis of the dominant n_pod-dimensional left singular
+   subspace of the N x T snapshot matrix, by the randomized range finder of Halko,
+   Martinsson and Tropp with two power steps (hzb_pod_basis: complex products in FP32,
+   Gram-Schmidt twice in FP64); the coefficients c = U^H x by hzb_pod_project.
 3. Network: hzb_mlp (BF16 weights, FP32 accumulation, hand-written CUDA kernels)
    maps the direction (3 numbers) to the n_pod complex POD coefficients (2 n_pod
    real outputs, scaled to unit RMS), trained with Adam on the MSE loss.
-4. Guess: x0 = U c(d), passed to hzb_solve_data; the zero-guess solve is the
-   fallback (a guess never changes the converged answer, only the iterations).
+4. Guess: x0 = U c(d) (hzb_pod_guess on the network's outputs), passed to
+   hzb_solve_data; the zero-guess solve is the fallback (a guess never changes the
+   converged answer, only the iterations).
 5. The held-out batches run once more through the accelerated scheme (Sec. 5):
    hzb_compress, then the reduced system, the guess restricted to the skeleton.
 
@@ -59,20 +61,11 @@ class WarmStart:
             X[:, a:a + d.shape[0]] = out
         return X
 
-    def pod_basis(self, X, oversample: int = 64, seed: int = 7):
-        """Leading n_pod left singular vectors of X (randomized range finder, one power step)."""
-        torch = self.torch
-        g = torch.Generator(device="cuda").manual_seed(seed)
-        X32 = X.to(torch.complex64)
-        k = min(self.n_pod + oversample, X.shape[1])
-        Om = torch.complex(torch.randn(X.shape[1], k, device="cuda", generator=g),
-                           torch.randn(X.shape[1], k, device="cuda", generator=g))
-        Q, _ = torch.linalg.qr(X32 @ Om)
-        Q, _ = torch.linalg.qr(X32 @ (X32.conj().T @ Q))                 # one power iteration
-        Ub, _, _ = torch.linalg.svd(Q.conj().T @ X32, full_matrices=False)
-        U = (Q @ Ub[:, :self.n_pod]).to(torch.complex128)
-        U, _ = torch.linalg.qr(U)                                         # re-orthonormalise in FP64
-        return U.contiguous()
+    def pod_basis(self, X, power_steps: int = 2, seed: int = 7):
+        """Orthonormal basis of the dominant n_pod-dimensional subspace of the snapshots X
+        (N x T): randomized range finder with power steps, on the library's kernels
+        (hzb_pod_basis)."""
+        return self.s.pod_basis(X, self.n_pod, power_steps=power_steps, seed=seed)
 
     def fit(self, dirs: np.ndarray, X=None, epochs: int = 400, batch: int = 256, lr: float = 1e-3,
             lr_final: float = 2e-5):
@@ -81,7 +74,7 @@ class WarmStart:
             X = self.training_densities(dirs)
         t0 = time.time()
         self.U = self.pod_basis(X)
-        C = self.U.conj().T @ X                                         # n_pod x T coefficients
+        C = self.s.pod_project(self.U, X)                               # n_pod x T coefficients
         # T x 2 n_pod targets: row t = (Re c_0, Im c_0, Re c_1, Im c_1, ...) of sample t
         T = torch.stack([C.real, C.imag], dim=-1).permute(1, 0, 2).reshape(X.shape[1], 2 * self.n_pod).contiguous()
         torch.cuda.synchronize()
@@ -108,28 +101,24 @@ class WarmStart:
         return self
 
     def guess(self, dirs: np.ndarray):
-        """x0 = U c(d) for directions (R x 3): N x R complex128 device tensor."""
+        """x0 = U c(d) for directions (R x 3): N x R complex128 device tensor (network
+        forward pass and POD expansion on the library's kernels)."""
         torch = self.torch
         D = torch.from_numpy(np.ascontiguousarray(dirs, dtype=np.float32)).cuda()
-        y = self.mlp.forward(D).double() * self.scale                   # R x 2n_pod
-        c = torch.complex(y[:, 0::2], y[:, 1::2]).T                       # n_pod x R
-        return (self.U @ c).contiguous()
+        y = self.mlp.forward(D)                                         # R x 2 n_pod, FP32
+        return self.s.pod_guess(self.U, y.contiguous(), self.scale)
 
 
-def plane_wave_data(x_nodes, dirs, k):
-    """v = exp(i k d . x) at the nodes (N x R complex128, device)."""
-    import torch
-    X = torch.from_numpy(np.ascontiguousarray(x_nodes)).cuda()
-    D = torch.from_numpy(np.ascontiguousarray(dirs, dtype=np.float64)).cuda()
-    return torch.exp(1j * k * (X @ D.T)).contiguous()
+def plane_wave_data(s, dirs):
+    """v = exp(i k d . x) at the nodes (N x R complex128, device), by the library."""
+    return s.plane_waves(dirs, device=True)
 
 
-def iterations_with_and_without(s, ws: WarmStart, dirs, k, tol: float):
+def iterations_with_and_without(s, ws: WarmStart, dirs, tol: float):
     """Per-direction GMRES iterations to the relative residual tol, zero guess vs warm start."""
-    x, _, _ = s.get_nodes()
     it0, it1 = [], []
     for r in range(dirs.shape[0]):
-        v = plane_wave_data(x, dirs[r:r + 1], k)
+        v = plane_wave_data(s, dirs[r:r + 1])
         st0 = s.solve_data(v)
         x0 = ws.guess(dirs[r:r + 1])
         st1 = s.solve_data(v, x0=x0)
@@ -160,7 +149,7 @@ def main():
     t_fit = time.time() - t0
     # iterations to 1e-7 on the held-out directions: FP64 path, zero guess vs warm start
     s.set_options(precision=0, gmres_tol=1e-7)
-    it0, it1 = iterations_with_and_without(s, ws, held, wl.k, 1e-7)
+    it0, it1 = iterations_with_and_without(s, ws, held, 1e-7)
     # density error of the bare guess (reference: mixed refinement to 1e-11)
     s.set_options(precision=1, gmres_tol=1e-11, verify_final=1)
     Xh = ws.training_densities(held)
@@ -178,7 +167,7 @@ def main():
         its = []
         for a in range(0, held.shape[0], 64):
             d = held[a:a + 64]
-            v = plane_wave_data(x, d, wl.k)
+            v = plane_wave_data(s, d)
             st = s.solve_data(v, x0=ws.guess(d) if warm else None)
             its.append(st.iterations)
             part = torch.empty((out.shape[0], d.shape[0]), dtype=out.dtype, device=out.device)

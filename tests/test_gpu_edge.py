@@ -80,7 +80,7 @@ def test_empty_requests_and_bad_selectors_are_refused(tiny):
                  lambda: s.solve_plane_waves(np.zeros((0, 3))),
                  lambda: s.set_interbody_engine(7),
                  lambda: s.set_interbody_engine(-2),
-                 lambda: s.set_fp64_interbody_engine(2),
+                 lambda: s.set_fp64_interbody_engine(3),
                  lambda: s.set_modal_engine(3)):
         with pytest.raises(HzbError) as e:
             call()
