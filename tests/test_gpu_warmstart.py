@@ -139,10 +139,12 @@ def test_mlp_tensor_core_products_match_oracle_with_bf16_operands():
     t = rng.standard_normal((256, 512)).astype(np.float32)
     y = net.forward(x)
     y_ref, _ = omlp.forward(ref_params, x.astype(np.float64), operand)
-    assert rel_l2(y, y_ref) < 1e-4
+    # an operand whose FP32 (GPU) and FP64 (oracle) values straddle a BF16 rounding
+    # boundary rounds to neighbouring values (2^-8 apart): ~1e-4 after four layers
+    assert rel_l2(y, y_ref) < 1e-3
     loss, g = net.gradients(x, t)
     L_ref, g_ref = omlp.gradients(ref_params, x.astype(np.float64), t.astype(np.float64), operand)
-    assert abs(loss - L_ref) < 1e-4 * L_ref
+    assert abs(loss - L_ref) < 1e-3 * L_ref
     for (gW, gb), (rW, rb) in zip(net.layers(g), g_ref):
         assert rel_l2(gW, rW) < 1e-3
         assert rel_l2(gb, rb) < 1e-3
