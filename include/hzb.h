@@ -194,7 +194,9 @@ hzb_status hzb_build_scattering_matrices(hzb_ctx *ctx);
  * the shape and the wavenumber only, not on where the bodies sit), and each shape's
  * skeleton of the accelerated scheme when it has one (J, T, the reduced S_p and the
  * proxy radius; Sec. 5: the ID is local to the shape).  Needs a built context.  The
- * format is this library's own (magic "HZBSCAT1", version 3, host byte order).
+ * format is this library's own (magic "HZBSCAT1", version 4, host byte order): each
+ * skeleton is stored with its ID tolerance and proxy radius, and a skeleton the caller
+ * set (hzb_set_skeleton) with the arrangement of its shape's bodies.
  * Errors: HZB_ESTATE (not built), HZB_EINVAL (cannot write), HZB_ECUDA. */
 hzb_status hzb_save_scattering(hzb_ctx *ctx, const char *path);
 
@@ -203,8 +205,10 @@ hzb_status hzb_save_scattering(hzb_ctx *ctx, const char *path);
  * the order of their first hzb_add_body), then proceed as after a build.  The bodies'
  * positions and rotations may differ from the saving context's.  Saved skeletons
  * are restored where their proxy sphere still encloses every body of the shape and
- * excludes all others (caller-given skeletons always); when every shape has one, the
- * acceleration is on as after hzb_compress.  Version 2 files (no skeletons) load too.
+ * excludes all others, caller-given skeletons only when the shape's bodies sit where they
+ * sat when the file was written (hzb_get_skeleton_info reports each restored skeleton's
+ * eps); when every shape has one, the acceleration is on as after hzb_compress.
+ * Version 2 files (no skeletons) and version 3 files load too.
  * Errors: HZB_ESTATE (no bodies, or already built), HZB_EINVAL (unreadable file, other
  * version, or a k / eta / shape mismatch: nothing is loaded), HZB_ENOMEM, HZB_ECUDA. */
 hzb_status hzb_load_scattering(hzb_ctx *ctx, const char *path);
@@ -386,7 +390,9 @@ hzb_status hzb_eval_field(hzb_ctx *ctx, int n, const double *x, double *out);
  *   proxy_radius: rho for every shape, or 0 = per shape midway between its largest
  *                 node radius and the nearest other body's bounding sphere
  * Needs hzb_build_scattering_matrices.  HZB_EINVAL if a proxy sphere cannot enclose
- * its body while excluding every other body (bodies too close).  Device memory: about
+ * its body while excluding every other body (bodies too close), or if an open shell is
+ * asked for eps < 1e-6 (the proxy sphere is sampled at the body's N_F azimuths, which
+ * leaves an error floor near 1e-6 on a shell's off-diagonal blocks).  Device memory: about
  * 3 k n complex doubles per shape while it is compressed, then k n + 1.5 k^2. */
 hzb_status hzb_compress(hzb_ctx *ctx, double eps, int n_theta, double proxy_radius);
 
@@ -399,6 +405,12 @@ hzb_status hzb_set_skeleton(hzb_ctx *ctx, int body, int k, const int *J, const d
 /* The skeleton of the shape of `body`: *k (0: none); J (k ints, ascending) and T
  * (k x n complex, row-major, rows in the order of J) are filled when not NULL. */
 hzb_status hzb_get_skeleton(hzb_ctx *ctx, int body, int *k, int *J, double *T);
+
+/* The skeleton of the shape of `body`: *k its size (0: none), *eps the ID tolerance and
+ * *rho the proxy radius it was computed for (both 0 for a skeleton the caller set);
+ * after hzb_load_scattering, the values stored with the restored skeleton.  Any output
+ * may be NULL. */
+hzb_status hzb_get_skeleton_info(hzb_ctx *ctx, int body, int *k, double *eps, double *rho);
 
 /* on = 1: solves go through the reduced system (HZB_ESTATE without skeletons);
  * on = 0: the direct solve of Eq. (precond). */

@@ -146,6 +146,7 @@ def lib():
         "hzb_interbody_bodies": (i, [p, i, p, i, i, p, i, i]),
         "hzb_pod_basis": (i, [p, i, i, p, i, i, ctypes.c_ulonglong, p]),
         "hzb_incident_plane_waves": (i, [p, i, p, p, i]),
+        "hzb_get_skeleton_info": (i, [p, i, ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(d)]),
         "hzb_pod_project": (i, [p, i, i, i, p, p, p]),
         "hzb_pod_expand": (i, [p, i, i, i, p, p, p]),
         "hzb_pod_guess": (i, [p, i, i, i, p, p, d, p]),
@@ -548,6 +549,12 @@ class Solver:
         T = np.zeros((k.value, n), dtype=np.complex128)
         self._check(lib().hzb_get_skeleton(self._h, int(body), ctypes.byref(k), _ptr(J), _ptr(T)))
         return J, T
+
+    def get_skeleton_info(self, body: int):
+        """(k, eps, rho) of the skeleton of the body's shape (eps = rho = 0: set by the caller)."""
+        k, e, r = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        self._check(lib().hzb_get_skeleton_info(self._h, int(body), ctypes.byref(k), ctypes.byref(e), ctypes.byref(r)))
+        return k.value, e.value, r.value
 
     def get_skeleton_size(self, body: int) -> int:
         k = ctypes.c_int()

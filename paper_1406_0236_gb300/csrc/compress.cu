@@ -36,6 +36,7 @@
 namespace hzb {
 
 static const double CP_PI = 3.14159265358979323846;
+static const double OPEN_SHELL_EPS_FLOOR = 1e-6;   // smallest ID tolerance accepted for open shells
 
 // ------------------------------------------------------------------ block reductions
 
@@ -900,7 +901,10 @@ static hzb_status compress_shape(hzb_ctx *c, int shape, double eps, int n_theta,
     Z.release();
     st = install_skeleton(c, sd, J, T);
     T.release();
-    if (!st) sd.skel_rho = rho;
+    if (!st) {
+        sd.skel_rho = rho;
+        sd.skel_eps = eps;
+    }
     return done(st);
 }
 
@@ -954,6 +958,7 @@ void release_compression(hzb_ctx *c)
         s->St32.release(); s->red_offs.release();
         s->skel_k = 0;
         s->skel_rho = 0.0;
+        s->skel_eps = 0.0;
         s->skel_J.clear();
     }
     c->rb.release();
@@ -1413,6 +1418,15 @@ extern "C" hzb_status hzb_compress(hzb_ctx *c, double eps, int n_theta, double p
             st = fail(c, HZB_EINVAL, "proxy sphere must enclose its body and exclude every other body");
         }
         if (st) break;
+        // The proxy sphere is sampled at the body's N_F azimuths only.  For an open shell
+        // that leaves an error floor near 1e-6 on the off-diagonal blocks of Eq. (ip0) at
+        // small N_F (offset proxy rings remove it; pinned on the CPU): tighter tolerances
+        // are refused rather than missed silently.
+        if (c->shapes[s]->geom.spec.kind == HZB_OPEN_SHELL && eps < OPEN_SHELL_EPS_FLOOR) {
+            st = fail(c, HZB_EINVAL, "open-shell shapes are compressed only for eps >= 1e-6 (the proxy sphere "
+                                     "is sampled at the body's azimuths, whose error floor is near 1e-6)");
+            break;
+        }
         const int nt = n_theta > 0 ? n_theta : std::max(16, (int)std::ceil(1.2 * c->shapes[s]->geom.NG));
         st = compress_shape(c, (int)s, eps, nt, rho);
     }
@@ -1452,6 +1466,7 @@ extern "C" hzb_status hzb_set_skeleton(hzb_ctx *c, int body, int k, const int *J
     Td.release();
     if (st) return st;
     sd.skel_rho = 0.0;
+    sd.skel_eps = 0.0;
     bool all = true;
     for (ShapeDev *s : c->shapes) all = all && s->skel_k > 0;
     if (all) {
@@ -1476,6 +1491,17 @@ extern "C" hzb_status hzb_get_skeleton(hzb_ctx *c, int body, int *k, int *J, dou
             check_cuda(c, cudaStreamSynchronize(c->stream), "copy T"))
             return HZB_ECUDA;
     }
+    return HZB_OK;
+}
+
+extern "C" hzb_status hzb_get_skeleton_info(hzb_ctx *c, int body, int *k, double *eps, double *rho)
+{
+    CP_GUARD(c);
+    if (body < 0 || body >= (int)c->bodies.size()) return fail(c, HZB_EINVAL, "bad body");
+    const ShapeDev &sd = *c->shapes[c->bodies[body].shape];
+    if (k) *k = sd.skel_k;
+    if (eps) *eps = sd.skel_eps;
+    if (rho) *rho = sd.skel_rho;
     return HZB_OK;
 }
 

@@ -101,6 +101,7 @@ struct ShapeDev {
     // accelerated scheme (compress.cu, Sec. 5): the shape's skeleton and reduced blocks
     int skel_k = 0;                       // skeleton size k (0: none)
     double skel_rho = 0.0;                // proxy radius it was computed for (0: given by the caller)
+    double skel_eps = 0.0;                // ID tolerance it was computed for (0: given by the caller)
     std::vector<int> skel_J;              // skeleton nodes, shape-local, ascending
     DevBuf<double2> T64;                  // k x n row-major: V_p^* = T
     DevBuf<double2> U64;                  // n x k row-major: U_p = T^T
@@ -181,8 +182,8 @@ struct hzb_ctx {
     hzb::DevBuf<int2> blockpairs;              // unordered TargetBlock pairs on different bodies (nbody_sym.cu)
     long long n_blockpairs = 0;                // 0: not built, -1: none (one body)
     int nbody64_engine = -1;                   // FP64/double-float sums: -1 auto (pair-symmetric for R <= 4),
-                                               // 0 one-directional, 1 pair-symmetric (lean double-float),
-                                               // 2 pair-symmetric (double-float with normalised operations)
+                                               // 0 one-directional, 1 pair-symmetric (double-float: lean forms),
+                                               // 2 as -1 with the normalised double-float kernels
     hzb::DevBuf<int> kerr;                     // device error flag of kernels with bounded waits
     hzb::DevBuf<float> Ximg;                   // embedded, TF32-split modal panel (TMA modal GEMM)
     bool kerr_ready = false;
@@ -271,6 +272,7 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y);
 hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   // nbody_df.cu
 hzb_status interbody_dfl_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y);   // nbody_dfl.cu
+hzb_status interbody_dfl(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);   // nbody_dfl.cu
 hzb_status interbody_tc(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);
 hzb_status modal_gemm_tma(hzb_ctx *c, ShapeDev &sd, int ncols, const float2 *X, float2 *Cout);  // modal_tma.cu
 hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit,

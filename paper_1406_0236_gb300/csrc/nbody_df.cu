@@ -408,8 +408,12 @@ hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
     if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
     hzb_status st = ensure_df(c);
     if (st) return st;
-    if (c->nbody64_engine == 2) return interbody_df_sym(c, R, sigma, y);
+    if (c->nbody64_engine == 2 && R <= 4) return interbody_df_sym(c, R, sigma, y);
     if (c->nbody64_engine == 1 || (c->nbody64_engine < 0 && R <= 4)) return interbody_dfl_sym(c, R, sigma, y);
+    if (c->nbody64_engine != 2) {
+        const int ns = c->tunedf_split > 0 ? c->tunedf_split : default_nsplit(c, R, 1);
+        return interbody_dfl(c, R, sigma, y, ns);
+    }
     const int N = (int)c->N;
     const int rc = R == 1 ? 1 : (R <= 4 ? 4 : 8);
     const int tpt = c->tunedf_tpt > 0 ? c->tunedf_tpt : 1;

@@ -23,6 +23,7 @@
 // sin(delta) = delta - delta^3/6 + delta^5/120 (truncation below 1e-17) and angle addition.
 // The translation unit is compiled with -fmad=false so that the compiler never fuses
 // the separately rounded operations these transformations depend on.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -275,6 +276,121 @@ nbody_dfl_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restri
     }
 }
 
+// One-directional form for several right-hand sides (the refinement residual of a
+// batched solve): one CTA per (TargetBlock, chunk of RC right-hand sides, source chunk),
+// thread t owns target t of the block; sources in tiles of DFL_OT staged in shared memory.
+// Per ordered pair the geometry, e^{ikr} and the kernel value
+//     G = E [X - i (k r X + eta)],  E = e^{ikr} / r,  X = n_j.d / r^2
+// are formed once and serve the RC right-hand sides (a double-float complex
+// multiply-add each).  Source chunks write partial sums that a second kernel adds in a
+// fixed order, so the result is bit-reproducible.
+static const int DFL_OT = 64;
+
+template <int RC>
+__global__ void __launch_bounds__(512, 1)
+nbody_dfl_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pa,
+                 const float4 *__restrict__ pb, const float4 *__restrict__ pc, const double4 *__restrict__ pos64,
+                 const double2 *__restrict__ sigma, const float4 *__restrict__ tab, DflConst K,
+                 double2 *__restrict__ y, size_t split_stride)
+{
+    __shared__ float4 s_a[DFL_OT], s_b[DFL_OT], s_c[DFL_OT];
+    __shared__ float4 s_sig[DFL_OT][RC];
+    __shared__ float4 s_tab[DFL_TAB];
+    const TargetBlock tb = blocks[blockIdx.x];
+    const int r0 = blockIdx.y * RC;
+    const int tid = threadIdx.x;
+    for (int q = tid; q < DFL_TAB; q += blockDim.x) s_tab[q] = tab[q];
+    const int g0 = tb.start + min(tid, tb.count - 1);
+    const float4 TA = pa[g0], TB = pb[g0];
+    const dd tx = {TA.x, TB.x}, ty = {TA.y, TB.y}, tz = {TA.z, TB.z};
+    dd ar[RC], ai[RC];
+#pragma unroll
+    for (int c = 0; c < RC; ++c) ar[c] = ai[c] = {0.f, 0.f};
+    const int c0 = blockIdx.z * chunk, c1 = min(N, c0 + chunk);
+    for (int range = 0; range < 2; ++range) {
+        const int lo = range ? max(c0, tb.excl_hi) : c0;
+        const int hi = range ? c1 : min(c1, tb.excl_lo);
+        for (int j0 = lo; j0 < hi; j0 += DFL_OT) {
+            const int cnt = min(DFL_OT, hi - j0);
+            __syncthreads();
+            for (int q = tid; q < cnt; q += blockDim.x) {
+                const int g = j0 + q;
+                s_a[q] = pa[g];
+                s_b[q] = pb[g];
+                s_c[q] = pc[g];
+                const double wq = pos64[g].w * 0.07957747154594767;
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const double2 v = (r0 + c < R) ? sigma[(size_t)g * R + r0 + c] : make_double2(0.0, 0.0);
+                    const double vr = v.x * wq, vi = v.y * wq;
+                    const float hr = (float)vr, hi2 = (float)vi;
+                    s_sig[q][c] = make_float4(hr, (float)(vr - (double)hr), hi2, (float)(vi - (double)hi2));
+                }
+            }
+            __syncthreads();
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 A4 = s_a[jj], B4 = s_b[jj], C4 = s_c[jj];
+                const dd dx = sub(tx, {A4.x, B4.x}), dy = sub(ty, {A4.y, B4.y}), dz = sub(tz, {A4.z, B4.z});
+                const float px = dx.h * dx.h, py = dy.h * dy.h, pz = dz.h * dz.h;
+                const float ex = fmaf(dx.h + dx.h, dx.l, fmaf(dx.h, dx.h, -px));
+                const float ey = fmaf(dy.h + dy.h, dy.l, fmaf(dy.h, dy.h, -py));
+                const float ez = fmaf(dz.h + dz.h, dz.l, fmaf(dz.h, dz.h, -pz));
+                const float m1 = fmaxf(px, py), l1 = fminf(px, py);
+                const float s1 = m1 + l1, e1 = l1 - (s1 - m1);
+                const float m2 = fmaxf(s1, pz), l2 = fminf(s1, pz);
+                const float s2 = m2 + l2, e2 = l2 - (s2 - m2);
+                const dd r2 = {s2, (e1 + e2) + ((ex + ey) + ez)};
+                const float y0 = rsqrtf(r2.h);
+                const float q0 = y0 * y0, q0e = fmaf(y0, y0, -q0);
+                const float u = r2.h * q0;
+                const float ue = fmaf(r2.l, q0, fmaf(r2.h, q0e, fmaf(r2.h, q0, -u)));
+                const float e = (1.0f - u) - ue;
+                const dd ir = {y0, y0 * e * fmaf(e, 0.375f, 0.5f)};
+                const dd r = mul(r2, ir);
+                const dd kr = mul(K.k, r);
+                dd cs, sn;
+                dfl_cis(mul(K.kt, r), s_tab, K, cs, sn);
+                const dd Er = mul(cs, ir), Ei = mul(sn, ir);
+                const dd nx = {A4.w, B4.w}, ny = {C4.x, C4.z}, nz = {C4.y, C4.w};
+                const dd X = mul(add(add(mul(nx, dx), mul(ny, dy)), mul(nz, dz)), mul(ir, ir));
+                const dd Bv = add(mul(kr, X), K.eta);
+                const dd gr = add(mul(Er, X), mul(Ei, Bv)), gi = sub(mul(Ei, X), mul(Er, Bv));
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    const float4 S = s_sig[jj][c];
+                    const dd sr = {S.x, S.y}, si = {S.z, S.w};
+                    ar[c] = add(ar[c], sub(mul(gr, sr), mul(gi, si)));
+                    ai[c] = add(ai[c], add(mul(gr, si), mul(gi, sr)));
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < RC; ++c) { ar[c] = norm(ar[c]); ai[c] = norm(ai[c]); }
+        }
+    }
+    if (tid < tb.count) {
+        double2 *yo = y + blockIdx.z * split_stride;
+#pragma unroll
+        for (int c = 0; c < RC; ++c)
+            if (r0 + c < R)
+                yo[(size_t)(tb.start + tid) * R + r0 + c] =
+                    make_double2((double)ar[c].h + (double)ar[c].l, (double)ai[c].h + (double)ai[c].l);
+    }
+}
+
+__global__ void dfl_split_reduce_kernel(size_t n, int nsplit, const double2 *__restrict__ part,
+                                        double2 *__restrict__ y)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < nsplit; ++s) {
+        const double2 v = part[s * n + e];
+        sx += v.x;
+        sy += v.y;
+    }
+    y[e] = make_double2(sx, sy);
+}
+
 // cos/sin(2 pi m / 1024) split into double-float, built once per context
 static hzb_status ensure_dfl_table(hzb_ctx *c)
 {
@@ -301,6 +417,56 @@ static dd dd_of(double v)
     return {h, (float)(v - (double)h)};
 }
 
+static DflConst dfl_constants(const hzb_ctx *c)
+{
+    DflConst K;
+    K.k = dd_of(c->k);
+    K.kt = dd_of(c->k / (2.0 * M_PI));
+    K.twopi = dd_of(2.0 * M_PI);
+    K.eta = dd_of(c->eta);
+    return K;
+}
+
+// one-directional lean double-float sum (R right-hand sides in chunks of 1, 4 or 8, source
+// chunks for occupancy, added in a fixed order); node arrays as for the symmetric form
+hzb_status interbody_dfl(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit)
+{
+    hzb_status st = ensure_dfl_table(c);
+    if (st) return st;
+    const int N = (int)c->N;
+    const int rc = R == 1 ? 1 : (R <= 4 ? 4 : 8);
+    int chunk = (N + nsplit - 1) / nsplit;
+    chunk = ((chunk + DFL_OT - 1) / DFL_OT) * DFL_OT;
+    nsplit = (N + chunk - 1) / chunk;
+    const size_t n = (size_t)N * R;
+    double2 *out = y;
+    if (nsplit > 1) {
+        if (check_cuda(c, c->nb_part64.ensure(n * nsplit), "alloc partial sums")) return HZB_ENOMEM;
+        out = c->nb_part64.ptr;
+    }
+    const DflConst K = dfl_constants(c);
+    c->interbody_calls++;
+    c->launches += (nsplit > 1) ? 2 : 1;
+    const int slot = prof_begin(c, 2);
+    const int nb = (c->tune_limit_blocks > 0) ? std::min(c->tune_limit_blocks, c->n_tblocks - c->tblock_off)
+                                              : c->n_tblocks - c->tblock_off;
+    dim3 g(nb, (R + rc - 1) / rc, nsplit);
+    const TargetBlock *tb = c->tblocks.ptr + c->tblock_off;
+    if (rc == 1)
+        nbody_dfl_kernel<1><<<g, 512, 0, c->stream>>>(tb, N, R, chunk, c->dfa.ptr, c->dfb.ptr, c->dfc.ptr, c->pos64.ptr,
+                                                      sigma, c->dfltab.ptr, K, out, n);
+    else if (rc == 4)
+        nbody_dfl_kernel<4><<<g, 512, 0, c->stream>>>(tb, N, R, chunk, c->dfa.ptr, c->dfb.ptr, c->dfc.ptr, c->pos64.ptr,
+                                                      sigma, c->dfltab.ptr, K, out, n);
+    else
+        nbody_dfl_kernel<8><<<g, 512, 0, c->stream>>>(tb, N, R, chunk, c->dfa.ptr, c->dfb.ptr, c->dfc.ptr, c->pos64.ptr,
+                                                      sigma, c->dfltab.ptr, K, out, n);
+    if (nsplit > 1) dfl_split_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, nsplit, out, y);
+    cudaError_t e = cudaGetLastError();
+    prof_end(c, slot);
+    return check_cuda(c, e, "nbody_dfl_kernel");
+}
+
 // pair-symmetric lean double-float sum; the split node arrays (dfa, dfb, dfc) come from
 // the double-float set-up of nbody_df.cu (ensure_df), which the caller has run
 hzb_status interbody_dfl_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
@@ -316,11 +482,7 @@ hzb_status interbody_dfl_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y
     if (c->n_blockpairs < 0) return HZB_OK;
     if (c->n_blockpairs > 0x7fffffffLL) return fail(c, HZB_EINVAL, "too many block pairs for one launch");
     c->launches += 1;
-    DflConst K;
-    K.k = dd_of(c->k);
-    K.kt = dd_of(c->k / (2.0 * M_PI));
-    K.twopi = dd_of(2.0 * M_PI);
-    K.eta = dd_of(c->eta);
+    const DflConst K = dfl_constants(c);
     const int slot = prof_begin(c, 2);
     const int rc = (R == 1) ? 1 : 2;
     dim3 g((unsigned)c->n_blockpairs, (R + rc - 1) / rc, 1);

@@ -12,11 +12,17 @@
 //              (row = target ring);
 //   then per shape the skeleton of the accelerated scheme (Sec. 5): int32 k (0: none),
 //              double rho (the proxy radius it was computed for, 0 if given by the
-//              caller); if k > 0: k int32 skeleton nodes (ascending), k n complex
-//              doubles of T (row-major), k k complex doubles of the reduced S_p.
-// Version 2 files (no skeleton section) load too.  A skeleton loads only where its
-// proxy sphere still separates the bodies of the new arrangement; when every shape
-// has one, the reduced system is built and solves use it.
+//              caller), double eps (the ID tolerance, 0 if given by the caller); for a
+//              caller's skeleton int32 m and the m bodies of the shape it was set for
+//              (centre, rotation: 12 doubles each); if k > 0: k int32 skeleton nodes
+//              (ascending), k n complex doubles of T (row-major), k k complex doubles of
+//              the reduced S_p.
+// Version 2 files (no skeleton section) and version 3 files (no eps, no arrangement)
+// load too.  A computed skeleton loads only where its proxy sphere still separates the
+// bodies of the new arrangement, a caller's skeleton only into the arrangement it was
+// set for (it carries no proxy sphere that would validate another); when every shape
+// has one, the reduced system is built and solves use it.  hzb_get_skeleton_info
+// reports the restored skeleton's eps.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -55,7 +61,7 @@ extern "C" hzb_status hzb_save_scattering(hzb_ctx *c, const char *path)
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(c, HZB_EINVAL, std::string("cannot open for writing: ") + path);
     bool ok = true;
-    const int version = 3, ns = (int)c->shapes.size();
+    const int version = 4, ns = (int)c->shapes.size();
     ok &= std::fwrite(HZB_SCAT_MAGIC, 1, 8, f) == 8;
     ok &= std::fwrite(&version, sizeof(int), 1, f) == 1;
     ok &= std::fwrite(&ns, sizeof(int), 1, f) == 1;
@@ -95,6 +101,15 @@ extern "C" hzb_status hzb_save_scattering(hzb_ctx *c, const char *path)
         const int k = sd.skel_k, n = sd.geom.NG * sd.geom.NF;
         ok &= std::fwrite(&k, sizeof(int), 1, f) == 1;
         ok &= std::fwrite(&sd.skel_rho, sizeof(double), 1, f) == 1;
+        ok &= std::fwrite(&sd.skel_eps, sizeof(double), 1, f) == 1;
+        if (sd.skel_rho == 0.0) {                          // the arrangement a caller's skeleton is for
+            const int m = (int)sd.bodies.size();
+            ok &= std::fwrite(&m, sizeof(int), 1, f) == 1;
+            for (int b : sd.bodies) {
+                ok &= std::fwrite(c->bodies[b].c, sizeof(double), 3, f) == 3;
+                ok &= std::fwrite(c->bodies[b].rot, sizeof(double), 9, f) == 9;
+            }
+        }
         if (k == 0 || !ok) continue;
         ok &= std::fwrite(sd.skel_J.data(), sizeof(int), k, f) == (size_t)k;
         const size_t nt = (size_t)k * n, ns2 = (size_t)k * k;
@@ -127,7 +142,7 @@ extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
     int version = 0, ns = 0;
     double k = 0.0, eta = 0.0;
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, HZB_SCAT_MAGIC, 8) == 0;
-    ok = ok && std::fread(&version, sizeof(int), 1, f) == 1 && (version == 2 || version == 3);
+    ok = ok && std::fread(&version, sizeof(int), 1, f) == 1 && version >= 2 && version <= 4;
     ok = ok && std::fread(&ns, sizeof(int), 1, f) == 1 && std::fread(&k, sizeof(double), 1, f) == 1 &&
          std::fread(&eta, sizeof(double), 1, f) == 1;
     if (!ok) {
@@ -190,19 +205,45 @@ extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
     }
     c->t_setup_ms = 0.0;
     c->state = 3;
-    if (version == 3) {
-        // skeletons: each is restored where its proxy sphere still fits the arrangement
+    if (version >= 3) {
+        // skeletons: each is restored where its proxy sphere still fits the arrangement, a
+        // caller's skeleton only into the arrangement it was set for
         bool all = true;
         for (int s = 0; s < ns; ++s) {
             ShapeDev &sd = *c->shapes[s];
             const int n = sd.geom.NG * sd.geom.NF;
             int k = 0;
-            double rho = 0.0;
+            double rho = 0.0, eps = 0.0;
+            bool same_arrangement = true;
             if (std::fread(&k, sizeof(int), 1, f) != 1 || std::fread(&rho, sizeof(double), 1, f) != 1 || k < 0 ||
-                k > n) {
+                k > n || (version >= 4 && std::fread(&eps, sizeof(double), 1, f) != 1)) {
                 std::fclose(f);
                 release_compression(c);
                 return fail(c, HZB_EINVAL, "file ends early or holds a bad skeleton size");
+            }
+            if (version >= 4 && rho == 0.0) {
+                int m = 0;
+                if (std::fread(&m, sizeof(int), 1, f) != 1 || m < 0 || m > (1 << 20)) {
+                    std::fclose(f);
+                    release_compression(c);
+                    return fail(c, HZB_EINVAL, "file ends early or holds a bad body count");
+                }
+                same_arrangement = m == (int)sd.bodies.size();
+                for (int q = 0; q < m; ++q) {
+                    double xf[12];
+                    if (std::fread(xf, sizeof(double), 12, f) != 12) {
+                        std::fclose(f);
+                        release_compression(c);
+                        return fail(c, HZB_EINVAL, "file ends early");
+                    }
+                    if (same_arrangement) {
+                        const BodyRec &b = c->bodies[sd.bodies[q]];
+                        same_arrangement = std::memcmp(xf, b.c, 3 * sizeof(double)) == 0 &&
+                                           std::memcmp(xf + 3, b.rot, 9 * sizeof(double)) == 0;
+                    }
+                }
+            } else if (version == 3 && rho == 0.0) {
+                same_arrangement = false;                  // no record of the arrangement: not restored
             }
             if (k == 0) {
                 all = false;
@@ -224,7 +265,7 @@ extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
                 release_compression(c);
                 return fail(c, HZB_EINVAL, "bad skeleton indices in the file");
             }
-            if (rho > 0.0 && !proxy_fits(c, s, rho)) {
+            if ((rho > 0.0 && !proxy_fits(c, s, rho)) || (rho == 0.0 && !same_arrangement)) {
                 all = false;
                 continue;
             }
@@ -243,6 +284,7 @@ extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
                 return st;
             }
             sd.skel_rho = rho;
+            sd.skel_eps = eps;
         }
         if (all) {
             if ((st = build_reduced(c))) {

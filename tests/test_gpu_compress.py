@@ -298,3 +298,32 @@ def test_compressed_solve_with_device_tensors(sep):
     out = torch.empty_like(vd)
     s.get_density(out)
     assert rel_l2(out.cpu().numpy(), host) < 1e-9
+
+
+def _shells_and_sphere():
+    shell = W.ShapeSpec(W.OPEN_SHELL, (1.0, 0.8, np.pi / 3, 0.1), 8, 6, 17)
+    ball = W.ShapeSpec(W.SPHERE, (0.8,), 6, 6, 17)
+    bodies = [W.Body(shell, np.array([-3.2, 0.0, 0.0]), W.rotation_taking_z_to([0.2, 0.3, 1.0])),
+              W.Body(shell, np.array([3.1, 0.4, 0.2]), W.rotation_taking_z_to([-1.0, 0.2, 0.1])),
+              W.Body(ball, np.array([0.0, 3.3, -0.2]), np.eye(3))]
+    return W.Workload("shells_sphere", bodies, 2.0, 2.0, np.array([[0.0, 0.0, 1.0]]))
+
+
+def test_open_shells_compressed_only_above_the_proxy_floor():
+    """Open shells: eps < 1e-6 is refused (the proxy sphere is sampled at the body's
+    azimuths only); at eps = 1e-5 the compressed solve agrees with the direct one to the
+    tolerance times the conditioning."""
+    require_gpu()
+    from paper_1406_0236_gb300 import HzbError
+    wl = _shells_and_sphere()
+    s = gpu_solver(wl, tol=1e-12)
+    s.solve_plane_waves(wl.directions)
+    direct = s.get_density().copy()
+    with pytest.raises(HzbError) as e:
+        s.compress(1e-9)
+    assert e.value.status == -1 and "open-shell" in str(e.value)
+    s.compress(1e-5)
+    assert 0 < s.reduced_size < s.N
+    st = s.solve_plane_waves(wl.directions)
+    assert st.converged
+    assert rel_l2(s.get_density(), direct) < 1e-3

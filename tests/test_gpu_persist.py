@@ -105,3 +105,35 @@ def test_skeletons_saved_and_restored(tmp_path):
     fresh = gpu_solver(cw, precision=0, tol=1e-12)
     fresh.solve_plane_waves(cw.directions)
     assert rel_l2(t.get_density(), fresh.get_density()) < 1e-12
+
+
+def test_saved_skeletons_carry_eps_and_caller_skeletons_their_arrangement(tmp_path):
+    """Version-4 files: a computed skeleton is restored with the tolerance it was computed
+    for; a skeleton the caller set is restored only into the arrangement it was set for."""
+    require_gpu()
+    from paper_1406_0236_gb300 import Options, Solver
+    wl = W.separated_spheroids(spacing=4.0, n_panels=6, gl_order=8, n_modes=21)
+    s = gpu_solver(wl, precision=0, tol=1e-12)
+    s.compress(1e-9)
+    k, eps, rho = s.get_skeleton_info(0)
+    assert k > 0 and eps == 1e-9 and rho > 0
+    path = str(tmp_path / "computed.bin")
+    s.save_scattering(path)
+    t = Solver.from_workload(wl, Options(precision=0, gmres_tol=1e-12))
+    t.load_scattering(path)
+    assert t.get_skeleton_info(0) == (k, 1e-9, rho)
+    # the caller's skeleton (the computed one, given back by hand)
+    J, T = s.get_skeleton(0)
+    u = gpu_solver(wl, precision=0, tol=1e-12)
+    u.set_skeleton(0, J, T)
+    assert u.get_skeleton_info(0) == (J.size, 0.0, 0.0)
+    path2 = str(tmp_path / "caller.bin")
+    u.save_scattering(path2)
+    same = Solver.from_workload(wl, Options(precision=0, gmres_tol=1e-12))
+    same.load_scattering(path2)
+    assert same.get_skeleton_size(0) == J.size
+    moved = [W.Body(b.shape, b.center + np.array([0.0, 0.0, 0.5]), b.rot) for b in wl.bodies]
+    mw = W.Workload("moved", moved, wl.k, wl.eta, wl.directions)
+    other = Solver.from_workload(mw, Options(precision=0, gmres_tol=1e-12))
+    other.load_scattering(path2)
+    assert other.get_skeleton_size(0) == 0 and other.reduced_size == 0
