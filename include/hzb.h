@@ -59,7 +59,9 @@ typedef enum {
  * the data, the guess or the operator), and non-convergence as HZB_ENOCONV.  Every
  * wait of a kernel on an mbarrier is bounded: when one runs out the kernel frees its
  * tensor memory, writes NaN to its outputs and sets a flag that the call reports as
- * HZB_ETIMEOUT (the flag is then cleared, so the context stays usable).  Geometry is
+ * HZB_ETIMEOUT (the flag is then cleared, so the context stays usable); inside a solve
+ * the flag is read once, at the end of the solve (no synchronisation per launch), unless
+ * the NaN outputs stopped GMRES first (HZB_ENAN).  Geometry is
  * checked when the nodes are generated: intersecting bodies and non-finite or
  * degenerate nodes give HZB_EINVAL.
  *

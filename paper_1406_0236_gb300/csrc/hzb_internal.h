@@ -216,6 +216,7 @@ struct hzb_ctx {
     unsigned char gkey[256];
     bool gkey_valid = false;
     bool capturing = false;
+    bool in_solve = false;                     // inside solve_driver: error flags are read at its end
     // accelerated scheme (compress.cu): the reduced system of Eq. (ip6) as a context of its
     // own over the skeleton nodes; its local operator is the dense S_p of each body
     hzb_ctx *rctx = nullptr;

@@ -548,7 +548,10 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
     const size_t NR = (size_t)c->N * R;
     hzb_status st;
     DevBuf<double2> &bbuf = c->s_b, &rbuf = c->s_r, &dbuf = c->s_d;
-    auto cleanup = [&]() {};
+    // kernels with bounded waits leave their error flag for the end of the solve (no
+    // per-launch synchronisation inside the iteration)
+    c->in_solve = true;
+    auto cleanup = [&]() { c->in_solve = false; };
     if (check_cuda(c, c->sol.ensure(NR), "alloc densities") || check_cuda(c, bbuf.ensure(NR), "alloc rhs")) {
         cleanup();
         return HZB_ENOMEM;
@@ -639,6 +642,16 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
     }
     cudaEventRecord(c->ev1, c->stream);
     if (check_cuda(c, cudaEventSynchronize(c->ev1), "solve")) { cleanup(); return HZB_ECUDA; }
+    cleanup();
+    if (c->kerr_ready) {                          // a bounded tensor-core wait that ran out during the solve
+        int flag = 0;
+        if (check_cuda(c, cudaMemcpy(&flag, c->kerr.ptr, sizeof(int), cudaMemcpyDeviceToHost), "read error flag"))
+            return HZB_ECUDA;
+        if (flag) {
+            cudaMemset(c->kerr.ptr, 0, sizeof(int));
+            return fail(c, HZB_ETIMEOUT, "tensor-core wait timed out during the solve");
+        }
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     c->prof_on = false;

@@ -582,7 +582,8 @@ hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
     cudaError_t e = cudaGetLastError();
     prof_end(c, slot);
     if (check_cuda(c, e, "nbody_tc5_kernel")) return HZB_ECUDA;
-    if (!c->capturing) {               // a bounded wait that ran out: outputs are NaN
+    if (!c->capturing && !c->in_solve) {   // a bounded wait that ran out: outputs are NaN (a solve
+                                           // reads the flag once at its end instead)
         int flag = 0;
         if (check_cuda(c, cudaMemcpyAsync(&flag, c->kerr.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
                        "read error flag") ||
