@@ -75,86 +75,6 @@ __device__ __forceinline__ dd norm(dd a)
     return {s, a.l - (s - a.h)};
 }
 
-// The same operations on two independent values at once with packed f32x2 instructions
-// (round to nearest, no flush to zero): lane 0 and lane 1 of every register are the two
-// directions of a node pair.  Negation flips the two sign bits with an integer xor.
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float a, float b)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
-__device__ __forceinline__ f2 padd(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 psub(f2 a, f2 b)
-{
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 pmul(f2 a, f2 b)
-{
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 pfma(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2 pneg(f2 a)
-{
-    f2 d;
-    asm("xor.b64 %0, %1, 0x8000000080000000;" : "=l"(d) : "l"(a));
-    return d;
-}
-
-struct pdd {
-    f2 h, l;
-};
-
-__device__ __forceinline__ pdd pd_pack(dd a, dd b) { return {pk(a.h, b.h), pk(a.l, b.l)}; }
-__device__ __forceinline__ pdd pd_splat(dd a) { return {pk(a.h, a.h), pk(a.l, a.l)}; }
-
-__device__ __forceinline__ pdd pd_mul(pdd a, pdd b)
-{
-    const f2 p = pmul(a.h, b.h);
-    f2 e = pfma(a.h, b.h, pneg(p));
-    e = pfma(a.h, b.l, e);
-    e = pfma(a.l, b.h, e);
-    return {p, e};
-}
-
-__device__ __forceinline__ pdd pd_add(pdd a, pdd b)
-{
-    const f2 s = padd(a.h, b.h), bb = psub(s, a.h);
-    const f2 e = padd(psub(a.h, psub(s, bb)), psub(b.h, bb));
-    return {s, padd(e, padd(a.l, b.l))};
-}
-
-// two_sum(a.h, -b.h) written with subtractions: (a - (s - bb)) + (-b - bb) = (a - (s - bb)) - (b + bb)
-__device__ __forceinline__ pdd pd_sub(pdd a, pdd b)
-{
-    const f2 s = psub(a.h, b.h), bb = psub(s, a.h);
-    const f2 e = psub(psub(a.h, psub(s, bb)), padd(b.h, bb));
-    return {s, padd(e, psub(a.l, b.l))};
-}
-
-__device__ __forceinline__ pdd pd_norm(pdd a)
-{
-    const f2 s = padd(a.h, a.l);
-    return {s, psub(a.l, psub(s, a.h))};
-}
-
 }  // namespace
 
 static const int DFL_T = 512;          // targets per CTA (= TargetBlock size)
@@ -262,7 +182,6 @@ nbody_dfl_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restri
         if (DFL_S < bj.count) fetch(DFL_S);
     }
     const bool warp_live = warp * 32 < bi.count;
-    const dd nmx = neg(mx), nmy = neg(my), nmz = neg(mz);
     int buf = 0;
     for (int j0 = 0; j0 < bj.count; j0 += DFL_S, buf ^= 1) {
         const int cnt = min(DFL_S, bj.count - j0);
@@ -276,8 +195,6 @@ nbody_dfl_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restri
         dd asr[RC], asi[RC];
 #pragma unroll
         for (int c = 0; c < RC; ++c) asr[c] = asi[c] = {0.f, 0.f};
-        // RC == 1: target-side sum in the low halves, the tile's source-side sum in the high
-        pdd accR = pd_pack(atr[0], {0.f, 0.f}), accI = pd_pack(ati[0], {0.f, 0.f});
         for (int s = 0; s < DFL_S; ++s) {
             const int q = (lane + s) & (DFL_S - 1);
             const float4 A4 = T.a[q], B4 = T.b[q], C4 = T.c[q];
@@ -310,59 +227,30 @@ nbody_dfl_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restri
             const dd Er = mul(cs, ir), Ei = mul(sn, ir);
             const dd Pr = add(Er, mul(Ei, kr)), Pi = sub(Ei, mul(Er, kr));
             const dd Qr = mul(K.eta, Ei), Qi = neg(mul(K.eta, Er));
+            // i <- j: normal of source j
             const dd nx = {A4.w, B4.w}, ny = {C4.x, C4.z}, nz = {C4.y, C4.w};
-            if constexpr (RC == 1) {
-                // both directions in the two halves of packed registers: i <- j with the
-                // source normal n_j, j <- i with the target normal, negated (d reversed)
-                const pdd NX = pd_pack(nx, nmx), NY = pd_pack(ny, nmy), NZ = pd_pack(nz, nmz);
-                const pdd X = pd_mul(pd_add(pd_add(pd_mul(NX, pd_splat(dx)), pd_mul(NY, pd_splat(dy))),
-                                            pd_mul(NZ, pd_splat(dz))),
-                                     pd_splat(ir2));
-                const pdd GR = pd_add(pd_mul(X, pd_splat(Pr)), pd_splat(Qr));
-                const pdd GI = pd_add(pd_mul(X, pd_splat(Pi)), pd_splat(Qi));
-                const float4 S = T.sig[q][0];
-                const pdd SR = pd_pack({S.x, S.y}, wr[0]), SI = pd_pack({S.z, S.w}, wi[0]);
-                accR = pd_add(accR, pd_sub(pd_mul(GR, SR), pd_mul(GI, SI)));
-                accI = pd_add(accI, pd_add(pd_mul(GR, SI), pd_mul(GI, SR)));
-                // the source-side halves move one lane down
-                const int from = (lane + 1) & 31;
-                float a, b;
-                upk(accR.h, a, b); accR.h = pk(a, __shfl_sync(0xffffffffu, b, from));
-                upk(accR.l, a, b); accR.l = pk(a, __shfl_sync(0xffffffffu, b, from));
-                upk(accI.h, a, b); accI.h = pk(a, __shfl_sync(0xffffffffu, b, from));
-                upk(accI.l, a, b); accI.l = pk(a, __shfl_sync(0xffffffffu, b, from));
-            } else {
-                // i <- j: normal of source j
-                const dd X1 = mul(add(add(mul(nx, dx), mul(ny, dy)), mul(nz, dz)), ir2);
-                const dd g1r = add(mul(X1, Pr), Qr), g1i = add(mul(X1, Pi), Qi);
-                // j <- i: normal of target i, d reversed
-                const dd X2 = neg(mul(add(add(mul(mx, dx), mul(my, dy)), mul(mz, dz)), ir2));
-                const dd g2r = add(mul(X2, Pr), Qr), g2i = add(mul(X2, Pi), Qi);
+            const dd X1 = mul(add(add(mul(nx, dx), mul(ny, dy)), mul(nz, dz)), ir2);
+            const dd g1r = add(mul(X1, Pr), Qr), g1i = add(mul(X1, Pi), Qi);
+            // j <- i: normal of target i, d reversed
+            const dd X2 = neg(mul(add(add(mul(mx, dx), mul(my, dy)), mul(mz, dz)), ir2));
+            const dd g2r = add(mul(X2, Pr), Qr), g2i = add(mul(X2, Pi), Qi);
 #pragma unroll
-                for (int c = 0; c < RC; ++c) {
-                    const float4 S = T.sig[q][c];
-                    const dd sr = {S.x, S.y}, si = {S.z, S.w};
-                    atr[c] = add(atr[c], sub(mul(g1r, sr), mul(g1i, si)));
-                    ati[c] = add(ati[c], add(mul(g1r, si), mul(g1i, sr)));
-                    asr[c] = add(asr[c], sub(mul(g2r, wr[c]), mul(g2i, wi[c])));
-                    asi[c] = add(asi[c], add(mul(g2r, wi[c]), mul(g2i, wr[c])));
-                }
-#pragma unroll
-                for (int c = 0; c < RC; ++c) {
-                    const int from = (lane + 1) & 31;
-                    asr[c].h = __shfl_sync(0xffffffffu, asr[c].h, from);
-                    asr[c].l = __shfl_sync(0xffffffffu, asr[c].l, from);
-                    asi[c].h = __shfl_sync(0xffffffffu, asi[c].h, from);
-                    asi[c].l = __shfl_sync(0xffffffffu, asi[c].l, from);
-                }
+            for (int c = 0; c < RC; ++c) {
+                const float4 S = T.sig[q][c];
+                const dd sr = {S.x, S.y}, si = {S.z, S.w};
+                atr[c] = add(atr[c], sub(mul(g1r, sr), mul(g1i, si)));
+                ati[c] = add(ati[c], add(mul(g1r, si), mul(g1i, sr)));
+                asr[c] = add(asr[c], sub(mul(g2r, wr[c]), mul(g2i, wi[c])));
+                asi[c] = add(asi[c], add(mul(g2r, wi[c]), mul(g2i, wr[c])));
             }
-        }
-        if constexpr (RC == 1) {                           // unpack the tile's sums
-            float a, b, c2, d2;
-            upk(accR.h, a, b); upk(accR.l, c2, d2);
-            atr[0] = {a, c2}; asr[0] = {b, d2};
-            upk(accI.h, a, b); upk(accI.l, c2, d2);
-            ati[0] = {a, c2}; asi[0] = {b, d2};
+#pragma unroll
+            for (int c = 0; c < RC; ++c) {
+                const int from = (lane + 1) & 31;
+                asr[c].h = __shfl_sync(0xffffffffu, asr[c].h, from);
+                asr[c].l = __shfl_sync(0xffffffffu, asr[c].l, from);
+                asi[c].h = __shfl_sync(0xffffffffu, asi[c].h, from);
+                asi[c].l = __shfl_sync(0xffffffffu, asi[c].l, from);
+            }
         }
 #pragma unroll
         for (int c = 0; c < RC; ++c) { atr[c] = norm(atr[c]); ati[c] = norm(ati[c]); }
