@@ -48,7 +48,7 @@ FLOPS_PER_PAIR = 36       # algorithmic flops of one pair interaction at R = 1 (
 ORACLE_ITERS = 16
 # DRAM bytes (read + write) per launch on this workload from one ncu capture of each kernel
 # (profiles/); None for a kernel without a capture of its current version.
-DRAM_BYTES_NCU = {"nbody64_sym_kernel": 25.96e6, "nbody32_sym_kernel": 15.42e6}
+DRAM_BYTES_NCU = {"nbody64_sym_kernel": 25.96e6, "nbody32_sym_kernel": 15.85e6, "nbody_dfl_sym_kernel": 30.14e6}
 # FP32-pipe (FMA) thread operations per unordered node pair of the lean double-float kernel,
 # counted by ncu (profiles/nbody_dfl_sym_kernel_mixed4_shells.md)
 DFL_OPS_PER_UNORDERED_PAIR = 440
@@ -563,6 +563,7 @@ def main():
     perdf = tdf / max(ndf, 1)
     opsdf = DFL_OPS_PER_UNORDERED_PAIR * pairs / 2
     roofdf = {"kernel": "nbody_dfl_sym_kernel", "bound": "alu", "ms_per_launch": perdf,
+              "traffic": DRAM_BYTES_NCU.get("nbody_dfl_sym_kernel"),
               "share_of_step": tdf / sum(times),
               "achieved": FLOPS_PER_PAIR * pairs / (perdf * 1e-3) / 1e12 if ndf else None, "unit": "TFLOP/s",
               "note": "achieved counts the pair kernel's 36 algorithmic flops per ordered pair; in double-float "
