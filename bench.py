@@ -223,7 +223,7 @@ def timed_solves(torch, s, d, n, flush, barrier, ev0, ev1):
     return times, stats
 
 
-def mlp_leg(torch, local, n_train=4096, n_held=512, batch=64, epochs=400):
+def mlp_leg(torch, local, n_train=4096, n_held=512, batch=64, epochs=1600):
     """The metric's "+MLP" half on its own workload (two unit spheres, 8,200 unknowns,
     k = 2): 4,096 training solves (untimed), POD basis and network training on the
     library's kernels (timed, reported), then the 512 held-out directions in batches of
@@ -247,23 +247,31 @@ def mlp_leg(torch, local, n_train=4096, n_held=512, batch=64, epochs=400):
     X = ws.training_densities(train)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
-    ws.fit(train, X, epochs=epochs)
+    ws.fit(train, X, epochs=epochs, lr=3e-3, lr_final=1e-5)
     Xh = ws.training_densities(held)                     # references (mixed refinement to 1e-11)
     G = ws.guess(held)
     gerr = (torch.linalg.vector_norm(G - Xh, dim=0) / torch.linalg.vector_norm(Xh, dim=0)).cpu().numpy()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def run(prec, tol, warm, residual):
-        s.set_options(precision=prec, gmres_tol=tol, verify_final=1 if prec == 0 else 0, residual=residual)
+        s.set_options(precision=prec, gmres_tol=tol, verify_final=1 if prec == 0 else 0, residual=residual,
+                      inner_tol=1e-6)
         vs = [s.plane_waves(held[a:a + batch]) for a in range(0, n_held, batch)]
         out = torch.empty_like(Xh)
         its = []
+        split = {"solve_ms": 0.0, "fp32_interbody_ms": 0.0, "fp32_interbody_launches": 0, "residual_interbody_ms": 0.0,
+                 "residual_interbody_launches": 0}
         torch.cuda.synchronize()
         ev0.record()
         for q, a in enumerate(range(0, n_held, batch)):
             d = held[a:a + batch]
             st = s.solve_data(vs[q], x0=ws.guess(d) if warm else None)
             its.append(st.iterations)
+            split["solve_ms"] += st.t_solve_ms
+            split["fp32_interbody_ms"] += st.t_nbody32_ms
+            split["fp32_interbody_launches"] += st.n_nbody32
+            split["residual_interbody_ms"] += st.t_nbodydf_ms + st.t_nbody64_ms
+            split["residual_interbody_launches"] += st.n_nbodydf + st.n_nbody64
             part = torch.empty((out.shape[0], d.shape[0]), dtype=out.dtype, device=out.device)
             s.get_density(part)
             out[:, a:a + d.shape[0]] = part
@@ -272,10 +280,11 @@ def mlp_leg(torch, local, n_train=4096, n_held=512, batch=64, epochs=400):
         ms = ev0.elapsed_time(ev1)
         err = float((torch.linalg.vector_norm(out - Xh, dim=0) / torch.linalg.vector_norm(Xh, dim=0)).max())
         return {"value": 1e3 * n_held / ms, "unit": "RHS solves/s", "ms": ms, "iterations_per_batch": its,
-                "density_err_max": err}
+                "density_err_max": err, "split_over_batches": split}
 
     res = {"workload": "two_spheres_8200 (k = 2)", "train": n_train, "held_out": n_held, "batch_rhs": batch,
            "pod_modes": ws.n_pod, "mlp": "3 -> 4 x 512 GELU -> 512, BF16 tensor-core products", "epochs": epochs,
+           "inner_tol": 1e-6,
            "t_training_solves_s": t_data, "t_pod_s": ws.t_pod, "t_train_s": ws.t_train,
            "guess_rel_err_median": float(np.median(gerr)), "guess_rel_err_max": float(gerr.max()),
            "fp64_gpu_zero_guess": run(0, 3e-8, False, 0),

@@ -99,13 +99,16 @@ typedef struct {
     double gmres_tol;      /* relative residual of the preconditioned system */
     int restart;           /* GMRES restart length (<= 0: no restart, up to maxit) */
     int maxit;             /* total GMRES iterations (inner iterations in mixed mode) */
-    double inner_tol;      /* mixed mode: relative tolerance of each inner FP32 solve */
+    double inner_tol;      /* mixed mode: relative tolerance of each inner FP32 solve; with a
+                              guess x0, the first inner solve stops at inner_tol * |b| (absolute)
+                              instead, since it starts from the FP32 operator's residual */
     int max_outer;         /* mixed mode: maximum refinement steps */
     int verify_final;      /* mixed mode: 1 (default) = stop only on a computed FP64 residual;
                               0 = after an FP64 residual r_k, stop once the bound
                               rel_k * max(c_1, inner_tol) * 10 <= gmres_tol holds for the next
                               correction (c_1: contraction observed in the first refinement
-                              step), saving the last FP64 apply */
+                              step; from a guess, the first step's residual rel_1 itself),
+                              saving the last FP64 apply */
     int residual;          /* mixed mode: precision of the refinement residual's inter-body sum,
                               HZB_PREC_FP64 (default) or HZB_PREC_DOUBLE_FLOAT */
 } hzb_options;

@@ -607,18 +607,35 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
         double worst = *std::max_element(rel.begin(), rel.end());
         conv = worst <= c->opt.gmres_tol;
         double c1 = -1.0;            // contraction observed in the first refinement step
+        // From a guess, the first correction solves with the FP32 operator's residual and
+        // lands on the FP32-operator solution whatever the tolerance, so reducing that
+        // residual below inner_tol * |b| buys nothing: in this step the inner tolerance is
+        // absolute (relative to b), and a good guess needs fewer inner iterations.  A guess
+        // whose FP32 residual is already below that level is better than any such
+        // correction would leave it: the step is skipped and refinement starts from the
+        // guess's high-precision residual.
+        bool guess_step = x0 != nullptr;
         while (!conv && outer < c->opt.max_outer && it < c->opt.maxit) {
             const double want = c->opt.verify_final ? 0.3 : 0.1;
             double tin = std::max(c->opt.inner_tol, want * c->opt.gmres_tol / std::max(worst, 1e-300));
+            bool skip = false;
+            if (guess_step) {
+                const double t_abs = c->opt.inner_tol / std::max(worst, 1e-300);
+                skip = t_abs >= 1.0;
+                tin = std::max(tin, t_abs);
+            }
             tin = std::min(tin, 0.5);
-            int iin = 0, cin = 0;
+            int iin = 0, cin = 1;
             double rin = 0.0;
-            st = gmres_solve(c, R, rbuf.ptr, dbuf.ptr, 1, HZB_PREC_MIXED_FP32, tin, c->opt.maxit - it,
-                             c->opt.restart, &iin, &rin, &cin);
-            if (st && st != HZB_ENOCONV) { cleanup(); return st; }
-            it += iin;
-            axpby_kernel<<<nblocks((long long)NR), 256, 0, c->stream>>>((long long)NR, 1.0, x, 1.0, dbuf.ptr, x);
-            c->launches++;
+            if (!skip) {
+                cin = 0;
+                st = gmres_solve(c, R, rbuf.ptr, dbuf.ptr, 1, HZB_PREC_MIXED_FP32, tin, c->opt.maxit - it,
+                                 c->opt.restart, &iin, &rin, &cin);
+                if (st && st != HZB_ENOCONV) { cleanup(); return st; }
+                it += iin;
+                axpby_kernel<<<nblocks((long long)NR), 256, 0, c->stream>>>((long long)NR, 1.0, x, 1.0, dbuf.ptr, x);
+                c->launches++;
+            }
             ++outer;
             if (!c->opt.verify_final && c1 >= 0.0) {
                 // the residual after this correction is bounded by worst * max(c1, tin);
@@ -633,7 +650,12 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
             if ((st = true_residual(c, R, bbuf.ptr, x, rbuf.ptr, rel))) { cleanup(); return st; }
             double nw = *std::max_element(rel.begin(), rel.end());
             if (!std::isfinite(nw)) { cleanup(); return fail(c, HZB_ENAN, "non-finite refinement residual"); }
-            if (c1 < 0.0) c1 = nw / std::max(worst, 1e-300);
+            // c1 bounds the contraction of later steps by where the FP32 operator's solution
+            // lands: from zero that is nw / 1; after a guess's first step, which aimed at the
+            // absolute level inner_tol * |b|, it is nw itself, not nw over the guess's FP32
+            // residual.  A skipped step observes no contraction: the next one sets c1.
+            if (c1 < 0.0 && !skip) c1 = guess_step ? nw : nw / std::max(worst, 1e-300);
+            guess_step = false;
             worst = nw;
             conv = worst <= c->opt.gmres_tol;
         }

@@ -411,7 +411,7 @@ hzb_status interbody_df(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
     if (c->nbody64_engine == 2 && R <= 4) return interbody_df_sym(c, R, sigma, y);
     if (c->nbody64_engine == 1 || (c->nbody64_engine < 0 && R <= 4)) return interbody_dfl_sym(c, R, sigma, y);
     if (c->nbody64_engine != 2) {
-        const int ns = c->tunedf_split > 0 ? c->tunedf_split : default_nsplit(c, R, 1);
+        const int ns = c->tunedf_split > 0 ? c->tunedf_split : dfl_default_nsplit(c, R);
         return interbody_dfl(c, R, sigma, y, ns);
     }
     const int N = (int)c->N;

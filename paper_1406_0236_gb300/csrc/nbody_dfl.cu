@@ -277,30 +277,36 @@ nbody_dfl_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restri
 }
 
 // One-directional form for several right-hand sides (the refinement residual of a
-// batched solve): one CTA per (TargetBlock, chunk of RC right-hand sides, source chunk),
-// thread t owns target t of the block; sources in tiles of DFL_OT staged in shared memory.
-// Per ordered pair the geometry, e^{ikr} and the kernel value
+// batched solve): one CTA per (TargetBlock part, chunk of RC right-hand sides, source
+// chunk); a CTA of NT threads owns NT targets of a 512-target block (512 / NT CTAs per
+// block), one per thread; sources in tiles of DFL_OT staged in shared memory.  Per
+// ordered pair the geometry, e^{ikr} and the kernel value
 //     G = E [X - i (k r X + eta)],  E = e^{ikr} / r,  X = n_j.d / r^2
 // are formed once and serve the RC right-hand sides (a double-float complex
-// multiply-add each).  Source chunks write partial sums that a second kernel adds in a
+// multiply-add each, ~48 FP32 operations against ~240 for the pair), so wide chunks
+// (RC = 16 with 512 threads, RC = 32 with 256 threads and up to 255 registers) repeat
+// the pair work least.  Source chunks write partial sums that a second kernel adds in a
 // fixed order, so the result is bit-reproducible.
 static const int DFL_OT = 64;
 
-template <int RC>
-__global__ void __launch_bounds__(512, 1)
+template <int RC, int NT>
+__global__ void __launch_bounds__(NT, 1)
 nbody_dfl_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pa,
                  const float4 *__restrict__ pb, const float4 *__restrict__ pc, const double4 *__restrict__ pos64,
                  const double2 *__restrict__ sigma, const float4 *__restrict__ tab, DflConst K,
                  double2 *__restrict__ y, size_t split_stride)
 {
-    __shared__ float4 s_a[DFL_OT], s_b[DFL_OT], s_c[DFL_OT];
-    __shared__ float4 s_sig[DFL_OT][RC];
+    constexpr int PARTS = DFL_T / NT;
+    constexpr int OT = RC >= 32 ? DFL_OT / 2 : DFL_OT;   // source tile: static shared memory under 48 KB
+    __shared__ float4 s_a[OT], s_b[OT], s_c[OT];
+    __shared__ float4 s_sig[OT][RC];
     __shared__ float4 s_tab[DFL_TAB];
-    const TargetBlock tb = blocks[blockIdx.x];
+    const TargetBlock tb = blocks[blockIdx.x / PARTS];
+    const int t0 = (blockIdx.x % PARTS) * NT;
     const int r0 = blockIdx.y * RC;
     const int tid = threadIdx.x;
-    for (int q = tid; q < DFL_TAB; q += blockDim.x) s_tab[q] = tab[q];
-    const int g0 = tb.start + min(tid, tb.count - 1);
+    for (int q = tid; q < DFL_TAB; q += NT) s_tab[q] = tab[q];
+    const int g0 = tb.start + min(t0 + tid, tb.count - 1);
     const float4 TA = pa[g0], TB = pb[g0];
     const dd tx = {TA.x, TB.x}, ty = {TA.y, TB.y}, tz = {TA.z, TB.z};
     dd ar[RC], ai[RC];
@@ -310,10 +316,10 @@ nbody_dfl_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
     for (int range = 0; range < 2; ++range) {
         const int lo = range ? max(c0, tb.excl_hi) : c0;
         const int hi = range ? c1 : min(c1, tb.excl_lo);
-        for (int j0 = lo; j0 < hi; j0 += DFL_OT) {
-            const int cnt = min(DFL_OT, hi - j0);
+        for (int j0 = lo; j0 < hi; j0 += OT) {
+            const int cnt = min(OT, hi - j0);
             __syncthreads();
-            for (int q = tid; q < cnt; q += blockDim.x) {
+            for (int q = tid; q < cnt; q += NT) {
                 const int g = j0 + q;
                 s_a[q] = pa[g];
                 s_b[q] = pb[g];
@@ -367,12 +373,12 @@ nbody_dfl_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
             for (int c = 0; c < RC; ++c) { ar[c] = norm(ar[c]); ai[c] = norm(ai[c]); }
         }
     }
-    if (tid < tb.count) {
+    if (t0 + tid < tb.count) {
         double2 *yo = y + blockIdx.z * split_stride;
 #pragma unroll
         for (int c = 0; c < RC; ++c)
             if (r0 + c < R)
-                yo[(size_t)(tb.start + tid) * R + r0 + c] =
+                yo[(size_t)(tb.start + t0 + tid) * R + r0 + c] =
                     make_double2((double)ar[c].h + (double)ar[c].l, (double)ai[c].h + (double)ai[c].l);
     }
 }
@@ -427,14 +433,30 @@ static DflConst dfl_constants(const hzb_ctx *c)
     return K;
 }
 
-// one-directional lean double-float sum (R right-hand sides in chunks of 1, 4 or 8, source
-// chunks for occupancy, added in a fixed order); node arrays as for the symmetric form
+// right-hand sides per CTA of the one-directional kernel
+int dfl_rc(int R) { return R == 1 ? 1 : (R <= 4 ? 4 : (R <= 8 ? 8 : (R <= 16 ? 16 : 32))); }
+
+// source chunks of the one-directional kernel: about four CTAs per SM in all (one is
+// resident at a time: 512 threads at <= 128 registers, or 256 at <= 255)
+int dfl_default_nsplit(hzb_ctx *c, int R)
+{
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
+    const int rc = dfl_rc(R), nt = rc == 32 ? 256 : 512;
+    const long long ctas = (long long)c->n_tblocks * (DFL_T / nt) * ((R + rc - 1) / rc);
+    const long long ns = (4LL * sms + ctas - 1) / ctas;
+    return (int)std::min<long long>(64, std::max<long long>(1, ns));
+}
+
+// one-directional lean double-float sum (R right-hand sides in chunks of 1, 4, 8, 16 or
+// 32, source chunks for occupancy, added in a fixed order); node arrays as for the
+// symmetric form
 hzb_status interbody_dfl(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit)
 {
     hzb_status st = ensure_dfl_table(c);
     if (st) return st;
     const int N = (int)c->N;
-    const int rc = R == 1 ? 1 : (R <= 4 ? 4 : 8);
+    const int rc = dfl_rc(R);
     int chunk = (N + nsplit - 1) / nsplit;
     chunk = ((chunk + DFL_OT - 1) / DFL_OT) * DFL_OT;
     nsplit = (N + chunk - 1) / chunk;
@@ -450,17 +472,19 @@ hzb_status interbody_dfl(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
     const int slot = prof_begin(c, 2);
     const int nb = (c->tune_limit_blocks > 0) ? std::min(c->tune_limit_blocks, c->n_tblocks - c->tblock_off)
                                               : c->n_tblocks - c->tblock_off;
-    dim3 g(nb, (R + rc - 1) / rc, nsplit);
     const TargetBlock *tb = c->tblocks.ptr + c->tblock_off;
-    if (rc == 1)
-        nbody_dfl_kernel<1><<<g, 512, 0, c->stream>>>(tb, N, R, chunk, c->dfa.ptr, c->dfb.ptr, c->dfc.ptr, c->pos64.ptr,
-                                                      sigma, c->dfltab.ptr, K, out, n);
-    else if (rc == 4)
-        nbody_dfl_kernel<4><<<g, 512, 0, c->stream>>>(tb, N, R, chunk, c->dfa.ptr, c->dfb.ptr, c->dfc.ptr, c->pos64.ptr,
-                                                      sigma, c->dfltab.ptr, K, out, n);
-    else
-        nbody_dfl_kernel<8><<<g, 512, 0, c->stream>>>(tb, N, R, chunk, c->dfa.ptr, c->dfb.ptr, c->dfc.ptr, c->pos64.ptr,
-                                                      sigma, c->dfltab.ptr, K, out, n);
+    auto launch = [&](auto kern, int nt) {
+        dim3 g((unsigned)(nb * (DFL_T / nt)), (R + rc - 1) / rc, nsplit);
+        kern<<<g, nt, 0, c->stream>>>(tb, N, R, chunk, c->dfa.ptr, c->dfb.ptr, c->dfc.ptr, c->pos64.ptr, sigma,
+                                      c->dfltab.ptr, K, out, n);
+    };
+    switch (rc) {
+    case 1: launch(nbody_dfl_kernel<1, 512>, 512); break;
+    case 4: launch(nbody_dfl_kernel<4, 512>, 512); break;
+    case 8: launch(nbody_dfl_kernel<8, 512>, 512); break;
+    case 16: launch(nbody_dfl_kernel<16, 512>, 512); break;
+    default: launch(nbody_dfl_kernel<32, 256>, 256); break;
+    }
     if (nsplit > 1) dfl_split_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, nsplit, out, y);
     cudaError_t e = cudaGetLastError();
     prof_end(c, slot);

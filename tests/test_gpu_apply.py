@@ -159,11 +159,12 @@ def test_spheroids_258560_sampled_rows():
 
 
 @pytest.mark.parametrize("engine", [0, 1, 2])
-@pytest.mark.parametrize("R", [1, 3, 9])
+@pytest.mark.parametrize("R", [1, 3, 9, 17, 40])
 def test_interbody_double_float(pair, R, engine):
     """Double-float (two FP32 numbers) inter-body sum: FP64-class accuracy; the
-    one-directional (0), the pair-symmetric lean (1) and the pair-symmetric normalised
-    (2) kernel."""
+    one-directional (0; right-hand sides in chunks of 1, 4, 8, 16 and 32, the last with
+    two 256-thread CTAs per target block, ragged chunks at R = 17 and 40), the
+    pair-symmetric lean (1) and the pair-symmetric normalised (2) kernel."""
     s, P = pair
     sig = rand_c((P.N, R), 81 + R)
     s.set_fp64_interbody_engine(engine)

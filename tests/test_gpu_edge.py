@@ -31,7 +31,7 @@ def tiny():
 
 
 @pytest.mark.parametrize("engine", [0, 1])
-@pytest.mark.parametrize("R", [1, 3, 6])
+@pytest.mark.parametrize("R", [1, 3, 6, 20])
 def test_fp64_and_double_float_engines_on_tiny_bodies(tiny, R, engine):
     s, P = tiny
     sig = rand_c((P.N, R), 191 + R)

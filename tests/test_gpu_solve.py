@@ -138,6 +138,32 @@ def test_restarted_gmres_and_initial_guess():
     assert st3.converged and st3.iterations <= 1
 
 
+def test_mixed_refinement_from_a_guess():
+    """Mixed precision from a guess: the first correction solves with the FP32 operator's
+    residual and aims at the absolute level inner_tol |b|, so a guess 1e-3 off needs fewer
+    inner iterations than a zero start; a guess whose FP32 residual is already below that
+    level skips the FP32 step (no inner iteration) and keeps its accuracy; both end at the
+    zero-start answer."""
+    require_gpu()
+    from oracle import fields
+    wl = W.two_spheres(n_panels=6, gl_order=8, n_modes=21)
+    s = gpu_solver(wl, precision=1, tol=1e-10, inner_tol=1e-5)
+    x, _, _ = s.get_nodes()
+    v = fields.plane_wave(x, wl.directions, wl.k)
+    st0 = s.solve_data(v)
+    assert st0.converged
+    ref = s.get_density().copy()
+    g = np.random.default_rng(3)
+    noise = g.standard_normal(ref.shape) + 1j * g.standard_normal(ref.shape)
+    x0 = ref + 1e-3 * np.linalg.norm(ref) / np.linalg.norm(noise) * noise
+    st1 = s.solve_data(v, x0=x0)
+    assert st1.converged and st1.iterations < st0.iterations
+    assert rel_l2(s.get_density(), ref) < 1e-8
+    st2 = s.solve_data(v, x0=ref)
+    assert st2.converged and st2.iterations == 0
+    assert rel_l2(s.get_density(), ref) < 1e-12
+
+
 def test_error_statuses():
     require_gpu()
     from paper_1406_0236_gb300 import HzbError, Solver
