@@ -109,8 +109,9 @@ typedef struct {
                               correction (c_1: contraction observed in the first refinement
                               step; from a guess, the first step's residual rel_1 itself),
                               saving the last FP64 apply */
-    int residual;          /* mixed mode: precision of the refinement residual's inter-body sum,
-                              HZB_PREC_FP64 (default) or HZB_PREC_DOUBLE_FLOAT */
+    int residual;          /* mixed mode: precision of the refinement residual (its inter-body
+                              sum and D^{-1}, and b = -D^{-1} v), HZB_PREC_FP64 (default) or
+                              HZB_PREC_DOUBLE_FLOAT */
 } hzb_options;
 
 typedef struct {
@@ -319,7 +320,10 @@ hzb_status hzb_interbody_bodies(hzb_ctx *ctx, int R, const double *sigma, int bo
 
 /* tau = alpha * sigma + beta * D^{-1} y (the per-body FFT -> S_p -> inverse FFT of
  * the Remark after Eq. (precond)).  sigma may be NULL when alpha = 0.  Always the
- * direct D^{-1} on all N nodes, also while the accelerated scheme is on. */
+ * direct D^{-1} on all N nodes, also while the accelerated scheme is on.  precision:
+ * HZB_PREC_FP64, HZB_PREC_MIXED_FP32 (DFTs and GEMMs in FP32) or HZB_PREC_DOUBLE_FLOAT
+ * (DFTs and GEMMs in double-float on the FP32 pipe, about 1e-13 relative; the first
+ * such call after a build splits the scattering matrices into a cached copy). */
 hzb_status hzb_local_inverse(hzb_ctx *ctx, int R, const double *y, const double *sigma,
                              double alpha, double beta, double *tau, int on_device,
                              int precision);

@@ -22,11 +22,11 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr", "-I", INCLUDE]
 
 SOURCES = ["api.cpp", "geometry.cpp", "setup.cu", "nbody.cu", "modal.cu", "krylov.cu", "mlp.cu", "noalloc.cu",
-           "nbody_df.cu", "nbody_tc.cu", "nbody_sym.cu", "nbody_tc5.cu", "persist.cu", "modal_tma.cu", "compress.cu", "nbody_dfl.cu", "peaks.cu", "pod.cu"]
+           "nbody_df.cu", "nbody_tc.cu", "nbody_sym.cu", "nbody_tc5.cu", "persist.cu", "modal_tma.cu", "compress.cu", "nbody_dfl.cu", "peaks.cu", "pod.cu", "modal_dfl.cu"]
 # double-float error-free transformations must not be contracted into fused multiply-adds
 # the FP32 inter-body kernel flushes denormals (irrelevant to its values, cheaper intrinsics)
 PER_FILE = {"nbody_df.cu": ["-fmad=false"], "nbody_dfl.cu": ["-fmad=false"], "nbody.cu": ["-ftz=true"], "nbody_tc.cu": ["-ftz=true"], "nbody_sym.cu": ["-ftz=true"], "nbody_tc5.cu": ["-ftz=true"]}
-HEADERS = ["hzb_internal.h", "curve.h", "kernel_math.cuh", "dfloat.cuh"]
+HEADERS = ["hzb_internal.h", "curve.h", "kernel_math.cuh", "dfloat.cuh", "lean_df.cuh"]
 
 
 def nvcc() -> str:

@@ -130,6 +130,7 @@ hzb_status hzb_destroy(hzb_ctx *c)
     release_compression(c);
     for (ShapeDev *s : c->shapes) {
         s->ring.release(); s->body_offs.release(); s->A64.release(); s->S64.release(); s->S32.release();
+        s->Sdd.release();
         s->Aimg.release();
         delete s;
     }
@@ -434,8 +435,9 @@ hzb_status hzb_local_inverse(hzb_ctx *c, int R, const double *y, const double *s
         if (check_cuda(c, c->io_out.ensure(n), "alloc")) return HZB_ENOMEM;
         out = c->io_out.ptr;
     }
-    st = (precision == HZB_PREC_MIXED_FP32) ? local_inverse32(c, R, dy, ds, alpha, beta, out)
-                                            : local_inverse64(c, R, dy, ds, alpha, beta, out);
+    st = (precision == HZB_PREC_MIXED_FP32)     ? local_inverse32(c, R, dy, ds, alpha, beta, out)
+         : (precision == HZB_PREC_DOUBLE_FLOAT) ? local_inverse_dfl(c, R, dy, ds, alpha, beta, out)
+                                                : local_inverse64(c, R, dy, ds, alpha, beta, out);
     if (st) return st;
     return finish_out(c, out, tau, n, on_device);
 }

@@ -95,6 +95,8 @@ struct ShapeDev {
     DevBuf<double2> A64;                  // (M+1) x NG x NG: A~_p
     DevBuf<double2> S64;                  // (M+1) x NG x NG: S_p = A~_p^{-1}
     DevBuf<float2> S32;                   // FP32 copy of S64
+    DevBuf<float4> Sdd;                   // S64 split into double-float (re.hi, re.lo, im.hi, im.lo), on first use
+    bool Sdd_ready = false;               // cleared whenever S64 is rewritten
     DevBuf<float> Aimg;                   // embedded, TF32-split S_p for the TMA modal GEMM (modal_tma.cu)
     alignas(64) unsigned char tmA[128];   // its TMA tensor map (CUtensorMap)
     bool tmA_ready = false;
@@ -298,6 +300,9 @@ hzb_status local_inverse64(hzb_ctx *c, int R, const double2 *y, const double2 *s
                            double alpha, double beta, double2 *tau);
 hzb_status local_inverse32(hzb_ctx *c, int R, const double2 *y, const double2 *sigma,
                            double alpha, double beta, double2 *tau);
+// the same in double-float on the FP32 pipe (modal_dfl.cu), for the refinement residual
+hzb_status local_inverse_dfl(hzb_ctx *c, int R, const double2 *y, const double2 *sigma, double alpha, double beta,
+                             double2 *tau);
 
 // krylov.cu
 hzb_status apply_op(hzb_ctx *c, int R, const double2 *x, double2 *z, int precision);

@@ -7,9 +7,10 @@
 // residual estimates per iteration.  The paper stops at a residual of 1e-9 and does
 // not state restart or orthogonalisation; zero initial guess unless one is given.
 //
-// Mixed precision (FP64 outer refinement): r = b - A x with the FP64 operator,
-// an inner GMRES on A d = r whose operator applies run the FP32 inter-body sum and
-// FP32 modal GEMMs (Arnoldi and least squares stay FP64), x += d, repeat.
+// Mixed precision (FP64 outer refinement): r = b - A x with the FP64 operator (or its
+// double-float form on the FP32 pipe), an inner GMRES on A d = r whose operator
+// applies run the FP32 inter-body sum and FP32 modal GEMMs (Arnoldi and least squares
+// stay FP64), x += d, repeat.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -258,7 +259,7 @@ hzb_status apply_op(hzb_ctx *c, int R, const double2 *x, double2 *z, int precisi
     }
     if (precision == HZB_PREC_DOUBLE_FLOAT) {
         if ((st = interbody_df(c, R, x, c->w_c.ptr))) return st;
-        return local_inverse64(c, R, c->w_c.ptr, x, 1.0, 1.0, z);
+        return local_inverse_dfl(c, R, c->w_c.ptr, x, 1.0, 1.0, z);
     }
     if ((st = interbody64(c, R, x, c->w_c.ptr))) return st;
     return local_inverse64(c, R, c->w_c.ptr, x, 1.0, 1.0, z);
@@ -564,7 +565,9 @@ hzb_status solve_driver(hzb_ctx *c, int R, const double2 *v, const double2 *x0, 
     // b = -D^{-1} v, unless given
     if (b_given) {
         if ((st = vec_copy(c, bbuf.ptr, b_given, NR))) { cleanup(); return st; }
-    } else if ((st = local_inverse64(c, R, v, nullptr, 0.0, -1.0, bbuf.ptr))) {
+    } else if ((st = (c->opt.precision != HZB_PREC_FP64 && c->opt.residual == HZB_PREC_DOUBLE_FLOAT)
+                         ? local_inverse_dfl(c, R, v, nullptr, 0.0, -1.0, bbuf.ptr)
+                         : local_inverse64(c, R, v, nullptr, 0.0, -1.0, bbuf.ptr))) {
         cleanup();
         return st;
     }

@@ -11,11 +11,8 @@
 //     w_i K(x_j, x_i) sigma_i / (4 pi) ... = E [X_2 - i (k r X_2 + eta)] sigma'_i,  X_2 = -n_i.d / r^2,
 // sigma' = w sigma / (4 pi); E, r and k r are shared by the two directions.
 //
-// Arithmetic.  A value is hi + lo (two floats).  Products and sums are the error-free
-// transformations of Dekker (two_prod by a fused multiply-add) and Knuth (two_sum),
-// but the result is left unnormalised (lo may reach a few ulps of hi instead of half
-// an ulp), which saves the renormalising fast_two_sum of every operation; accumulators
-// are renormalised once per tile.  1/r: the hardware estimate of 1/sqrt(r^2) and one
+// Arithmetic: lean double-float (lean_df.cuh): error-free products and sums left
+// unnormalised, accumulators renormalised once per tile.  1/r: the hardware estimate of 1/sqrt(r^2) and one
 // Halley step (cubic convergence, so the estimate's 2^-23 error falls below 2^-60).
 // e^{i k r}: k r / (2 pi) in turns is reduced to [-1/2, 1/2] and then to the nearest of
 // 1024 table angles (cos, sin in double-float, shared memory); the remainder
@@ -28,54 +25,11 @@
 #include <vector>
 
 #include "hzb_internal.h"
+#include "lean_df.cuh"
 
 namespace hzb {
 
-namespace {
-
-struct dd {
-    float h, l;
-};
-
-__device__ __forceinline__ dd two_sum(float a, float b)
-{
-    const float s = a + b;
-    const float bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-
-// unnormalised double-float product: the exact product of the high parts plus the cross terms
-__device__ __forceinline__ dd mul(dd a, dd b)
-{
-    const float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, e);
-    e = fmaf(a.l, b.h, e);
-    return {p, e};
-}
-
-__device__ __forceinline__ dd add(dd a, dd b)
-{
-    const dd s = two_sum(a.h, b.h);
-    return {s.h, s.l + (a.l + b.l)};
-}
-
-__device__ __forceinline__ dd sub(dd a, dd b)
-{
-    const dd s = two_sum(a.h, -b.h);
-    return {s.h, s.l + (a.l - b.l)};
-}
-
-__device__ __forceinline__ dd neg(dd a) { return {-a.h, -a.l}; }
-
-// renormalise (|lo| <= ulp(hi) / 2 again)
-__device__ __forceinline__ dd norm(dd a)
-{
-    const float s = a.h + a.l;
-    return {s, a.l - (s - a.h)};
-}
-
-}  // namespace
+using namespace lean;
 
 static const int DFL_T = 512;          // targets per CTA (= TargetBlock size)
 static const int DFL_S = 32;           // sources per tile (one per lane)

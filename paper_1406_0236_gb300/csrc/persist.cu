@@ -189,6 +189,7 @@ extern "C" hzb_status hzb_load_scattering(hzb_ctx *c, const char *path)
         }
         to_fp32_copy_kernel<<<(unsigned)((nmat + 255) / 256), 256, 0, c->stream>>>(nmat, sd.S64.ptr, sd.S32.ptr);
         sd.tmA_ready = false;
+        sd.Sdd_ready = false;
         if (check_cuda(c, cudaGetLastError(), "to_fp32_copy_kernel")) {
             std::fclose(f);
             return HZB_ECUDA;

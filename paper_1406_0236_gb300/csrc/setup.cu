@@ -740,6 +740,7 @@ hzb_status build_shape_matrices(hzb_ctx *c, ShapeDev &sd)
     }
     gj_colswap_kernel<<<M1, 256, 0, c->stream>>>(NG, sd.S64.ptr, d_perm.ptr);
     to_fp32_kernel<<<(unsigned)((nmat + 255) / 256), 256, 0, c->stream>>>(nmat, sd.S64.ptr, sd.S32.ptr);
+    sd.Sdd_ready = false;
     if (check_cuda(c, cudaGetLastError(), "gauss-jordan")) { cleanup(); return HZB_ECUDA; }
     std::vector<int> sing(M1, 0);
     if (check_cuda(c, cudaMemcpyAsync(sing.data(), d_sing.ptr, M1 * sizeof(int), cudaMemcpyDeviceToHost, c->stream),

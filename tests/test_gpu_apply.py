@@ -99,7 +99,7 @@ def test_local_inverse_tensor_cores(pair, R, engine):
     assert rel_l2(got, ref) < 1e-5
 
 
-@pytest.mark.parametrize("R", [1, 4])
+@pytest.mark.parametrize("R", [1, 4, 24])
 def test_local_inverse(pair, R):
     s, P = pair
     y = rand_c((P.N, R), 31 + R)
@@ -109,6 +109,10 @@ def test_local_inverse(pair, R):
     assert rel_l2(got, ref) < 1e-11
     got32 = s.local_inverse(y, sig, alpha=0.5, beta=-2.0, precision=1)
     assert rel_l2(got32, ref) < 1e-5
+    # double-float DFTs and mode GEMMs on the FP32 pipe: the FP64 bar
+    gotdf = s.local_inverse(y, sig, alpha=0.5, beta=-2.0, precision=2)
+    assert rel_l2(gotdf, ref) < 1e-11
+    assert np.abs(gotdf - ref).max() < 1e-11 * np.abs(ref).max()
 
 
 def test_apply_fp64(pair):

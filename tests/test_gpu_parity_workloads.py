@@ -51,6 +51,9 @@ def test_spheroids8_local_inverse_against_oracle(spheroids8):
     assert rel_l2(got, ref) <= 1e-11
     rows = np.random.default_rng(802).choice(P.N, 2048, replace=False)
     assert np.abs(got[rows] - ref[rows]).max() <= 1e-11 * np.abs(ref).max()
+    gotdf = s.local_inverse(y, precision=2)              # double-float, the refinement residual's D^{-1}
+    assert rel_l2(gotdf, ref) <= 1e-11
+    assert np.abs(gotdf[rows] - ref[rows]).max() <= 1e-11 * np.abs(ref).max()
 
 
 def test_spheroids8_green_identity_through_direct_mixed_solve():
