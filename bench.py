@@ -11,7 +11,8 @@ sigma + D^{-1} B sigma, density in HBM), i.e. every step of the hot path; the
 setup (scattering matrices) is done once before timing.  The headline `value` is
 right-hand-side solves per second of the mixed-precision path (FP32 inter-body sum
 and modal GEMMs inside GMRES; refinement residual with its inter-body sum in
-double-float on the FP32 pipe, FP64 accumulation, D^{-1} and Arnoldi in FP64) stopped at
+double-float on the FP32 pipe with FP64 accumulation, D^{-1} in double-float, Arnoldi in
+FP64) stopped at
 a residual that gives a density error <= 1e-7 against an FP64-accurate reference
 (checked every run); `mixed_fp64_residual` is the same solve with the residual's sum on
 the FP64 pipe, `fp64_gpu` the plain FP64 GPU path on the same geometry.  Roofline
@@ -602,7 +603,7 @@ def main():
             "config": {"workload": WORKLOAD, "n_unknowns": N, "rhs_per_step_per_gpu": 1,
                        "precision": "FP32 inter-body sum and modal GEMMs inside GMRES; refinement residual: "
                                     "inter-body sum in double-float (pair kernels on the FP32 pipe, FP64 "
-                                    "accumulation into y), D^{-1} and Arnoldi in FP64",
+                                    "accumulation into y), D^{-1} in double-float, Arnoldi in FP64",
                        "tol_residual": TOL_MIXED, "density_err_vs_fp64_reference": dens_err,
                        "reference": "mixed refinement to %g with the FP64-pipe residual" % TOL_REF,
                        "l2": "flushed (512 MB write) between timed steps",

@@ -1337,9 +1337,11 @@ hzb_status solve_reduced(hzb_ctx *c, int R, const double2 *v, const double2 *x0,
     cudaEventRecord(c->ev0, c->stream);
     const long long l0 = c->launches, rl0 = r->launches;
     hzb_status st;
-    // v~ = T A^{-1} v per body; right-hand side -v~
-    if ((st = local_inverse64(c, R, v, nullptr, 0.0, 1.0, c->w_a.ptr))) return st;
+    // v~ = T A^{-1} v per body; right-hand side -v~.  The two direct D^{-1} applies run in
+    // double-float when the refinement residual does (mixed path), else in FP64.
     const bool df = c->opt.precision != HZB_PREC_FP64;
+    auto dinv = (df && c->opt.residual == HZB_PREC_DOUBLE_FLOAT) ? local_inverse_dfl : local_inverse64;
+    if ((st = dinv(c, R, v, nullptr, 0.0, 1.0, c->w_a.ptr))) return st;
     if ((st = restrict_all(c, R, c->w_a.ptr, -1.0, c->rb.ptr, df))) return st;
     if (x0 && (st = restrict_all(c, R, x0, 1.0, c->rx.ptr, df))) return st;
     hzb_stats rs{};
@@ -1370,7 +1372,7 @@ hzb_status solve_reduced(hzb_ctx *c, int R, const double2 *v, const double2 *x0,
         c->launches++;
     }
     if (check_cuda(c, cudaGetLastError(), "extend")) return HZB_ECUDA;
-    if ((st = local_inverse64(c, R, c->w_b.ptr, nullptr, 0.0, 1.0, c->sol.ptr))) return st;
+    if ((st = dinv(c, R, c->w_b.ptr, nullptr, 0.0, 1.0, c->sol.ptr))) return st;
     c->sol_R = R;
     cudaEventRecord(c->ev1, c->stream);
     if (check_cuda(c, cudaEventSynchronize(c->ev1), "reduced solve")) return HZB_ECUDA;
