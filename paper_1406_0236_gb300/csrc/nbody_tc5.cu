@@ -41,12 +41,12 @@ static const int T5_B_BYTES = 64 * T5_K * 4;            // one B operand tile (8
 static const int T5_SMEM = 4 * T5_A_BYTES + 4 * T5_B_BYTES + 1024 + 1024;   // + source tile, alignment
 static const int T5_STAGE = 4 * T5_A_BYTES + 4 * T5_B_BYTES;              // one operand stage (96 KB)
 
-// Pair kernels of one target and two sources (packed f32x2), phase reduced to a fraction
-// of a turn (1.5 * 2^23 rounding constant, valid while k r / (2 pi) < 2^22).
+// Pair kernels of one target and two sources (packed f32x2); e^{ikr} straight from the
+// transcendental unit, which scales its argument to turns itself (that rounding is the
+// one an explicit reduction to a fraction of a turn would make).
 __device__ __forceinline__ void t5_pair2(f2x tx, f2x ty, f2x tz, f2x sx, f2x sy, f2x sz, f2x nx, f2x ny, f2x nz,
-                                         f2x k2, f2x eta2, f2x kt2, f2x &gre, f2x &gim)
+                                         f2x k2, f2x eta2, f2x &gre, f2x &gim)
 {
-    const f2x rnd2 = f2_splat(12582912.0f), twopi2 = f2_splat(6.283185307179586f);
     const f2x dx = f2_sub(tx, sx), dy = f2_sub(ty, sy), dz = f2_sub(tz, sz);
     const f2x r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
     float ra, rb;
@@ -54,10 +54,9 @@ __device__ __forceinline__ void t5_pair2(f2x tx, f2x ty, f2x tz, f2x sx, f2x sy,
     const f2x ir = f2_pack(rsqrtf(ra), rsqrtf(rb));
     const f2x X = f2_mul(f2_fma(nx, dx, f2_fma(ny, dy, f2_mul(nz, dz))), f2_mul(ir, ir));
     const f2x A = f2_mul(X, ir), B = f2_fma(k2, X, f2_mul(eta2, ir));
-    const f2x t = f2_mul(f2_mul(r2, ir), kt2);
-    const f2x th = f2_mul(f2_sub(t, f2_sub(f2_add(t, rnd2), rnd2)), twopi2);
+    const f2x kr = f2_mul(f2_mul(r2, ir), k2);
     float ta, tb, sa, ca, sb, cb;
-    f2_unpack(th, ta, tb);
+    f2_unpack(kr, ta, tb);
     __sincosf(ta, &sa, &ca);
     __sincosf(tb, &sb, &cb);
     const f2x s2 = f2_pack(sa, sb), c2 = f2_pack(ca, cb);
@@ -65,23 +64,24 @@ __device__ __forceinline__ void t5_pair2(f2x tx, f2x ty, f2x tz, f2x sx, f2x sy,
     gim = f2_sub(f2_mul(s2, A), f2_mul(c2, B));
 }
 
-// TF32 hi + lo split of a packed pair: hi rounded to TF32, lo = x - hi rounded to TF32.
+// TF32 hi + lo split of a packed pair: hi rounded to TF32, lo = x - hi rounded to TF32
+// (integer rounding, t5_tf32i).
 __device__ __forceinline__ void t5_split2(f2x x, uint32_t &h0, uint32_t &h1, uint32_t &l0, uint32_t &l1)
 {
     float a, b;
     f2_unpack(x, a, b);
-    h0 = t5_tf32(a);
-    h1 = t5_tf32(b);
+    h0 = t5_tf32i(a);
+    h1 = t5_tf32i(b);
     const f2x lo = f2_sub(x, f2_pack(__uint_as_float(h0), __uint_as_float(h1)));
     f2_unpack(lo, a, b);
-    l0 = t5_tf32(a);
-    l1 = t5_tf32(b);
+    l0 = t5_tf32i(a);
+    l1 = t5_tf32i(b);
 }
 
 template <int RC>
 __global__ void __launch_bounds__(T5_THREADS, 1)
 nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pos,
-                 const float4 *__restrict__ nrm, const float2 *__restrict__ sw, float k, float eta, float kt,
+                 const float4 *__restrict__ nrm, const float2 *__restrict__ sw, float k, float eta,
                  float2 *__restrict__ ypart, double2 *__restrict__ y, size_t split_stride, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char t5_smem_raw[];
@@ -109,7 +109,7 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
         const float4 p = pos[tb.start + sub * T5_M + row];
         tx = f2_splat(p.x); ty = f2_splat(p.y); tz = f2_splat(p.z);
     }
-    const f2x k2 = f2_splat(k), eta2 = f2_splat(eta), kt2 = f2_splat(kt);
+    const f2x k2 = f2_splat(k), eta2 = f2_splat(eta);
     // B-operand duty: right-hand side bn, sources 4 bc .. 4 bc + 3 (threads with bc < 8)
     const int bn = tid % RC, bc = tid / RC;
     const bool bduty = bc < T5_K / 4;
@@ -179,13 +179,13 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
         if (bduty) {   // B operands: rows bn (B1 = Re s', B2 = -Im s') and bn + RC (B1 = Im s', B2 = Re s')
             uint32_t h[4], l[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { h[q] = t5_tf32(bv[q].x); l[q] = t5_tf32(bv[q].x - __uint_as_float(h[q])); }
+            for (int q = 0; q < 4; ++q) { h[q] = t5_tf32i(bv[q].x); l[q] = t5_tf32i(bv[q].x - __uint_as_float(h[q])); }
             t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn, bc), h[0], h[1], h[2], h[3]);
             t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
             t5_st4(sB + 2 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
             t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { h[q] = t5_tf32(bv[q].y); l[q] = t5_tf32(bv[q].y - __uint_as_float(h[q])); }
+            for (int q = 0; q < 4; ++q) { h[q] = t5_tf32i(bv[q].y); l[q] = t5_tf32i(bv[q].y - __uint_as_float(h[q])); }
             t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
             t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
 #pragma unroll
@@ -207,7 +207,7 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
                 t5_pair2(tx, ty, tz, *reinterpret_cast<const f2x *>(&s_src[0][q]),
                          *reinterpret_cast<const f2x *>(&s_src[1][q]), *reinterpret_cast<const f2x *>(&s_src[2][q]),
                          *reinterpret_cast<const f2x *>(&s_src[3][q]), *reinterpret_cast<const f2x *>(&s_src[4][q]),
-                         *reinterpret_cast<const f2x *>(&s_src[5][q]), k2, eta2, kt2, gr, gi);
+                         *reinterpret_cast<const f2x *>(&s_src[5][q]), k2, eta2, gr, gi);
                 t5_split2(gr, rh[2 * p], rh[2 * p + 1], rl[2 * p], rl[2 * p + 1]);
                 t5_split2(gi, ih[2 * p], ih[2 * p + 1], il[2 * p], il[2 * p + 1]);
             }
@@ -323,7 +323,7 @@ __device__ __forceinline__ void ws_prod_sync()
 template <int RC>
 __global__ void __launch_bounds__(WS_THREADS, 1)
 nbody_tc5ws_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pos,
-                   const float4 *__restrict__ nrm, const float2 *__restrict__ sw, float k, float eta, float kt,
+                   const float4 *__restrict__ nrm, const float2 *__restrict__ sw, float k, float eta,
                    float2 *__restrict__ ypart, double2 *__restrict__ y, size_t split_stride, int *__restrict__ err)
 {
     constexpr int NC = 2 * RC;                         // accumulator columns: [Re y | Im y]
@@ -380,7 +380,7 @@ nbody_tc5ws_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chu
             const float4 p = pos[tb.start + sub * T5_M + row];
             tx = f2_splat(p.x); ty = f2_splat(p.y); tz = f2_splat(p.z);
         }
-        const f2x k2 = f2_splat(k), eta2 = f2_splat(eta), kt2 = f2_splat(kt);
+        const f2x k2 = f2_splat(k), eta2 = f2_splat(eta);
         const int bn = tid % RC, bc = tid / RC;
         const bool bduty = bc < T5_K / 4;
         const int rb = r0 + bn;
@@ -414,13 +414,13 @@ nbody_tc5ws_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chu
             if (bduty) {
                 uint32_t h[4], l[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) { h[q] = t5_tf32(bv[q].x); l[q] = t5_tf32(bv[q].x - __uint_as_float(h[q])); }
+                for (int q = 0; q < 4; ++q) { h[q] = t5_tf32i(bv[q].x); l[q] = t5_tf32i(bv[q].x - __uint_as_float(h[q])); }
                 t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn, bc), h[0], h[1], h[2], h[3]);
                 t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
                 t5_st4(sB + 2 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
                 t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) { h[q] = t5_tf32(bv[q].y); l[q] = t5_tf32(bv[q].y - __uint_as_float(h[q])); }
+                for (int q = 0; q < 4; ++q) { h[q] = t5_tf32i(bv[q].y); l[q] = t5_tf32i(bv[q].y - __uint_as_float(h[q])); }
                 t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
                 t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
 #pragma unroll
@@ -443,7 +443,7 @@ nbody_tc5ws_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chu
                              *reinterpret_cast<const f2x *>(&s_src[2][q]),
                              *reinterpret_cast<const f2x *>(&s_src[3][q]),
                              *reinterpret_cast<const f2x *>(&s_src[4][q]),
-                             *reinterpret_cast<const f2x *>(&s_src[5][q]), k2, eta2, kt2, gr, gi);
+                             *reinterpret_cast<const f2x *>(&s_src[5][q]), k2, eta2, gr, gi);
                     t5_split2(gr, rh[2 * p], rh[2 * p + 1], rl[2 * p], rl[2 * p + 1]);
                     t5_split2(gi, ih[2 * p], ih[2 * p + 1], il[2 * p], il[2 * p + 1]);
                 }
@@ -561,22 +561,22 @@ hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
     if (!sw) return HZB_ENOMEM;
     const int rc = (R <= 16) ? 16 : 32;
     dim3 grid(c->n_tblocks * 4, (R + rc - 1) / rc, nsplit);
-    const float k = (float)c->k, eta = (float)c->eta, kt = (float)(c->k / (2.0 * M_PI));
+    const float k = (float)c->k, eta = (float)c->eta;
     if (ws && rc == 16)
         nbody_tc5ws_kernel<16><<<grid, WS_THREADS, WS_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
-                                                                        c->nrm32.ptr, sw, k, eta, kt, part, y, n,
+                                                                        c->nrm32.ptr, sw, k, eta, part, y, n,
                                                                         c->kerr.ptr);
     else if (ws)
         nbody_tc5ws_kernel<32><<<grid, WS_THREADS, WS_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
-                                                                        c->nrm32.ptr, sw, k, eta, kt, part, y, n,
+                                                                        c->nrm32.ptr, sw, k, eta, part, y, n,
                                                                         c->kerr.ptr);
     else if (rc == 16)
         nbody_tc5_kernel<16><<<grid, T5_THREADS, T5_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
-                                                                      c->nrm32.ptr, sw, k, eta, kt, part, y, n,
+                                                                      c->nrm32.ptr, sw, k, eta, part, y, n,
                                                                       c->kerr.ptr);
     else
         nbody_tc5_kernel<32><<<grid, T5_THREADS, T5_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
-                                                                      c->nrm32.ptr, sw, k, eta, kt, part, y, n,
+                                                                      c->nrm32.ptr, sw, k, eta, part, y, n,
                                                                       c->kerr.ptr);
     if (nsplit > 1) split_reduce_f2(c, n, nsplit, part, y);
     cudaError_t e = cudaGetLastError();

@@ -16,6 +16,13 @@ __device__ __forceinline__ uint32_t t5_tf32(float x)
     return r;
 }
 
+// The same rounding (to nearest, ties away from zero, 10 stored mantissa bits) in two
+// integer operations on the bit pattern: add half of the 13 dropped bits' range and
+// clear them; equal to cvt.rna for every finite x (a NaN may come out as an infinity).
+// The conversion instruction has a fraction of the integer pipe's throughput, so the
+// hot loops that split every pair kernel use this form.
+__device__ __forceinline__ uint32_t t5_tf32i(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+
 // Byte offset of the 16-byte chunk c (4 TF32 values along K) of row `row` in a K-major
 // tile with 128-byte rows and the 128-byte swizzle: 8-row atoms of 1024 bytes, chunk
 // index XOR (row mod 8).
