@@ -270,6 +270,9 @@ hzb_status hzb_set_modal_engine(hzb_ctx *ctx, int engine);
  * three-term split, accumulators in tensor memory, 16 or 32 right-hand sides per CTA);
  * 6 = the same contraction as a warp-specialised pipeline (producer, MMA and epilogue
  * warps synchronised by mbarriers, two operand stages, two accumulators);
+ * 7 = engine 5 with single-term TF32 products (no hi/lo split: about 3e-4 relative
+ * error in the sum instead of ~3e-6, about 1.4x faster; only ever chosen here, never by
+ * the default or the autotuner, for inner solves whose refinement absorbs it);
  * -1 (default) = tcgen05 tensor cores when R >= 16, else as 0, unless hzb_autotune
  * timed the engines for this R.  Returns HZB_EINVAL for other values. */
 hzb_status hzb_set_interbody_engine(hzb_ctx *ctx, int engine);

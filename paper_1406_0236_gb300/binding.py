@@ -252,7 +252,8 @@ class Solver:
     def set_interbody_engine(self, engine: int):
         """FP32 inter-body sum engine: 0 CUDA cores, 1 tensor cores, 2 scalar CUDA-core kernel,
         3 packed-pair CUDA-core kernel, 4 pair-symmetric packed kernel, 5 tcgen05 tensor cores,
-        6 tcgen05 warp-specialised pipeline, -1 auto (tensor cores for R >= 16 or as tuned)."""
+        6 tcgen05 warp-specialised pipeline, 7 tcgen05 with single-term TF32 products (opt-in,
+        ~3e-4 relative error), -1 auto (tensor cores for R >= 16 or as tuned)."""
         self._check(lib().hzb_set_interbody_engine(self._h, int(engine)))
 
     def set_fp64_interbody_engine(self, engine: int):

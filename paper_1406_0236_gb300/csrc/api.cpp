@@ -608,7 +608,7 @@ hzb_status hzb_set_fp64_interbody_engine(hzb_ctx *c, int engine)
 hzb_status hzb_set_interbody_engine(hzb_ctx *c, int engine)
 {
     if (!c) return HZB_EINVAL;
-    if (engine < -1 || engine > 6) return fail(c, HZB_EINVAL, "engine in {-1, 0, ..., 6}");
+    if (engine < -1 || engine > 7) return fail(c, HZB_EINVAL, "engine in {-1, 0, ..., 7}");
     c->nbody_engine = engine;
     return HZB_OK;
 }

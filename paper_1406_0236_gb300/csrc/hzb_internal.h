@@ -279,8 +279,9 @@ hzb_status interbody_dfl(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
 int dfl_default_nsplit(hzb_ctx *c, int R);                                                  // nbody_dfl.cu
 hzb_status interbody_tc(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit);
 hzb_status modal_gemm_tma(hzb_ctx *c, ShapeDev &sd, int ncols, const float2 *X, float2 *Cout);  // modal_tma.cu
+enum { T5_SPLIT3 = 0, T5_WS = 1, T5_SINGLE = 2 };   // forms of the tcgen05 inter-body kernel
 hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit,
-                         bool ws);   // nbody_tc5.cu; ws: warp-specialised form
+                         int mode);  // nbody_tc5.cu
 const float2 *weighted_sigma32(hzb_ctx *c, int R, const double2 *sigma);      // nbody.cu; nullptr on failure
 hzb_status ensure_sctab(hzb_ctx *c);                                          // nbody.cu: FP64 cos/sin table
 hzb_status interbody64_sym(hzb_ctx *c, int R, const double2 *sigma, double2 *y);  // nbody_sym.cu

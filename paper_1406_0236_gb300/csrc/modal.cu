@@ -354,11 +354,9 @@ namespace hzb {
 // A B ~ Ahi Bhi + Ahi Blo + Alo Bhi, FP32 accumulation (about FP32 accuracy).
 // mma.sync m16n8k8; 64 x 64 output tile per CTA, 4 warps of 32 x 32, K step 32.
 
-__device__ __forceinline__ uint32_t to_tf32(float x)
+__device__ __forceinline__ uint32_t to_tf32(float x)       // = cvt.rna.tf32.f32 for finite x
 {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
 __device__ __forceinline__ void mma_tf32(float *d, const uint32_t *a, const uint32_t *b)

@@ -39,8 +39,8 @@ static inline int kpitch(int n) { return (2 * n + 3) & ~3; }
 
 __device__ __forceinline__ void mt_split(double a, float &hi, float &lo)
 {
-    hi = __uint_as_float(t5_tf32((float)a));
-    lo = __uint_as_float(t5_tf32((float)(a - (double)hi)));
+    hi = __uint_as_float(t5_tf32i((float)a));
+    lo = __uint_as_float(t5_tf32i((float)(a - (double)hi)));
 }
 
 // plane (2p + h), row m, column k of the embedded, split S_p

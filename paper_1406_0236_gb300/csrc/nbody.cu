@@ -526,13 +526,17 @@ hzb_status interbody64(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 hzb_status interbody32(hzb_ctx *c, int R, const double2 *sigma, double2 *y)
 {
     // many right-hand sides: contraction on the tensor cores, tcgen05 (nbody_tc5.cu) or
-    // mma.sync (nbody_tc.cu); engine choice 0 CUDA cores, 1 mma.sync, 2 tcgen05
+    // mma.sync (nbody_tc.cu); engine choice 0 CUDA cores, 1 mma.sync, 2 tcgen05, 3 tcgen05
+    // warp-specialised, 4 tcgen05 with single-term TF32 products (opt-in only)
     int e = -1;
     if (c->nbody_engine == 1) e = 1;
     else if (c->nbody_engine == 5) e = 2;
     else if (c->nbody_engine == 6) e = 3;
+    else if (c->nbody_engine == 7) e = 4;
     else if (c->nbody_engine < 0) e = (c->tune32_tc >= 0 && c->tune32_tc_R == R) ? c->tune32_tc : (R >= 16 ? 2 : 0);
-    if (e == 2 || e == 3) return interbody_tc5(c, R, sigma, y, default_nsplit_tc5(c, R), e == 3);
+    if (e >= 2 && e <= 4)
+        return interbody_tc5(c, R, sigma, y, default_nsplit_tc5(c, R),
+                             e == 2 ? T5_SPLIT3 : (e == 3 ? T5_WS : T5_SINGLE));
     if (e == 1) {
         int ns = c->tunetc_split > 0 ? c->tunetc_split : default_nsplit_tc(c, R);
         return interbody_tc(c, R, sigma, y, ns);
@@ -775,11 +779,11 @@ hzb_status autotune(hzb_ctx *c, int R, int which, double *best_ms)
             }
             float t5 = 1e30f;
             {
-                if (interbody_tc5(c, R, c->io_in.ptr, c->io_out.ptr, default_nsplit_tc5(c, R), false))
+                if (interbody_tc5(c, R, c->io_in.ptr, c->io_out.ptr, default_nsplit_tc5(c, R), T5_SPLIT3))
                     return fail(c, HZB_ECUDA, "autotune launch failed");
                 cudaEventRecord(c->ev0, c->stream);
                 for (int q = 0; q < 3; ++q)
-                    if (interbody_tc5(c, R, c->io_in.ptr, c->io_out.ptr, default_nsplit_tc5(c, R), false))
+                    if (interbody_tc5(c, R, c->io_in.ptr, c->io_out.ptr, default_nsplit_tc5(c, R), T5_SPLIT3))
                         return fail(c, HZB_ECUDA, "autotune launch failed");
                 cudaEventRecord(c->ev1, c->stream);
                 if (cudaEventSynchronize(c->ev1) != cudaSuccess) return fail(c, HZB_ECUDA, "autotune launch failed");

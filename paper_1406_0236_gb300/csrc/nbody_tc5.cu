@@ -78,7 +78,7 @@ __device__ __forceinline__ void t5_split2(f2x x, uint32_t &h0, uint32_t &h1, uin
     l1 = t5_tf32i(b);
 }
 
-template <int RC>
+template <int RC, int TERMS>
 __global__ void __launch_bounds__(T5_THREADS, 1)
 nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk, const float4 *__restrict__ pos,
                  const float4 *__restrict__ nrm, const float2 *__restrict__ sw, float k, float eta,
@@ -181,17 +181,17 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
 #pragma unroll
             for (int q = 0; q < 4; ++q) { h[q] = t5_tf32i(bv[q].x); l[q] = t5_tf32i(bv[q].x - __uint_as_float(h[q])); }
             t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn, bc), h[0], h[1], h[2], h[3]);
-            t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
+            if (TERMS == 3) t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
             t5_st4(sB + 2 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
-            t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
+            if (TERMS == 3) t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
 #pragma unroll
             for (int q = 0; q < 4; ++q) { h[q] = t5_tf32i(bv[q].y); l[q] = t5_tf32i(bv[q].y - __uint_as_float(h[q])); }
             t5_st4(sB + 0 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), h[0], h[1], h[2], h[3]);
-            t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
+            if (TERMS == 3) t5_st4(sB + 1 * T5_B_BYTES + t5_chunk_off(bn + RC, bc), l[0], l[1], l[2], l[3]);
 #pragma unroll
             for (int q = 0; q < 4; ++q) { h[q] ^= 0x80000000u; l[q] ^= 0x80000000u; }
             t5_st4(sB + 2 * T5_B_BYTES + t5_chunk_off(bn, bc), h[0], h[1], h[2], h[3]);
-            t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
+            if (TERMS == 3) t5_st4(sB + 3 * T5_B_BYTES + t5_chunk_off(bn, bc), l[0], l[1], l[2], l[3]);
         }
         __syncthreads();                               // source tile staged
         if (it + 1 < ntile) prefetch(it + 1);          // overlaps the pair kernels and the MMAs
@@ -213,9 +213,9 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
             }
             const uint32_t off = t5_chunk_off(row, c);
             t5_st4(sA + 0 * T5_A_BYTES + off, rh[0], rh[1], rh[2], rh[3]);
-            t5_st4(sA + 1 * T5_A_BYTES + off, rl[0], rl[1], rl[2], rl[3]);
+            if (TERMS == 3) t5_st4(sA + 1 * T5_A_BYTES + off, rl[0], rl[1], rl[2], rl[3]);
             t5_st4(sA + 2 * T5_A_BYTES + off, ih[0], ih[1], ih[2], ih[3]);
-            t5_st4(sA + 3 * T5_A_BYTES + off, il[0], il[1], il[2], il[3]);
+            if (TERMS == 3) t5_st4(sA + 3 * T5_A_BYTES + off, il[0], il[1], il[2], il[3]);
         }
         // make the generic-proxy stores visible to the tensor cores, then issue
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -223,11 +223,13 @@ nbody_tc5_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // products: (A tile, B tile) = Re G x B1 and Im G x B2, each hi.hi, hi.lo, lo.hi
-            const int am[6] = {0, 0, 1, 2, 2, 3}, bm[6] = {0, 1, 0, 2, 3, 2};
+            // (TERMS = 3) or hi.hi alone (TERMS = 1: the first and fourth of these)
+            constexpr int NP = TERMS == 3 ? 6 : 2;
+            const int am[6] = {0, TERMS == 3 ? 0 : 2, 1, 2, 2, 3}, bm[6] = {0, TERMS == 3 ? 1 : 2, 0, 2, 3, 2};
 #pragma unroll
             for (int ks = 0; ks < T5_K / 8; ++ks)
 #pragma unroll
-                for (int p = 0; p < 6; ++p)
+                for (int p = 0; p < NP; ++p)
                     t5_mma(tmem, t5_desc(sA + am[p] * T5_A_BYTES + 32 * ks), t5_desc(sB + bm[p] * T5_B_BYTES + 32 * ks),
                            t5_idesc(NC), (ks | p) ? 1u : 0u);
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -516,8 +518,12 @@ nbody_tc5ws_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chu
     if (tid == 0 && s_abort) atomicExch(err, 1);
 }
 
-hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit, bool ws)
+// mode: T5_SPLIT3 (three-term TF32 split, FP32-level products), T5_WS (the same, warp-
+// specialised), T5_SINGLE (TF32 products alone: about 3e-4 relative error in the sum, 1.4x
+// faster; for inner solves whose refinement tolerates it)
+hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, int nsplit, int mode)
 {
+    const bool ws = mode == T5_WS;
     if (!c->nodes_ready) return fail(c, HZB_ESTATE, "nodes not built");
     const int N = (int)c->N;
     int chunk = (N + nsplit - 1) / nsplit;
@@ -538,9 +544,13 @@ hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
     static bool attr_done[64] = {false};
     const int dev = c->opt.device;
     if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        if (check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<16, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                T5_SMEM), "tcgen05 kernel shared memory") ||
-            check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<32, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               T5_SMEM), "tcgen05 kernel shared memory") ||
+            check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               T5_SMEM), "tcgen05 kernel shared memory") ||
+            check_cuda(c, cudaFuncSetAttribute(nbody_tc5_kernel<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                T5_SMEM), "tcgen05 kernel shared memory") ||
             check_cuda(c, cudaFuncSetAttribute(nbody_tc5ws_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                WS_SMEM), "tcgen05 kernel shared memory") ||
@@ -570,14 +580,15 @@ hzb_status interbody_tc5(hzb_ctx *c, int R, const double2 *sigma, double2 *y, in
         nbody_tc5ws_kernel<32><<<grid, WS_THREADS, WS_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
                                                                         c->nrm32.ptr, sw, k, eta, part, y, n,
                                                                         c->kerr.ptr);
-    else if (rc == 16)
-        nbody_tc5_kernel<16><<<grid, T5_THREADS, T5_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
-                                                                      c->nrm32.ptr, sw, k, eta, part, y, n,
-                                                                      c->kerr.ptr);
-    else
-        nbody_tc5_kernel<32><<<grid, T5_THREADS, T5_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr,
-                                                                      c->nrm32.ptr, sw, k, eta, part, y, n,
-                                                                      c->kerr.ptr);
+    else {
+        auto launch = [&](auto kern) {
+            kern<<<grid, T5_THREADS, T5_SMEM, c->stream>>>(c->tblocks.ptr, N, R, chunk, c->pos32.ptr, c->nrm32.ptr, sw,
+                                                           k, eta, part, y, n, c->kerr.ptr);
+        };
+        const bool single = mode == T5_SINGLE;
+        if (rc == 16) launch(single ? nbody_tc5_kernel<16, 1> : nbody_tc5_kernel<16, 3>);
+        else launch(single ? nbody_tc5_kernel<32, 1> : nbody_tc5_kernel<32, 3>);
+    }
     if (nsplit > 1) split_reduce_f2(c, n, nsplit, part, y);
     cudaError_t e = cudaGetLastError();
     prof_end(c, slot);

@@ -119,6 +119,8 @@ def test_apply_fp64(pair):
     s, P = pair
     sig = rand_c((P.N, 2), 51)
     assert rel_l2(s.apply(sig), P.apply(sig)) < 1e-11
+    # the refinement residual's operator: inter-body sum and D^{-1} in double-float
+    assert rel_l2(s.apply(sig, precision=2), P.apply(sig)) < 1e-11
 
 
 def test_device_tensors_round_trip(pair):
@@ -159,6 +161,9 @@ def test_spheroids_258560_sampled_rows():
         s.set_interbody_engine(engine)
         ytc = s.interbody(sig16, precision=1)
         assert rel_l2(ytc[rows], ref16) < 3e-5, engine
+    s.set_interbody_engine(7)            # single-term TF32 products: its own bar
+    ytc = s.interbody(sig16, precision=1)
+    assert rel_l2(ytc[rows], ref16) < 1e-3
     s.set_interbody_engine(-1)
 
 

@@ -61,6 +61,21 @@ def test_fp32_engines_on_tiny_bodies(tiny, R, engine):
     assert rel_l2(got, ref) < 5e-6
 
 
+@pytest.mark.parametrize("R", [5, 17])
+def test_single_term_tf32_engine_on_tiny_bodies(tiny, R):
+    """Engine 7: tcgen05 with TF32 products and no hi/lo split; its own bar, set by the
+    2^-11 rounding of both factors (measured ~3e-4 on the eight spheroids)."""
+    s, P = tiny
+    sig = rand_c((P.N, R), 211 + R)
+    ref = P.interbody(sig)
+    s.set_interbody_engine(7)
+    try:
+        got = s.interbody(sig, precision=1)
+    finally:
+        s.set_interbody_engine(-1)
+    assert rel_l2(got, ref) < 2e-3
+
+
 def test_solve_on_tiny_bodies(tiny):
     s, P = tiny
     from oracle import fields, gmres
@@ -78,7 +93,7 @@ def test_empty_requests_and_bad_selectors_are_refused(tiny):
     for call in (lambda: s.interbody(np.zeros((P.N, 0), complex)),
                  lambda: s.apply(np.zeros((P.N, 0), complex)),
                  lambda: s.solve_plane_waves(np.zeros((0, 3))),
-                 lambda: s.set_interbody_engine(7),
+                 lambda: s.set_interbody_engine(8),
                  lambda: s.set_interbody_engine(-2),
                  lambda: s.set_fp64_interbody_engine(3),
                  lambda: s.set_modal_engine(3)):

@@ -164,6 +164,25 @@ def test_mixed_refinement_from_a_guess():
     assert rel_l2(s.get_density(), ref) < 1e-12
 
 
+def test_mixed_solve_with_single_term_tf32_inner_sums():
+    """Inner FP32 solves on the single-term TF32 tensor-core engine (7) at R = 16: the
+    double-float refinement residual brings the densities to the mixed bar against the
+    FP64 solve."""
+    require_gpu()
+    wl = W.two_spheres(n_panels=6, gl_order=8, n_modes=21)
+    dirs = W.uniform_directions(16, 31)
+    s = gpu_solver(wl, tol=1e-12)
+    s.solve_plane_waves(dirs)
+    ref = s.get_density().copy()
+    m = gpu_solver(wl, precision=1, tol=1e-8, residual=2)
+    m.set_interbody_engine(7)
+    st = m.solve_plane_waves(dirs)
+    assert st.converged
+    got = m.get_density()
+    for r in range(16):
+        assert rel_l2(got[:, r], ref[:, r]) < 1e-7
+
+
 def test_error_statuses():
     require_gpu()
     from paper_1406_0236_gb300 import HzbError, Solver
