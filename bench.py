@@ -295,21 +295,25 @@ def mlp_leg(torch, local, n_train=4096, n_held=512, batch=64, epochs=1600):
     return res
 
 
-def cfg5_run(args, torch, local, clk_cls):
-    """The 48-body workload end to end (opt-in: --workload mixed48_shells): 16 spheres,
-    16 spheroids and 16 open shells on a jittered grid, k = 6, 24 x 16 x 121 nodes per
-    body (2,230,272 unknowns), 16 plane waves in one batch.  One timed mixed solve (FP32
-    inter-body sums on tcgen05 at R = 16 and FP32 modal GEMMs inside GMRES, the refinement
-    residual's sum in double-float), stopped at residual 1e-7; its density error against
-    the same system refined to 1e-10 (continued from the solution, residual computed);
-    Green's identity at 10 exterior targets from a separate solve with one interior point
-    source per body (in the wall for the shells)."""
+def batch_run(args, torch, local, clk_cls):
+    """A many-body, many-RHS workload end to end (opt-in):
+      --workload mixed48_shells: 16 spheres, 16 spheroids and 16 open shells on a jittered
+        grid, k = 6, 24 x 16 x 121 nodes per body (2,230,272 unknowns), 16 plane waves;
+      --workload mixed27: 27 uneven bodies (seeded spheres and spheroids, 12-24 panels x 16
+        GL nodes, 61-121 azimuthal nodes; 750,368 unknowns) on a 3 x 3 x 3 grid, k = 4, 64
+        plane waves.
+    One timed mixed solve of all right-hand sides in one batch (FP32 inter-body sums on
+    tcgen05 and FP32 modal GEMMs inside GMRES, the refinement residual in double-float),
+    stopped at residual 1e-7; its density error against the same system refined to 1e-10
+    (continued from the solution, residual computed); Green's identity at 10 exterior
+    targets from a separate solve with one interior point source per body (in the wall
+    for the shells)."""
     import numpy as np
 
     import workloads as W
     from paper_1406_0236_gb300 import HZB_PREC_DOUBLE_FLOAT, HZB_PREC_MIXED_FP32, Options, Solver
 
-    wl = W.mixed48()
+    wl = W.mixed48() if args.workload == "mixed48_shells" else W.mixed27()
     dirs = wl.directions
     opt = Options(device=local, precision=HZB_PREC_MIXED_FP32, gmres_tol=1e-7, inner_tol=1e-5, max_outer=6,
                   verify_final=0, residual=HZB_PREC_DOUBLE_FLOAT)
@@ -355,16 +359,16 @@ def cfg5_run(args, torch, local, clk_cls):
     line = {"metric": METRIC, "value": 1e3 * R / ms, "unit": "RHS solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+df64+f64", "data": "synthetic",
-            "config": {"workload": "mixed48_shells_2230272", "n_unknowns": N, "rhs_per_step": R, "k": wl.k,
-                       "precision": "FP32 inter-body sums (tcgen05, R = 16) and modal GEMMs inside GMRES; "
-                                    "refinement residual's inter-body sum in double-float",
+            "config": {"workload": "%s_%d" % (args.workload, N), "n_unknowns": N, "rhs_per_step": R, "k": wl.k,
+                       "precision": "FP32 inter-body sums (tcgen05, R = %d) and modal GEMMs inside GMRES; "
+                                    "refinement residual (inter-body sum and D^{-1}) in double-float" % R,
                        "tol_residual": 1e-7, "t_pre_s": t_pre,
                        "outer_iterations": st.outer_iterations, "inner_iterations": st.iterations,
                        "fp32_applies": st.n_nbody32, "df_residual_applies": st.n_nbodydf,
                        "nbody32_ms_per_launch": st.t_nbody32_ms / max(st.n_nbody32, 1),
                        "nbodydf_ms_per_launch": st.t_nbodydf_ms / max(st.n_nbodydf, 1),
                        "kernels": s.tuned_config(R),
-                       "l2": "inputs far larger than L2 (2.2 M nodes x 16 RHS)"},
+                       "l2": "inputs far larger than L2 (%d nodes x %d RHS)" % (N, R)},
             "density_err_vs_refined": {"max": float(derr.max()), "median": float(np.median(derr)),
                                        "reference": "same system, residual 1e-10 verified (%d more inner "
                                                     "iterations)" % st_ref.iterations},
@@ -400,8 +404,9 @@ def main():
     ap.add_argument("--accel-eps", type=float, default=1e-8,
                     help="ID tolerance of the accelerated-scheme solves (0 = skip them)")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned warm-start (+MLP) leg")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "mixed48_shells"],
-                    help="mixed48_shells: the 48-body, 2.2 M-unknown, 16-RHS solve end to end (opt-in, ~10 min)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "mixed48_shells", "mixed27"],
+                    help="mixed48_shells: the 48-body, 2.2 M-unknown, 16-RHS solve end to end (opt-in, ~20 min); "
+                         "mixed27: the 27-body, 750 k-unknown, 64-RHS solve end to end (opt-in)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -418,9 +423,9 @@ def main():
     from paper_1406_0236_gb300 import HZB_PREC_DOUBLE_FLOAT, HZB_PREC_FP64, HZB_PREC_MIXED_FP32, Options, Solver
 
     torch.cuda.set_device(local)
-    if args.workload == "mixed48_shells":
+    if args.workload in ("mixed48_shells", "mixed27"):
         if rank == 0:
-            print(json.dumps(cfg5_run(args, torch, local, ClockSampler)))
+            print(json.dumps(batch_run(args, torch, local, ClockSampler)))
         return
     dist = None
     if world > 1:
