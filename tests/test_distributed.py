@@ -7,6 +7,7 @@ import os
 import socket
 
 import numpy as np
+import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
@@ -69,17 +70,24 @@ def _worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_two_rank_partitioned_solve_equals_one_rank_oracle_solve():
+@pytest.mark.parametrize("world", [2, 3, 4])
+def test_partitioned_solve_equals_one_rank_oracle_solve(world):
+    """2 ranks: two body ranges; 3: one body each (uneven shares: the padded all-gather);
+    4: more ranks than bodies, one rank owns nothing and still joins every collective."""
     from oracle import Problem, fields, gmres
-    world = 2
     mgr = mp.Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     x0, it0, c0, parts = out[0]
-    x1, it1, c1, _ = out[1]
-    assert c0 and c1 and it0 == it1
-    assert np.array_equal(x0, x1)                     # every rank holds the same gathered solution
-    assert len(parts) == 2 and parts[0][0] == 0 and parts[0][1] == parts[1][0] and parts[1][1] == 3
+    for q in range(1, world):
+        xq, itq, cq, _ = out[q]
+        assert cq and itq == it0
+        assert np.array_equal(xq, x0)                 # every rank holds the same gathered solution
+    assert c0
+    assert len(parts) == world and parts[0][0] == 0 and parts[-1][1] == 3
+    assert all(parts[i][1] == parts[i + 1][0] for i in range(world - 1))
+    if world == 4:
+        assert parts[3] == (3, 3)
     wl = _workload()
     P = Problem(wl)
     v = fields.plane_wave(P.nodes.x, wl.directions, wl.k)
