@@ -73,14 +73,29 @@ def row_ranges(sizes: Sequence[int], parts: Sequence[Tuple[int, int]]) -> List[T
     return [(int(offs[b]), int(offs[e])) for b, e in parts]
 
 
+class RankFailure(RuntimeError):
+    """A collective of the partitioned solve failed: a peer rank left (raised, exited or
+    was killed between steps) or the process group's timeout ran out.  Raised on every
+    surviving rank at its next exchange, so no rank waits forever on a dead peer; the
+    solve cannot continue without that rank's bodies."""
+
+
 class Exchange:
-    """The two collectives of the partitioned solve, on torch.distributed."""
+    """The two collectives of the partitioned solve, on torch.distributed.  A failed
+    collective (a peer gone, or the group's timeout: pass a short `timeout` to
+    init_process_group to bound the wait) surfaces as RankFailure naming the step."""
 
     def __init__(self, dist, rows: Sequence[Tuple[int, int]]):
         self.dist = dist
         self.rows = list(rows)
         self.rank = dist.get_rank()
         self.world = dist.get_world_size()
+
+    def _collective(self, what, fn, *args):
+        try:
+            fn(*args)
+        except Exception as e:          # the backend's error type differs (gloo, NCCL)
+            raise RankFailure("%s failed on rank %d of %d: %s" % (what, self.rank, self.world, e)) from e
 
     def allgather_rows(self, local):
         """Full N x R array from every rank's owned rows (rank order = row order).  The
@@ -96,9 +111,10 @@ class Exchange:
         send[: t.shape[0]] = t
         parts = [t.new_zeros((mx, R)) for _ in counts]
         if t.is_complex():                    # the collectives move real views of the complex data
-            self.dist.all_gather([torch.view_as_real(p) for p in parts], torch.view_as_real(send))
+            self._collective("all-gather of sigma", self.dist.all_gather, [torch.view_as_real(p) for p in parts],
+                             torch.view_as_real(send))
         else:
-            self.dist.all_gather(parts, send)
+            self._collective("all-gather of sigma", self.dist.all_gather, parts, send)
         full = torch.cat([p[:n] for p, n in zip(parts, counts)], 0)
         return full.numpy() if is_np else full
 
@@ -108,10 +124,9 @@ class Exchange:
         is_np = isinstance(a, np.ndarray)
         t = torch.from_numpy(np.ascontiguousarray(a)) if is_np else a
         if t.is_complex():
-            r = torch.view_as_real(t)
-            self.dist.all_reduce(r)
+            self._collective("all-reduce of dot products", self.dist.all_reduce, torch.view_as_real(t))
         else:
-            self.dist.all_reduce(t)
+            self._collective("all-reduce of dot products", self.dist.all_reduce, t)
         return t.numpy() if is_np else t
 
 

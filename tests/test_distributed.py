@@ -135,3 +135,67 @@ def test_partition_balances_pair_work():
         assert max(loads) <= sum(w) / world + max(w)
     rr = row_ranges(sizes, partition_bodies(sizes, 3))
     assert rr[0][0] == 0 and rr[-1][1] == N
+
+
+class _FailingOperator(OracleOperator):
+    """Raises at its n-th apply: a rank that fails between two steps (nothing in flight)."""
+
+    def __init__(self, P, rows, fail_at):
+        super().__init__(P, rows)
+        self.calls = 0
+        self.fail_at = fail_at
+
+    def apply_local(self, sigma_full):
+        self.calls += 1
+        if self.calls == self.fail_at:
+            raise RuntimeError("injected rank failure")
+        return super().apply_local(sigma_full)
+
+
+def _failing_worker(rank, world, port, out):
+    import datetime
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    from oracle import Problem, fields
+    from paper_1406_0236_gb300.distributed import RankFailure
+    wl = _workload()
+    P = Problem(wl)
+    sizes = [b.shape.n_nodes for b in wl.bodies]
+    rows = row_ranges(sizes, partition_bodies(sizes, world))
+    ex = Exchange(dist, rows)
+    op = _FailingOperator(P, rows[rank], 3) if rank == 1 else OracleOperator(P, rows[rank])
+    v = fields.plane_wave(P.nodes.x, wl.directions, wl.k)
+    t0 = time.time()
+    try:
+        solve_partitioned(op, ex, v[rows[rank][0]:rows[rank][1]], 1e-12, maxit=200)
+        out[rank] = ("finished", "", time.time() - t0)
+    except RankFailure as e:
+        out[rank] = ("rank_failure", str(e), time.time() - t0)
+    except RuntimeError as e:
+        out[rank] = ("error", str(e), time.time() - t0)
+    # a failed rank leaves without tearing the group down; its sockets close with the process
+
+
+def test_a_failed_rank_ends_the_others_collectives_with_an_error():
+    """Failure detection on the host: rank 1 raises between two GMRES steps and exits;
+    rank 0's next exchange ends with RankFailure (peer gone, or the group's 20 s timeout)
+    instead of waiting forever."""
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    alive = [p.is_alive() for p in procs]
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    assert not any(alive), "a rank was still waiting after 120 s"
+    assert out[1][0] == "error" and "injected" in out[1][1]
+    assert out[0][0] == "rank_failure", out[0]
+    assert "rank 0 of 2" in out[0][1]
+    assert out[0][2] < 60.0
