@@ -49,7 +49,7 @@ FLOPS_PER_PAIR = 36       # algorithmic flops of one pair interaction at R = 1 (
 ORACLE_ITERS = 16
 # DRAM bytes (read + write) per launch on this workload from one ncu capture of each kernel
 # (profiles/); None for a kernel without a capture of its current version.
-DRAM_BYTES_NCU = {"nbody64_sym_kernel": 25.96e6, "nbody32_sym_kernel": 15.85e6, "nbody_dfl_sym_kernel": 30.14e6}
+DRAM_BYTES_NCU = {"nbody64_sym_kernel": 25.96e6, "nbody32_sym_kernel": 15.73e6, "nbody_dfl_sym_kernel": 30.14e6}
 # FP32-pipe (FMA) thread operations per unordered node pair of the lean double-float kernel,
 # counted by ncu (profiles/nbody_dfl_sym_kernel_mixed4_shells.md)
 DFL_OPS_PER_UNORDERED_PAIR = 440

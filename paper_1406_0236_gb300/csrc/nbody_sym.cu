@@ -168,11 +168,13 @@ nbody64_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict
 // G = X P + Q, P = E (1 - ikr), Q = -i eta E (X = n.d / r^2 with the source-side normal),
 // so that P and Q, computed once per node pair, leave two FMAs per direction;
 // e^{ikr} comes straight from the transcendental unit (its own argument scaling).
-// One right-hand side with two packed target pairs per thread fits 96 registers without
-// spills: five 128-thread CTAs per SM (20 warps) hide more of the FMA and transcendental-unit
-// latency than four.
+// One right-hand side with two packed target pairs per thread is held to 80 registers (a
+// few bytes of spills): six 128-thread CTAs per SM (24 warps) hide more of the FMA and
+// transcendental-unit latency than five at 96 registers, four at 120 or seven at 72 with
+// more spills (36.8 / 37.5 / 38.6 / 39.3 ms on 258,560 unknowns).
+static constexpr int SYM32_MIN_BLOCKS = 6;
 template <int RC, int TP>
-__global__ void __launch_bounds__(SYM_T / (2 * TP), (RC == 1 && TP == 2) ? 5 : 1)
+__global__ void __launch_bounds__(SYM_T / (2 * TP), (RC == 1 && TP == 2) ? SYM32_MIN_BLOCKS : 1)
 nbody32_sym_kernel(const int2 *__restrict__ pairs, const TargetBlock *__restrict__ blocks, int R,
                    const float4 *__restrict__ pos, const float4 *__restrict__ nrm, const float2 *__restrict__ sw,
                    float k, float eta, float kt, double2 *__restrict__ y)
