@@ -395,16 +395,17 @@ hzb_status hzb_eval_field(hzb_ctx *ctx, int n, const double *x, double *out);
 /* Compute every shape's ID on the GPU and switch the acceleration on.  The ID is of
  * the proxy matrix [K(z, y_j) w_j ; G(x_i, z) ; dG/dn_z(x_i, z)] (rows: points z of a
  * sphere of radius rho about the body centre, n_theta Gauss-Legendre rings in
- * cos(theta) times the body's N_F azimuths; each block scaled to unit Frobenius norm);
+ * cos(theta) times the body's N_F azimuths, or for an open shell 3 N_F azimuths in three
+ * classes offset by 0, 1/3 and 2/3 of the azimuthal step, which removes the ~1e-6 error
+ * floor that N_F azimuths leave on a shell's off-diagonal blocks; each block scaled to
+ * unit Frobenius norm);
  * its rank k counts the pivots of a column-pivoted QR with |R_jj| > eps |R_11|.
  *   eps:          tolerance in [0, 1); 0 keeps every column of nonzero pivot
  *   n_theta:      proxy rings, 0 = max(16, ceil(1.2 N_G)), at most 4096
  *   proxy_radius: rho for every shape, or 0 = per shape midway between its largest
  *                 node radius and the nearest other body's bounding sphere
  * Needs hzb_build_scattering_matrices.  HZB_EINVAL if a proxy sphere cannot enclose
- * its body while excluding every other body (bodies too close), or if an open shell is
- * asked for eps < 1e-6 (the proxy sphere is sampled at the body's N_F azimuths, which
- * leaves an error floor near 1e-6 on a shell's off-diagonal blocks).  Device memory: about
+ * its body while excluding every other body (bodies too close).  Device memory: about
  * 3 k n complex doubles per shape while it is compressed, then k n + 1.5 k^2. */
 hzb_status hzb_compress(hzb_ctx *ctx, double eps, int n_theta, double proxy_radius);
 

@@ -36,7 +36,6 @@
 namespace hzb {
 
 static const double CP_PI = 3.14159265358979323846;
-static const double OPEN_SHELL_EPS_FLOOR = 1e-6;   // smallest ID tolerance accepted for open shells
 
 // ------------------------------------------------------------------ block reductions
 
@@ -61,20 +60,26 @@ __device__ double block_sum(double v, double *sh)
 
 // ------------------------------------------------------------------ 1. proxy modal matrices
 
-// One block per (proxy ring r, body ring i): samples f_b(m) at the azimuth offset
-// 2 pi m / N_F for the three blocks, then M^_p(b n_theta + r, i) = sum_m f_b(m) cos(2 pi p m / N_F).
-// Mh: (M+1) matrices of 3 n_theta rows x N_G columns, column-major; fsq: per (i, r) the
-// three sums of |f_b|^2 (block norms).
-__global__ void proxy_modes_kernel(int NG, int NF, int nth, const double *__restrict__ ring,
+// One block per (proxy ring r, body ring i): samples f_b(m) at the azimuth
+// 2 pi (m + t / Q) / N_F for the three blocks, t = r / nth_base the ring's offset class
+// (Q = 1: the body's own azimuths; Q = 3: offsets 0, +1/3 and +2/3 of the azimuthal step,
+// a set closed under reflection, so M^_{-p} and M^_p have the same Gram matrix and one
+// pivoted QR per |p| still serves both), then M^_p(b nth + r, i) = sum_m f_b(m)
+// e^{-2 pi i p m / N_F} (for Q = 1, f_b is even in m and the sum is the cosine sum).
+// Mh: (M+1) matrices of 3 nth rows x N_G columns, column-major (nth = Q nth_base rings:
+// class-major, cth repeated per class); fsq: per (i, r) the three sums of |f_b|^2.
+__global__ void proxy_modes_kernel(int NG, int NF, int nth, int nth_base, int Q, const double *__restrict__ ring,
                                    const double *__restrict__ cth, double rho, double k, double eta,
                                    double2 *__restrict__ Mh, double *__restrict__ fsq)
 {
     extern __shared__ double2 psm[];
     double2 *f = psm;                                 // 3 x NF samples
     double *cs = (double *)(psm + 3 * NF);            // cos(2 pi m / NF)
+    double *sn = cs + NF;                             // sin(2 pi m / NF)
     __shared__ double red[32];
     const int r = blockIdx.x, i = blockIdx.y;
     const int M = (NF - 1) / 2, rows = 3 * nth;
+    const double frac = (double)(r / nth_base) / Q;   // the ring's azimuth offset, in steps
     const double ri = ring[8 * i], zi = ring[8 * i + 1], nri = ring[8 * i + 2], nzi = ring[8 * i + 3];
     const double wi = ring[8 * i + 4] * ri * 2.0 * CP_PI / NF;
     const double ct = cth[r], st = sqrt(fmax(0.0, 1.0 - ct * ct));
@@ -83,6 +88,8 @@ __global__ void proxy_modes_kernel(int NG, int NF, int nth, const double *__rest
         double sd, cd;
         sincospi(2.0 * m / NF, &sd, &cd);
         cs[m] = cd;
+        sn[m] = sd;
+        if (Q > 1) sincospi(2.0 * (m + frac) / NF, &sd, &cd);
         const double ux = st * cd, uy = st * sd, uz = ct;                    // n_z
         const double dx = rho * ux - ri, dy = rho * uy, dz = rho * uz - zi;  // z - y
         const double R = sqrt(dx * dx + dy * dy + dz * dz), iR = 1.0 / R;
@@ -121,6 +128,11 @@ __global__ void proxy_modes_kernel(int NG, int NF, int nth, const double *__rest
             const double cv = cs[idx];
             ax = fma(fb[m].x, cv, ax);
             ay = fma(fb[m].y, cv, ay);
+            if (Q > 1) {                              // f (cos - i sin)
+                const double sv = sn[idx];
+                ax = fma(fb[m].y, sv, ax);
+                ay = fma(-fb[m].x, sv, ay);
+            }
             idx += p;
             if (idx >= NF) idx -= NF;
         }
@@ -833,9 +845,15 @@ static hzb_status compress_shape(hzb_ctx *c, int shape, double eps, int n_theta,
 {
     ShapeDev &sd = *c->shapes[shape];
     const int NG = sd.geom.NG, NF = sd.geom.NF, M = sd.geom.M, n = NG * NF, modes = M + 1;
-    const int nth = n_theta, mrows = 3 * nth;
+    // proxy azimuths: the body's own N_F, or (open shells, whose cavity sits inside the proxy
+    // sphere with the body) 3 N_F in three offset classes, which removes the ~1e-6 error
+    // floor of the off-diagonal blocks of Eq. (ip0) at small N_F
+    const int Q = sd.geom.spec.kind == HZB_OPEN_SHELL ? 3 : 1;
+    const int nth = Q * n_theta, mrows = 3 * nth;
     std::vector<double> cthv, wts;
-    gauss_legendre(nth, cthv, wts);
+    gauss_legendre(n_theta, cthv, wts);
+    for (int t = 1; t < Q; ++t)
+        for (int r = 0; r < n_theta; ++r) cthv.push_back(cthv[r]);
     DevBuf<double> cth, fsq, scale, nrm2, thr2, beta;
     DevBuf<double2> Mh, u, Z;
     DevBuf<int> perm, rank, pos;
@@ -856,11 +874,11 @@ static hzb_status compress_shape(hzb_ctx *c, int shape, double eps, int n_theta,
     if (check_cuda(c, cudaMemcpyAsync(cth.ptr, cthv.data(), nth * sizeof(double), cudaMemcpyHostToDevice, c->stream),
                    "proxy"))
         return done(HZB_ECUDA);
-    const size_t smem = (size_t)NF * (3 * sizeof(double2) + sizeof(double));
+    const size_t smem = (size_t)NF * (3 * sizeof(double2) + 2 * sizeof(double));
     if (smem > 200 * 1024) return done(fail(c, HZB_EINVAL, "n_modes too large for the proxy modes"));
     cudaFuncSetAttribute(proxy_modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    proxy_modes_kernel<<<dim3(nth, NG), 128, smem, c->stream>>>(NG, NF, nth, sd.ring.ptr, cth.ptr, rho, c->k, c->eta,
-                                                                Mh.ptr, fsq.ptr);
+    proxy_modes_kernel<<<dim3(nth, NG), 128, smem, c->stream>>>(NG, NF, nth, n_theta, Q, sd.ring.ptr, cth.ptr, rho,
+                                                                c->k, c->eta, Mh.ptr, fsq.ptr);
     block_scale_kernel<<<1, 1024, 0, c->stream>>>(NG * nth, NF, fsq.ptr, scale.ptr);
     scale_rows_kernel<<<(unsigned)((mhn + 255) / 256), 256, 0, c->stream>>>(mhn, nth, scale.ptr, Mh.ptr);
     // row compression: column-pivoted QR of every mode
@@ -1420,15 +1438,6 @@ extern "C" hzb_status hzb_compress(hzb_ctx *c, double eps, int n_theta, double p
             st = fail(c, HZB_EINVAL, "proxy sphere must enclose its body and exclude every other body");
         }
         if (st) break;
-        // The proxy sphere is sampled at the body's N_F azimuths only.  For an open shell
-        // that leaves an error floor near 1e-6 on the off-diagonal blocks of Eq. (ip0) at
-        // small N_F (offset proxy rings remove it; pinned on the CPU): tighter tolerances
-        // are refused rather than missed silently.
-        if (c->shapes[s]->geom.spec.kind == HZB_OPEN_SHELL && eps < OPEN_SHELL_EPS_FLOOR) {
-            st = fail(c, HZB_EINVAL, "open-shell shapes are compressed only for eps >= 1e-6 (the proxy sphere "
-                                     "is sampled at the body's azimuths, whose error floor is near 1e-6)");
-            break;
-        }
         const int nt = n_theta > 0 ? n_theta : std::max(16, (int)std::ceil(1.2 * c->shapes[s]->geom.NG));
         st = compress_shape(c, (int)s, eps, nt, rho);
     }
