@@ -42,16 +42,19 @@ WORKLOAD = "spheroids8_258560"
 TOL_MIXED = 1e-7          # residual tolerance of the timed mixed solves (density error ~6e-9)
 TOL_REF = 1e-12           # reference density (FP64-accurate, untimed)
 TOL_FP64 = 1e-11          # the plain FP64 GPU path (density error <= 1e-10 against the reference)
-FLOPS_PER_PAIR = 36       # algorithmic flops of one pair interaction at R = 1 (FMA = 2)
+# algorithmic flops of one pair interaction at R = 1 (FMA = 2): d (3), r^2 (5), 1/r and r (2),
+# the phase (2), n.d and its scaling (7), the complex kernel value (9), the complex
+# multiply-add with sigma (8); rsqrt, sin and cos run on the transcendental unit besides
+FLOPS_PER_PAIR = 36
 # FP64 GMRES iterations of the FP64 GPU path on this workload at residual 3e-8, the stop that
-# gives a density error <= 1e-7 (3.9e-8; measured on GB300); the reference arm's oracle
+# gives a density error <= 1e-7 (3.9e-8, measured on GB300); the reference arm's oracle
 # solve is its apply time times this count (a full oracle GMRES would take hours)
 ORACLE_ITERS = 16
 # DRAM bytes (read + write) per launch on this workload from one ncu capture of each kernel
 # (profiles/); None for a kernel without a capture of its current version.
 DRAM_BYTES_NCU = {"nbody64_sym_kernel": 25.96e6, "nbody32_sym_kernel": 15.73e6, "nbody_dfl_sym_kernel": 30.14e6}
 # FP32-pipe (FMA) thread operations per unordered node pair of the lean double-float kernel,
-# counted by ncu (profiles/nbody_dfl_sym_kernel_mixed4_shells.md)
+# counted by ncu (thread instructions per unordered pair on the four-body case)
 DFL_OPS_PER_UNORDERED_PAIR = 440
 
 
