@@ -397,7 +397,7 @@ int dfl_default_nsplit(hzb_ctx *c, int R)
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
     const int rc = dfl_rc(R), nt = rc == 32 ? 256 : 512;
-    const long long ctas = (long long)c->n_tblocks * (DFL_T / nt) * ((R + rc - 1) / rc);
+    const long long ctas = std::max<long long>(1, (long long)c->n_tblocks * (DFL_T / nt) * ((R + rc - 1) / rc));
     const long long ns = (4LL * sms + ctas - 1) / ctas;
     return (int)std::min<long long>(64, std::max<long long>(1, ns));
 }
