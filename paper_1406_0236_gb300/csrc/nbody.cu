@@ -227,8 +227,7 @@ nbody32x2_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
 #pragma unroll
         for (int c = 0; c < RC; ++c) ax[m][c] = ay[m][c] = 0ull;
     }
-    const f2x k2 = f2_splat(k), eta2 = f2_splat(eta), kt2 = f2_splat(k_turns);
-    const f2x rnd2 = f2_splat(12582912.0f), twopi2 = f2_splat(6.283185307179586f);
+    const f2x k2 = f2_splat(k), eta2 = f2_splat(eta);
     const int c0 = blockIdx.z * chunk, c1 = min(N, c0 + chunk);
     for (int range = 0; range < 2; ++range) {
         const int lo = range ? max(c0, tb.excl_hi) : c0;
@@ -271,10 +270,11 @@ nbody32x2_kernel(const TargetBlock *__restrict__ blocks, int N, int R, int chunk
                     const f2x X = f2_mul(nd, f2_mul(ir, ir));
                     const f2x A = f2_mul(X, ir);
                     const f2x B = f2_fma(k2, X, f2_mul(eta2, ir));
-                    const f2x t = f2_mul(f2_mul(r2, ir), kt2);
-                    const f2x th = f2_mul(f2_sub(t, f2_sub(f2_add(t, rnd2), rnd2)), twopi2);
+                    // e^{ikr} straight from the transcendental unit, which scales its argument
+                    // to turns itself (the rounding an explicit reduction would make)
+                    const f2x kr = f2_mul(f2_mul(r2, ir), k2);
                     float tha, thb, sa, ca, sb, cb;
-                    f2_unpack(th, tha, thb);
+                    f2_unpack(kr, tha, thb);
                     __sincosf(tha, &sa, &ca);
                     __sincosf(thb, &sb, &cb);
                     const f2x s2 = f2_pack(sa, sb), c2 = f2_pack(ca, cb);
