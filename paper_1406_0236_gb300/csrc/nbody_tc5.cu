@@ -14,13 +14,16 @@
 //     [Re y | Im y] in the 128 x 2RC accumulator;
 //   * one thread issues 24 MMAs (4 k-steps of 8 sources x {Ahi Bhi, Ahi Blo, Alo Bhi}
 //     for both products) with tcgen05.mma.kind::tf32 into tensor memory and commits
-//     them to an mbarrier; the tile's accumulator starts from zero;
+//     them to an mbarrier; the tile's accumulator starts from zero.  The single-term
+//     form (TERMS = 1, opt-in engine) keeps only the hi parts: 8 MMAs, half the operand
+//     stores, about 3e-4 relative error in the sum;
 //   * after the commit, each warp reads 32 lanes x RC columns of the accumulator
 //     (tcgen05.ld) and adds them to running FP32 sums in registers: the tensor cores'
 //     internal accumulation is not rounded to nearest, so chaining ~10^4 tiles in tensor
 //     memory would drift.
-// The next tile's positions and densities are loaded into registers while the current
-// tile's pair kernels and MMAs run.  Every mbarrier wait is bounded; on a timeout the CTA
+// TF32 rounding is done by two integer operations on the bit pattern (t5_tf32i), which
+// measured faster than the conversion instruction.  The next tile's positions and
+// densities are loaded into registers while the current tile's pair kernels and MMAs run.  Every mbarrier wait is bounded; on a timeout the CTA
 // sets an error flag, writes NaN outputs, frees its tensor memory and returns.
 #include <algorithm>
 
