@@ -12,8 +12,9 @@
 // sigma' = w sigma / (4 pi); E, r and k r are shared by the two directions.
 //
 // Arithmetic: lean double-float (lean_df.cuh): error-free products and sums left
-// unnormalised, accumulators renormalised once per tile.  1/r: the hardware estimate of 1/sqrt(r^2) and one
-// Halley step (cubic convergence, so the estimate's 2^-23 error falls below 2^-60).
+// unnormalised, accumulators renormalised once per tile.  1/r: the hardware estimate of
+// 1/sqrt(r^2) and one Halley step (cubic convergence, so the estimate's 2^-23 error falls
+// below 2^-60).
 // e^{i k r}: k r / (2 pi) in turns is reduced to [-1/2, 1/2] and then to the nearest of
 // 1024 table angles (cos, sin in double-float, shared memory); the remainder
 // |delta| <= pi / 1024 enters through cos(delta) - 1 = -delta^2/2 + delta^4/24 and
